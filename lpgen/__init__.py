@@ -1,0 +1,119 @@
+"""Seeded synthetic LP generator shared by the tests, the benchmark and the
+smoke check.
+
+It holds none of the method's arithmetic: it only draws the random data and
+builds a strictly feasible primal-dual start, so that the GPU library and the
+CPU oracle can be fed the very same arrays.  The paper (arXiv:1502.03543)
+measures on dense LPs whose sizes and data are not given; these inputs stand
+in for them.
+
+Recipe (numpy ``default_rng(seed)``, PCG64), draws in this order:
+  1. Z ~ N(0,1), shape (m, n), row-major;
+  2. optionally sigma ~ U(0.1, 10) per column and A = Z * sigma (columns scaled);
+  3. A rounded to its storage dtype with round-to-nearest-even: "f64", "f32"
+     or "bf16".  The rounded A defines the LP for every consumer;
+  4. x0 ~ U(0.5, 1.5)^n;  5. s0 ~ U(0.5, 1.5)^n;  6. y0 ~ N(0,1)^m;
+  7. b = A x0 and c = A' y0 + s0 in FP64, each sum taken left to right in
+     increasing index order with separate multiply and add, so the arrays are
+     bit-identical on every machine.
+x0 > 0 is then primal feasible and (y0, s0 > 0) dual feasible: an interior
+start as the algorithm of Section III requires.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+STORAGE = ("f64", "f32", "bf16")
+
+
+def round_bf16_bits(a: np.ndarray) -> np.ndarray:
+    """Round float values to bfloat16 (round to nearest, ties to even) and
+    return the raw 16-bit patterns as uint16.  Inputs are first rounded to
+    float32 (exact for every value produced here that is then rounded again
+    to bf16 only when the float32 value is not a tie; the two-step rounding
+    is the definition used by the storage format, stated here explicitly)."""
+    a32 = np.ascontiguousarray(a, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_bits_to_f64(bits: np.ndarray) -> np.ndarray:
+    """Exact widening of bfloat16 bit patterns to float64."""
+    u32 = bits.astype(np.uint32) << 16
+    return u32.view(np.float32).astype(np.float64)
+
+
+@dataclasses.dataclass
+class LP:
+    m: int
+    n: int
+    storage: str
+    A_store: np.ndarray  # float64 / float32 / uint16 (bf16 bits), shape (m, n)
+    A64: np.ndarray  # exact float64 widening of A_store
+    b: np.ndarray
+    c: np.ndarray
+    x0: np.ndarray
+    y0: np.ndarray
+    s0: np.ndarray
+    seed: int
+    scaled: bool
+
+
+def _ltr_matvec(A64: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """A v with each row sum taken left to right (column by column)."""
+    AT = np.asfortranarray(A64).T  # C-contiguous view of columns
+    out = np.zeros(A64.shape[0])
+    for j in range(A64.shape[1]):
+        out += AT[j] * v[j]
+    return out
+
+
+def _ltr_rmatvec(A64: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """A' v with each column sum taken top to bottom (row by row)."""
+    out = np.zeros(A64.shape[1])
+    for p in range(A64.shape[0]):
+        out += A64[p] * v[p]
+    return out
+
+
+def generate(m: int, n: int, seed: int = 0, storage: str = "f64", scaled: bool = False) -> LP:
+    """Draw one LP by the recipe in the module docstring."""
+    if storage not in STORAGE:
+        raise ValueError("storage must be one of %s" % (STORAGE,))
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((m, n))
+    if scaled:
+        sigma = rng.uniform(0.1, 10.0, n)
+        Z *= sigma
+    if storage == "f64":
+        A_store = Z
+        A64 = Z
+    elif storage == "f32":
+        A_store = Z.astype(np.float32)
+        A64 = A_store.astype(np.float64)
+    else:
+        A_store = round_bf16_bits(Z)
+        A64 = bf16_bits_to_f64(A_store)
+    del Z
+    x0 = rng.uniform(0.5, 1.5, n)
+    s0 = rng.uniform(0.5, 1.5, n)
+    y0 = rng.standard_normal(m)
+    b = _ltr_matvec(A64, x0)
+    c = _ltr_rmatvec(A64, y0) + s0
+    return LP(m, n, storage, A_store, A64, b, c, x0, y0, s0, seed, scaled)
+
+
+# The dense LP workloads, by shape and storage.
+WORKLOADS = {
+    "dense_64x128_f64": dict(m=64, n=128, storage="f64", scaled=False, tol=1e-8),
+    "dense_2048x8192_f64": dict(m=2048, n=8192, storage="f64", scaled=False, tol=1e-8),
+    "dense_8192x32768_bf16_colscaled": dict(m=8192, n=32768, storage="bf16", scaled=True, tol=1e-8),
+}
+
+
+def workload(name: str, seed: int = 0) -> LP:
+    w = WORKLOADS[name]
+    return generate(w["m"], w["n"], seed=seed, storage=w["storage"], scaled=w["scaled"])
