@@ -1,0 +1,62 @@
+/*
+ * pdas_components.h -- step-by-step entry points of libpdas.
+ *
+ * Each call runs one stage of the Newton-direction solve of Eq. (3)/(4)
+ * (N. Divakar, arXiv:1502.03543, Section V) on the handle's workspace, so a
+ * caller or a test can check each stage on its own.  Conventions are those
+ * of pdas.h: device pointers, the handle's stream, status codes, no traps.
+ */
+#ifndef PDAS_COMPONENTS_H
+#define PDAS_COMPONENTS_H
+
+#include "pdas.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Forms D = S^{-1} X (Eq. 4) and the lower triangle of the normal matrix
+ * M = A D A' (Section V) in the workspace, in the handle's precision form
+ * (FP64 for PDAS_FP64 or once a mixed form has switched to FP64; FP32 from
+ * tensor-core or SIMT formation otherwise).  A: m x n (a_dtype); x, s: n. */
+pdas_status pdas_form_normal(pdas_handle h, const void* A, const double* x, const double* s);
+
+/* Copies the workspace matrix -- M after pdas_form_normal, the factor L
+ * after pdas_factor -- to dst as a dense row-major m x m array (lower
+ * triangle meaningful, the rest unspecified).  *dtype_out receives
+ * PDAS_A_F64 (double) or PDAS_A_F32 (float), the element type written. */
+pdas_status pdas_copy_matrix(pdas_handle h, void* dst, int* dtype_out);
+
+/* Loads the lower triangle of src (row-major m x m, element type given by
+ * dtype: PDAS_A_F64 or PDAS_A_F32, converted to the workspace precision)
+ * into the workspace matrix. */
+pdas_status pdas_load_matrix(pdas_handle h, const void* src, int dtype);
+
+/* Blocked Cholesky M = L L' of the workspace matrix, in place (the
+ * symmetric positive definite solve of Section V-A).  PDAS_ERR_NOT_SPD with
+ * pdas_last_error_index = the first failing pivot if M is not SPD. */
+pdas_status pdas_factor(pdas_handle h);
+
+/* With the workspace factor: forward substitution L z = rhs, then back
+ * substitution L' out = z.  rhs, out: m doubles (may alias). */
+pdas_status pdas_factor_solve(pdas_handle h, const double* rhs, double* out);
+
+/* Newton direction at (x, s) without stepping (Eq. 3 via Eq. 4):
+ * dy solves (A D A') dy = A x (with FP64 refinement in mixed forms),
+ * ds = -A' dy, dx = D(-ds) - x.  dx, ds: n; dy: m.  info may be NULL
+ * (psi, theta, gap fields are not set). */
+pdas_status pdas_direction(pdas_handle h, const void* A, const double* x, const double* s, double* dx, double* dy,
+                           double* ds, pdas_iter_info* info);
+
+/* out (m) = A v (n), FP64 accumulation of exactly widened A: the right-hand
+ * side A x of the normal equations. */
+pdas_status pdas_gemv(pdas_handle h, const void* A, const double* v, double* out);
+
+/* out (n) = A' u (m), FP64 accumulation: the product behind ds = -A' dy. */
+pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDAS_COMPONENTS_H */

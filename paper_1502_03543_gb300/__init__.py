@@ -1,0 +1,211 @@
+"""GB300-native primal-dual affine scaling (PDAS) Newton-direction solver.
+
+Python binding of libpdas (include/pdas.h): argument marshalling only.  Every
+step of the solve runs in the library's CUDA kernels; PyTorch supplies device
+memory and the stream.  Method: N. Divakar, "Primal Dual Affine Scaling on
+GPUs", arXiv:1502.03543 -- the Newton system Eq. (3) reduced to
+(A D A') dy = A x by Eq. (4), ds = -A' dy, dx = D(-ds) - x, then the psi ratio
+test and the alpha/psi step of the algorithm in Section III.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as N
+
+__all__ = ["Solver", "PdasError", "FORMS", "A_DTYPES"]
+
+FORMS = {"fp64": N.FP64, "tf32_ir": N.TF32_IR, "bf16_ir": N.BF16_IR, "fp32_ir": N.FP32_IR}
+A_DTYPES = {torch.float64: N.A_F64, torch.float32: N.A_F32, torch.bfloat16: N.A_BF16}
+STATUS_NAMES = {
+    N.OK: "ok", N.OPTIMAL: "optimal", N.OPTIMAL_EXACT: "optimal_exact", N.MAX_ITER: "max_iter",
+    N.STALLED: "stalled", N.ZERO_DIRECTION: "zero_direction", N.ERR_ARG: "err_arg",
+    N.ERR_NOT_INTERIOR: "err_not_interior", N.ERR_NOT_SPD: "err_not_spd", N.ERR_NONFINITE: "err_nonfinite",
+    N.ERR_TIMEOUT: "err_timeout", N.ERR_CUDA: "err_cuda", N.ERR_UNSUPPORTED: "err_unsupported",
+}
+
+
+class PdasError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = int(code)
+        msg = "%s: %s (%d)" % (where, N.status_str(code), code)
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+    if t.data_ptr() % 16:
+        raise ValueError("%s must be 16-byte aligned" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A libpdas handle for m x n problems (1 <= m < n).
+
+    form: "fp64" (plain FP64), "bf16_ir", "tf32_ir" or "fp32_ir" (mixed
+    precision with FP64 refinement).  a_dtype: torch dtype A is stored in.
+    stream: torch.cuda.Stream (default: the current stream at construction).
+    Other keyword options map to pdas_options fields."""
+
+    def __init__(self, m, n, form="fp64", a_dtype=torch.float64, stream=None, **opts):
+        self.m, self.n = int(m), int(n)
+        self.form = form
+        self.a_dtype = a_dtype
+        lib = N.lib()
+        o = N.Options()
+        lib.pdas_default_options(ctypes.byref(o))
+        o.form = FORMS[form]
+        o.a_dtype = A_DTYPES[a_dtype]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        for k, v in opts.items():
+            if not hasattr(o, k) or k in ("form", "a_dtype", "stream"):
+                raise TypeError("unknown option %r" % k)
+            setattr(o, k, v)
+        self.options = o
+        h = ctypes.c_void_p()
+        st = lib.pdas_create(self.m, self.n, ctypes.byref(o), ctypes.byref(h))
+        if st != N.OK:
+            raise PdasError(st, "pdas_create")
+        self._h = h
+
+    # -- life cycle --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().pdas_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st, where, ok=(N.OK,)):
+        if st not in ok:
+            detail = ""
+            if st == N.ERR_CUDA:
+                detail = N.lib().pdas_last_error_message(self._h).decode()
+            elif st == N.ERR_NOT_SPD:
+                detail = "pivot %d" % N.lib().pdas_last_error_index(self._h)
+            raise PdasError(st, where, detail)
+        return st
+
+    def profile_enable(self, enable=True):
+        """Start (clear) or stop per-stage CUDA-event timing on the handle's stream."""
+        self._check(N.lib().pdas_profile_enable(self._h, int(bool(enable))), "pdas_profile_enable")
+
+    def profile_read(self):
+        """dict(ms={stage: ms}, calls={stage: n}, launches=kernels launched)."""
+        p = N.Profile()
+        self._check(N.lib().pdas_profile_read(self._h, ctypes.byref(p)), "pdas_profile_read")
+        return p.as_dict()
+
+    def last_error_index(self):
+        return int(N.lib().pdas_last_error_index(self._h))
+
+    # -- argument marshalling ----------------------------------------------
+    def _A(self, A):
+        return _ptr(A, self.a_dtype, self.m * self.n, "A")
+
+    def _vn(self, v, name):
+        return _ptr(v, torch.float64, self.n, name)
+
+    def _vm(self, v, name):
+        return _ptr(v, torch.float64, self.m, name)
+
+    # -- the algorithm -------------------------------------------------------
+    def step(self, A, b, c, x, y, s, alpha=0.95, raise_on_error=True):
+        """One iteration in place on (x, y, s).  Returns (status, info dict)."""
+        info = N.IterInfo()
+        st = N.lib().pdas_step(self._h, self._A(A), self._vm(b, "b"), self._vn(c, "c"), self._vn(x, "x"),
+                               self._vm(y, "y"), self._vn(s, "s"), float(alpha), ctypes.byref(info))
+        if raise_on_error:
+            self._check(st, "pdas_step", ok=(N.OK, N.OPTIMAL_EXACT))
+        return st, info.as_dict()
+
+    def solve(self, A, b, c, x, y, s, alpha=0.95, tol=1e-8):
+        """Run to the stop test in place on (x, y, s).  Returns dict(status,
+        status_name, iters, rel_gap); errors (status < 0) are returned, not raised."""
+        iters = ctypes.c_int(0)
+        gap = ctypes.c_double(0.0)
+        st = N.lib().pdas_solve(self._h, self._A(A), self._vm(b, "b"), self._vn(c, "c"), self._vn(x, "x"),
+                                self._vm(y, "y"), self._vn(s, "s"), float(alpha), float(tol),
+                                ctypes.byref(iters), ctypes.byref(gap))
+        return dict(status=st, status_name=STATUS_NAMES.get(st, str(st)), iters=iters.value, rel_gap=gap.value)
+
+    def direction(self, A, x, s):
+        """Newton direction at (x, s): returns (dx, dy, ds, info dict)."""
+        dev = x.device
+        dx = torch.empty(self.n, dtype=torch.float64, device=dev)
+        ds = torch.empty(self.n, dtype=torch.float64, device=dev)
+        dy = torch.empty(self.m, dtype=torch.float64, device=dev)
+        info = N.IterInfo()
+        st = N.lib().pdas_direction(self._h, self._A(A), self._vn(x, "x"), self._vn(s, "s"), _ptr(dx), _ptr(dy),
+                                    _ptr(ds), ctypes.byref(info))
+        self._check(st, "pdas_direction")
+        return dx, dy, ds, info.as_dict()
+
+    def backward(self, dL_dx):
+        dA = torch.empty(self.m * self.n, dtype=torch.float64, device=dL_dx.device)
+        db = torch.empty(self.m, dtype=torch.float64, device=dL_dx.device)
+        dc = torch.empty(self.n, dtype=torch.float64, device=dL_dx.device)
+        st = N.lib().pdas_backward(self._h, self._vn(dL_dx, "dL_dx"), _ptr(dA), _ptr(db), _ptr(dc))
+        self._check(st, "pdas_backward")
+        return dA.view(self.m, self.n), db, dc
+
+    # -- components ----------------------------------------------------------
+    def form_normal(self, A, x, s):
+        self._check(N.lib().pdas_form_normal(self._h, self._A(A), self._vn(x, "x"), self._vn(s, "s")),
+                    "pdas_form_normal")
+
+    def copy_matrix(self, device="cuda"):
+        """The workspace matrix (M or its factor L) as an m x m tensor."""
+        out = torch.empty(self.m * self.m, dtype=torch.float64, device=device)
+        dt = ctypes.c_int(0)
+        self._check(N.lib().pdas_copy_matrix(self._h, _ptr(out), ctypes.byref(dt)), "pdas_copy_matrix")
+        if dt.value == N.A_F32:
+            out = out.view(torch.float32)[: self.m * self.m].clone()
+        return out.view(self.m, self.m)
+
+    def load_matrix(self, M):
+        dtype = {torch.float64: N.A_F64, torch.float32: N.A_F32}[M.dtype]
+        self._check(N.lib().pdas_load_matrix(self._h, _ptr(M, numel=self.m * self.m), dtype), "pdas_load_matrix")
+
+    def factor(self, raise_on_error=True):
+        st = N.lib().pdas_factor(self._h)
+        if raise_on_error:
+            self._check(st, "pdas_factor")
+        return st
+
+    def factor_solve(self, rhs):
+        out = torch.empty_like(rhs)
+        self._check(N.lib().pdas_factor_solve(self._h, self._vm(rhs, "rhs"), _ptr(out)), "pdas_factor_solve")
+        return out
+
+    def gemv(self, A, v):
+        out = torch.empty(self.m, dtype=torch.float64, device=v.device)
+        self._check(N.lib().pdas_gemv(self._h, self._A(A), self._vn(v, "v"), _ptr(out)), "pdas_gemv")
+        return out
+
+    def gemv_t(self, A, u):
+        out = torch.empty(self.n, dtype=torch.float64, device=u.device)
+        self._check(N.lib().pdas_gemv_t(self._h, self._A(A), self._vm(u, "u"), _ptr(out)), "pdas_gemv_t")
+        return out

@@ -1,0 +1,741 @@
+// api.cu -- the C ABI of libpdas (include/pdas.h, include/pdas_components.h):
+// handle life cycle, the per-iteration orchestration of the Newton-direction
+// solve (Eq. 3 via Eq. 4, Section V), the psi ratio test and the step of the
+// algorithm in Section III, and pdas_solve's outer loop.
+//
+// One iteration on the handle's stream (FP64 form):
+//   scaling D = x/s -> r = A x -> M = A D A' (lower) -> Cholesky -> L z = r ->
+//   L' dy = z -> w = A' dy, ds = -w, dx = D w - x -> psi, theta -> step, gap.
+// Mixed forms replace the SYRK and Cholesky by their low-precision versions
+// and refine dy in FP64 (refine()): the residual A x - A(D(A' dy)) is formed
+// matrix-free in FP64 and corrected with the low-precision factor, as plain
+// iterative refinement and, when that stalls, as conjugate gradients
+// preconditioned by the same factor.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "pdas_internal.cuh"
+#include "syrk_tc.cuh"
+
+using namespace pdas;
+
+struct pdas_ctx {
+  int64_t m = 0, n = 0, ldm = 0;
+  pdas_options opt{};
+  cudaStream_t st = nullptr;
+  // FP64 vectors
+  double *D = nullptr, *r = nullptr, *dy = nullptr, *dx = nullptr, *ds = nullptr, *w = nullptr, *u = nullptr;
+  double *z = nullptr, *rho = nullptr, *delta = nullptr, *kp = nullptr, *kq = nullptr, *kz = nullptr;
+  double* part = nullptr;     // reduction partials (kPartMax)
+  double* gt_part = nullptr;  // gemv_t partials, gt_chunks x n
+  int gt_chunks = 1;
+  int64_t gt_rows = 1;
+  unsigned* tickets = nullptr;
+  int* flags = nullptr;
+  Scalars* sc = nullptr;
+  Scalars* sc_host = nullptr;  // pinned
+  double* M64 = nullptr;
+  float* M32 = nullptr;
+  TcWorkspace tc{};
+  int cur_f64 = 1;     // the workspace matrix in use is M64
+  int refactored = 0;  // a mixed form switched to FP64 for good
+  int64_t err_index = -1;
+  char errmsg[256] = {0};
+  // diagnostics of the last direction
+  int last_sweeps = 0;
+  double last_resid = 0.0;
+  int last_fp64 = 0;
+  // profiling: event pairs around stages, and the kernel-launch count
+  bool prof = false;
+  std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_stage;  // per recorded pair: stage index
+  size_t ev_used = 0;
+  int open_stage = -1;
+  double prof_ms[PDAS_STAGE_COUNT] = {0};
+  int64_t prof_calls[PDAS_STAGE_COUNT] = {0};
+  int64_t launches = 0;
+};
+
+namespace {
+
+constexpr double kRefineAccept = 1e-12;
+
+bool is_mixed(const pdas_ctx* h) { return h->opt.form != PDAS_FP64; }
+
+pdas_status cuda_fail(pdas_ctx* h, cudaError_t e, const char* where) {
+  snprintf(h->errmsg, sizeof(h->errmsg), "%s: %s", where, cudaGetErrorString(e));
+  return PDAS_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
+  } while (0)
+
+// A launch helper that starts `k` kernels: checked and counted.
+#define KL(call, k)        \
+  do {                     \
+    CK(call);              \
+    h->launches += (k);    \
+  } while (0)
+
+int64_t chol_launches(int64_t m) {
+  int64_t k = 0;
+  for (int64_t k0 = 0; k0 < m; k0 += kTile) k += (m - k0 - kTile > 0) ? 2 : 1;
+  return k;
+}
+
+pdas_status prof_fold(pdas_ctx* h);
+
+cudaError_t prof_record(pdas_ctx* h) {
+  if (h->ev_used == h->evs.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    h->evs.push_back(e);
+  }
+  return cudaEventRecord(h->evs[h->ev_used++], h->st);
+}
+
+pdas_status stage_begin(pdas_ctx* h, int stage) {
+  if (!h->prof) return PDAS_OK;
+  if (h->ev_used + 2 > 8192) {
+    pdas_status s = prof_fold(h);
+    if (s != PDAS_OK) return s;
+  }
+  CK(prof_record(h));
+  h->open_stage = stage;
+  return PDAS_OK;
+}
+
+pdas_status stage_end(pdas_ctx* h) {
+  if (!h->prof || h->open_stage < 0) return PDAS_OK;
+  CK(prof_record(h));
+  h->ev_stage.push_back(h->open_stage);
+  h->open_stage = -1;
+  return PDAS_OK;
+}
+
+// Synchronise and add the recorded pairs to the accumulators.
+pdas_status prof_fold(pdas_ctx* h) {
+  CK(cudaStreamSynchronize(h->st));
+  for (size_t i = 0; i < h->ev_stage.size(); ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->evs[2 * i], h->evs[2 * i + 1]));
+    h->prof_ms[h->ev_stage[i]] += ms;
+    h->prof_calls[h->ev_stage[i]] += 1;
+  }
+  h->ev_stage.clear();
+  h->ev_used = 0;
+  h->open_stage = -1;
+  return PDAS_OK;
+}
+
+#define STAGE(h, k)                               \
+  do {                                            \
+    pdas_status s_ = stage_begin((h), (k));       \
+    if (s_ != PDAS_OK) return s_;                 \
+  } while (0)
+#define STAGE_END(h)                              \
+  do {                                            \
+    pdas_status s_ = stage_end(h);                \
+    if (s_ != PDAS_OK) return s_;                 \
+  } while (0)
+
+template <typename F>
+pdas_status with_dtype(int dt, F&& f) {
+  switch (dt) {
+    case PDAS_A_F64: return f((const double*)nullptr);
+    case PDAS_A_F32: return f((const float*)nullptr);
+    case PDAS_A_BF16: return f((const __nv_bfloat16*)nullptr);
+  }
+  return PDAS_ERR_ARG;
+}
+
+// Reads the device scalars (one small copy + stream sync).
+pdas_status read_scalars(pdas_ctx* h) {
+  CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return PDAS_OK;
+}
+
+pdas_status device_status(pdas_ctx* h) {
+  const Scalars& s = *h->sc_host;
+  if (s.status == PDAS_ERR_NOT_SPD) h->err_index = s.fail_index;
+  return (pdas_status)s.status;
+}
+
+pdas_status reset_status(pdas_ctx* h) {
+  CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->st));
+  return PDAS_OK;
+}
+
+// A v -> out (base == null) or base - A v -> out; norm_slot as in launch_gemv.
+pdas_status gemv(pdas_ctx* h, const void* A, const double* v, const double* base, double* out, int norm_slot) {
+  return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    KL(launch_gemv<T>(h->st, h->m, h->n, (const T*)A, v, base, out, h->part, h->tickets, h->sc, norm_slot), 1);
+    return PDAS_OK;
+  });
+}
+
+// w = A' u, then the finish mode (see launch_gemv_t_finish).
+pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const double* x, double* o0, double* o1,
+                   double* o2) {
+  pdas_status s = with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    KL(launch_gemv_t<T>(h->st, h->m, h->n, (const T*)A, u, h->gt_part, h->gt_chunks, h->gt_rows), 1);
+    return PDAS_OK;
+  });
+  if (s != PDAS_OK) return s;
+  KL(launch_gemv_t_finish(h->st, h->n, h->gt_chunks, h->gt_part, mode, x, h->D, o0, o1, o2, h->sc), 1);
+  return PDAS_OK;
+}
+
+pdas_status ensure_m64(pdas_ctx* h) {
+  if (!h->M64) CK(cudaMalloc(&h->M64, sizeof(double) * h->ldm * h->m));
+  return PDAS_OK;
+}
+
+bool want_fp64(const pdas_ctx* h) { return !is_mixed(h) || h->refactored; }
+
+// a3: the normal matrix in the current precision.
+pdas_status form_normal(pdas_ctx* h, const void* A) {
+  if (want_fp64(h)) {
+    pdas_status s = ensure_m64(h);
+    if (s != PDAS_OK) return s;
+    h->cur_f64 = 1;
+    return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
+      using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+      KL(launch_syrk_simt<T>(h->st, h->m, h->n, (const T*)A, h->D, h->M64, nullptr, h->ldm, h->sc), 1);
+      return PDAS_OK;
+    });
+  }
+  h->cur_f64 = 0;
+  if (h->opt.form == PDAS_FP32_IR) {
+    return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
+      using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+      KL(launch_syrk_simt<T>(h->st, h->m, h->n, (const T*)A, h->D, nullptr, h->M32, h->ldm, h->sc), 1);
+      return PDAS_OK;
+    });
+  }
+  int k = 0;
+  CK(tc_form_normal(h->st, &h->tc, h->opt.form, h->opt.a_dtype, A, h->D, h->m, h->n, h->M32, h->ldm, h->sc, &k));
+  h->launches += k;
+  return PDAS_OK;
+}
+
+pdas_status factor(pdas_ctx* h) {
+  if (h->cur_f64) KL(cholesky<double>(h->st, h->m, h->ldm, h->M64, h->sc), chol_launches(h->m));
+  else KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->sc), chol_launches(h->m));
+  return PDAS_OK;
+}
+
+// out = (L L')^{-1} rhs with the current factor (via h->z).
+pdas_status factor_solve(pdas_ctx* h, const double* rhs, double* out) {
+  if (h->cur_f64) {
+    KL(trsv_lower<double>(h->st, h->m, h->ldm, h->M64, rhs, h->z, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_upper_t<double>(h->st, h->m, h->ldm, h->M64, h->z, out, h->flags, h->tickets, h->sc), 1);
+  } else {
+    KL(trsv_lower<float>(h->st, h->m, h->ldm, h->M32, rhs, h->z, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_upper_t<float>(h->st, h->m, h->ldm, h->M32, h->z, out, h->flags, h->tickets, h->sc), 1);
+  }
+  return PDAS_OK;
+}
+
+// rho = r - A(D(A' v)); leaves w = A' v in h->w and ||rho||_inf in sc->rho_norm.
+pdas_status residual(pdas_ctx* h, const void* A, const double* v) {
+  pdas_status s = gemv_t(h, A, v, 2, nullptr, h->u, nullptr, h->w);
+  if (s != PDAS_OK) return s;
+  return gemv(h, A, h->u, h->r, h->rho, 1);
+}
+
+// M v (matrix-free, FP64) -> out.
+pdas_status apply_normal(pdas_ctx* h, const void* A, const double* v, double* out) {
+  pdas_status s = gemv_t(h, A, v, 2, nullptr, h->u, nullptr, nullptr);
+  if (s != PDAS_OK) return s;
+  return gemv(h, A, h->u, nullptr, out, -1);
+}
+
+// FP64 refinement of dy for the mixed forms (a6).  Plain sweeps
+// dy += (LL')^{-1}(r - M dy) while each cuts ||rho|| at least in half; if a
+// sweep does not, conjugate gradients on M dy = r preconditioned by (LL')^{-1}
+// take over from the best iterate.  Returns PDAS_OK with h->w = A' dy for
+// the final dy, or PDAS_ERR_NOT_SPD-like failure codes through the status.
+// *ok = 0 when neither reached the tolerance (the caller re-factors in FP64).
+pdas_status refine(pdas_ctx* h, const void* A, int* ok) {
+  *ok = 0;
+  const double tol = h->opt.refine_tol;
+  const int cap = h->opt.refine_max;
+  pdas_status s = residual(h, A, h->dy);
+  if (s != PDAS_OK) return s;
+  if ((s = read_scalars(h)) != PDAS_OK) return s;
+  if ((s = device_status(h)) != PDAS_OK) return s;
+  const double rn = h->sc_host->rnorm > 0 ? h->sc_host->rnorm : 1.0;
+  double res = h->sc_host->rho_norm / rn;
+  int sweeps = 0;
+  bool krylov = false;
+  while (res > tol && sweeps < cap) {
+    if ((s = factor_solve(h, h->rho, h->delta)) != PDAS_OK) return s;
+    KL(launch_axpy(h->st, h->m, 1.0, h->delta, h->dy, h->sc), 1);
+    ++sweeps;
+    if ((s = residual(h, A, h->dy)) != PDAS_OK) return s;
+    if ((s = read_scalars(h)) != PDAS_OK) return s;
+    if ((s = device_status(h)) != PDAS_OK) return s;
+    const double nres = h->sc_host->rho_norm / rn;
+    if (!(nres <= 0.5 * res)) {
+      res = nres;
+      krylov = true;
+      break;
+    }
+    res = nres;
+  }
+  if (krylov && res > tol) {
+    // Preconditioned CG from the current dy: rho = r - M dy (in h->rho).
+    if ((s = factor_solve(h, h->rho, h->kz)) != PDAS_OK) return s;
+    CK(cudaMemcpyAsync(h->kp, h->kz, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
+    KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1);
+    if ((s = read_scalars(h)) != PDAS_OK) return s;
+    double rz = h->sc_host->dot_a;
+    double best = res;
+    while (sweeps < 3 * cap && res > tol) {
+      if ((s = apply_normal(h, A, h->kp, h->kq)) != PDAS_OK) return s;
+      KL(launch_dot(h->st, h->m, h->kp, h->kq, h->part, h->tickets, h->sc, 1), 1);  // dot_b = p'Mp
+      KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1); // dot_a = rho'z
+      KL(launch_krylov_update(h->st, h->m, h->dy, h->kp, h->dy, +1, h->sc), 1);  // dy += a p
+      ++sweeps;
+      // true residual every step (FP64, matrix-free): keeps the recursion honest
+      if ((s = residual(h, A, h->dy)) != PDAS_OK) return s;
+      if ((s = read_scalars(h)) != PDAS_OK) return s;
+      if ((s = device_status(h)) != PDAS_OK) return s;
+      res = h->sc_host->rho_norm / rn;
+      if (res <= tol) break;
+      if (!(res < 4.0 * best) || !isfinite(res)) break;  // diverging: give up
+      if (res < best) best = res;
+      if ((s = factor_solve(h, h->rho, h->kz)) != PDAS_OK) return s;
+      KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1);
+      KL(launch_krylov_direction(h->st, h->m, h->kz, h->kp, rz, h->sc), 1);
+      if ((s = read_scalars(h)) != PDAS_OK) return s;
+      rz = h->sc_host->dot_a;
+    }
+  }
+  h->last_sweeps = sweeps;
+  h->last_resid = res;
+  // refine_tol is the target; a direction whose residual stalled at the FP64
+  // rounding floor of the matrix-free product is still accepted up to
+  // kRefineAccept (relative to ||A x||_inf).
+  *ok = res <= tol || res <= kRefineAccept;
+  return PDAS_OK;
+}
+
+// One Newton direction at (x, s): fills h->D, h->r, h->dy, h->dx, h->ds.
+pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double* s) {
+  pdas_status st;
+  if ((st = reset_status(h)) != PDAS_OK) return st;
+  STAGE(h, PDAS_STAGE_RHS);
+  KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+  if ((st = gemv(h, A, x, nullptr, h->r, 0)) != PDAS_OK) return st;  // r = A x (a2)
+  STAGE_END(h);
+  if (is_mixed(h) && !h->refactored && h->opt.dspread_refactor > 0) {
+    if ((st = read_scalars(h)) != PDAS_OK) return st;
+    if ((st = device_status(h)) != PDAS_OK) return st;
+    if (h->sc_host->dmax / h->sc_host->dmin > h->opt.dspread_refactor) h->refactored = 1;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    STAGE(h, PDAS_STAGE_NORMAL);
+    if ((st = form_normal(h, A)) != PDAS_OK) return st;
+    STAGE_END(h);
+    STAGE(h, PDAS_STAGE_FACTOR);
+    if ((st = factor(h)) != PDAS_OK) return st;
+    STAGE_END(h);
+    STAGE(h, PDAS_STAGE_SOLVE);
+    if ((st = factor_solve(h, h->r, h->dy)) != PDAS_OK) return st;
+    h->last_fp64 = h->cur_f64;
+    if (h->cur_f64) {
+      STAGE_END(h);
+      h->last_sweeps = 0;
+      h->last_resid = 0.0;
+      STAGE(h, PDAS_STAGE_DIR);
+      if ((st = gemv_t(h, A, h->dy, 1, x, h->dx, h->ds, nullptr)) != PDAS_OK) return st;  // a7
+      STAGE_END(h);
+      return PDAS_OK;
+    }
+    if ((st = read_scalars(h)) != PDAS_OK) return st;
+    st = device_status(h);
+    if (st == PDAS_ERR_NOT_SPD) {  // low-precision factor broke down: FP64 from now on
+      STAGE_END(h);
+      h->refactored = 1;
+      if ((st = reset_status(h)) != PDAS_OK) return st;
+      KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+      if ((st = gemv(h, A, x, nullptr, h->r, 0)) != PDAS_OK) return st;
+      continue;
+    }
+    if (st != PDAS_OK) return st;
+    int ok = 0;
+    if ((st = refine(h, A, &ok)) != PDAS_OK) return st;
+    STAGE_END(h);
+    if (ok) {
+      // w = A' dy of the accepted dy is in h->w: dx = D w - x, ds = -w
+      STAGE(h, PDAS_STAGE_DIR);
+      KL(launch_gemv_t_finish(h->st, h->n, 0, nullptr, 3, x, h->D, h->dx, h->ds, h->w, h->sc), 1);
+      STAGE_END(h);
+      return PDAS_OK;
+    }
+    h->refactored = 1;  // refinement failed: re-form and re-factor in FP64
+  }
+  return PDAS_ERR_NOT_SPD;
+}
+
+pdas_status check_vec_args(const void* A, const double* x, const double* s) {
+  if (!A || !x || !s) return PDAS_ERR_ARG;
+  return PDAS_OK;
+}
+
+void fill_info(pdas_ctx* h, pdas_iter_info* info, bool stepped) {
+  if (!info) return;
+  const Scalars& s = *h->sc_host;
+  memset(info, 0, sizeof(*info));
+  info->dmax = s.dmax;
+  info->dmin = s.dmin;
+  info->refine_sweeps = h->last_sweeps;
+  info->refine_resid = h->last_resid;
+  info->used_fp64 = h->last_fp64;
+  if (stepped) {
+    info->psi = s.psi;
+    info->theta = s.theta;
+    info->rel_gap = s.rel_gap;
+    info->cx = s.cx;
+    info->by = s.by;
+    info->xs = s.xs;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void pdas_default_options(pdas_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->form = PDAS_FP64;
+  opt->a_dtype = PDAS_A_F64;
+  opt->max_iter = 500;
+  opt->refine_tol = 1e-14;
+  opt->refine_max = 10;
+  opt->dspread_refactor = 1e8;
+  opt->stream = nullptr;
+  opt->splits = 0;
+  opt->stall_theta = 1e-12;
+  opt->stall_count = 5;
+}
+
+const char* pdas_status_str(pdas_status st) {
+  switch (st) {
+    case PDAS_OK: return "ok";
+    case PDAS_OPTIMAL: return "optimal (relative gap below tol)";
+    case PDAS_OPTIMAL_EXACT: return "optimal (psi <= 1, full step)";
+    case PDAS_MAX_ITER: return "iteration cap reached";
+    case PDAS_STALLED: return "stalled (step lengths below stall_theta)";
+    case PDAS_ZERO_DIRECTION: return "zero direction";
+    case PDAS_ERR_ARG: return "invalid argument";
+    case PDAS_ERR_NOT_INTERIOR: return "iterate not interior (x > 0 and s > 0 required)";
+    case PDAS_ERR_NOT_SPD: return "normal matrix not positive definite";
+    case PDAS_ERR_NONFINITE: return "non-finite value in direction or ratio test";
+    case PDAS_ERR_TIMEOUT: return "device-side wait timed out";
+    case PDAS_ERR_CUDA: return "CUDA error";
+    case PDAS_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_handle* out) {
+  if (!out) return PDAS_ERR_ARG;
+  *out = nullptr;
+  pdas_options opt;
+  if (opt_in) opt = *opt_in;
+  else pdas_default_options(&opt);
+  if (m < 1 || n <= m || m > (int64_t)1 << 20 || n > (int64_t)1 << 31) return PDAS_ERR_ARG;
+  if (opt.form < PDAS_FP64 || opt.form > PDAS_FP32_IR) return PDAS_ERR_ARG;
+  if (opt.a_dtype < PDAS_A_F64 || opt.a_dtype > PDAS_A_BF16) return PDAS_ERR_ARG;
+  if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || opt.splits < 0 || opt.splits > 3 ||
+      opt.stall_count < 1 || !(opt.stall_theta >= 0))
+    return PDAS_ERR_ARG;
+  if (opt.form == PDAS_BF16_IR && opt.a_dtype != PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
+  if (opt.form == PDAS_TF32_IR && opt.a_dtype == PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
+  pdas_ctx* h = new (std::nothrow) pdas_ctx();
+  if (!h) return PDAS_ERR_CUDA;
+  h->m = m;
+  h->n = n;
+  h->ldm = (m + 15) / 16 * 16;
+  h->opt = opt;
+  h->st = (cudaStream_t)opt.stream;
+  // gemv_t decomposition: row chunks so that ~4 blocks per SM stream A
+  {
+    const int64_t target_chunks = 64;
+    int64_t rows = (m + target_chunks - 1) / target_chunks;
+    if (rows < 16) rows = 16;
+    h->gt_rows = rows;
+    h->gt_chunks = (int)((m + rows - 1) / rows);
+  }
+  const int64_t nblk = (m + kTile - 1) / kTile;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  al((void**)&h->D, sizeof(double) * n);
+  al((void**)&h->dx, sizeof(double) * n);
+  al((void**)&h->ds, sizeof(double) * n);
+  al((void**)&h->w, sizeof(double) * n);
+  al((void**)&h->u, sizeof(double) * n);
+  al((void**)&h->r, sizeof(double) * m);
+  al((void**)&h->dy, sizeof(double) * m);
+  al((void**)&h->z, sizeof(double) * m);
+  al((void**)&h->rho, sizeof(double) * m);
+  al((void**)&h->delta, sizeof(double) * m);
+  al((void**)&h->kp, sizeof(double) * m);
+  al((void**)&h->kq, sizeof(double) * m);
+  al((void**)&h->kz, sizeof(double) * m);
+  al((void**)&h->part, sizeof(double) * kPartMax * 4);
+  al((void**)&h->gt_part, sizeof(double) * n * h->gt_chunks);
+  al((void**)&h->tickets, sizeof(unsigned) * T_COUNT);
+  al((void**)&h->flags, sizeof(int) * (nblk + 1));
+  al((void**)&h->sc, sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->sc_host, sizeof(Scalars));
+  if (e == cudaSuccess) {
+    if (opt.form == PDAS_FP64) al((void**)&h->M64, sizeof(double) * h->ldm * m);
+    else al((void**)&h->M32, sizeof(float) * h->ldm * m);
+  }
+  if (e == cudaSuccess && (opt.form == PDAS_BF16_IR || opt.form == PDAS_TF32_IR)) {
+    e = tc_workspace_create(&h->tc, opt.form, opt.a_dtype, opt.splits, m, n);
+    if (e == cudaErrorNotSupported) {
+      cudaGetLastError();
+      pdas_destroy(h);
+      return PDAS_ERR_UNSUPPORTED;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * T_COUNT, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    pdas_destroy(h);
+    return PDAS_ERR_CUDA;
+  }
+  h->cur_f64 = opt.form == PDAS_FP64;
+  *out = h;
+  return PDAS_OK;
+}
+
+void pdas_destroy(pdas_handle h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  double* vecs[] = {h->D, h->r, h->dy, h->dx, h->ds, h->w, h->u, h->z, h->rho, h->delta, h->kp, h->kq, h->kz,
+                    h->part, h->gt_part, h->M64};
+  for (double* p : vecs)
+    if (p) cudaFree(p);
+  if (h->M32) cudaFree(h->M32);
+  if (h->tickets) cudaFree(h->tickets);
+  if (h->flags) cudaFree(h->flags);
+  if (h->sc) cudaFree(h->sc);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  tc_workspace_destroy(&h->tc);
+  for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
+  delete h;
+}
+
+int64_t pdas_last_error_index(pdas_handle h) { return h ? h->err_index : -1; }
+
+const char* pdas_last_error_message(pdas_handle h) { return h ? h->errmsg : ""; }
+
+pdas_status pdas_profile_enable(pdas_handle h, int enable) {
+  if (!h) return PDAS_ERR_ARG;
+  if (enable) {
+    CK(cudaStreamSynchronize(h->st));
+    h->ev_stage.clear();
+    h->ev_used = 0;
+    h->open_stage = -1;
+    for (int i = 0; i < PDAS_STAGE_COUNT; ++i) {
+      h->prof_ms[i] = 0.0;
+      h->prof_calls[i] = 0;
+    }
+    h->launches = 0;
+  }
+  h->prof = enable != 0;
+  return PDAS_OK;
+}
+
+pdas_status pdas_profile_read(pdas_handle h, pdas_profile* out) {
+  if (!h || !out) return PDAS_ERR_ARG;
+  pdas_status s = prof_fold(h);
+  if (s != PDAS_OK) return s;
+  for (int i = 0; i < PDAS_STAGE_COUNT; ++i) {
+    out->ms[i] = h->prof_ms[i];
+    out->calls[i] = h->prof_calls[i];
+  }
+  out->launches = h->launches;
+  return PDAS_OK;
+}
+
+pdas_status pdas_direction(pdas_handle h, const void* A, const double* x, const double* s, double* dx, double* dy,
+                           double* ds, pdas_iter_info* info) {
+  if (!h || check_vec_args(A, x, s) != PDAS_OK || !dx || !dy || !ds) return PDAS_ERR_ARG;
+  h->err_index = -1;
+  pdas_status st = direction(h, A, x, s);
+  if (st != PDAS_OK) return st;
+  CK(cudaMemcpyAsync(dx, h->dx, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(ds, h->ds, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(dy, h->dy, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  st = device_status(h);
+  fill_info(h, info, false);
+  return st;
+}
+
+pdas_status pdas_step(pdas_handle h, const void* A, const double* b, const double* c, double* x, double* y,
+                      double* s, double alpha, pdas_iter_info* info) {
+  if (!h || check_vec_args(A, x, s) != PDAS_OK || !b || !c || !y) return PDAS_ERR_ARG;
+  if (!(alpha > 0.0 && alpha < 1.0)) return PDAS_ERR_ARG;
+  h->err_index = -1;
+  pdas_status st = direction(h, A, x, s);
+  if (st != PDAS_OK) return st;
+  STAGE(h, PDAS_STAGE_STEP);
+  KL(launch_psi(h->st, h->n, x, s, h->dx, h->ds, alpha, h->part, h->tickets, h->sc), 1);
+  KL(launch_step(h->st, h->m, h->n, b, c, x, y, s, h->dx, h->dy, h->ds, h->part, h->tickets, h->sc), 1);
+  STAGE_END(h);
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  st = device_status(h);
+  fill_info(h, info, st == PDAS_OK);
+  if (st != PDAS_OK) return st;
+  return h->sc_host->psi <= 1.0 ? PDAS_OPTIMAL_EXACT : PDAS_OK;
+}
+
+pdas_status pdas_solve(pdas_handle h, const void* A, const double* b, const double* c, double* x, double* y,
+                       double* s, double alpha, double tol, int* iters_out, double* rel_gap_out) {
+  if (iters_out) *iters_out = 0;
+  if (!h || check_vec_args(A, x, s) != PDAS_OK || !b || !c || !y) return PDAS_ERR_ARG;
+  if (!(alpha > 0.0 && alpha < 1.0) || !(tol > 0.0)) return PDAS_ERR_ARG;
+  h->err_index = -1;
+  h->refactored = 0;
+  // interior check before anything is modified
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  if ((st = device_status(h)) != PDAS_OK) return st;
+  int small = 0, k = 0;
+  pdas_status result = PDAS_MAX_ITER;
+  double gap = INFINITY;
+  for (k = 0; k < h->opt.max_iter; ++k) {
+    pdas_iter_info info;
+    st = pdas_step(h, A, b, c, x, y, s, alpha, &info);
+    if (st < 0) {
+      result = st;
+      break;
+    }
+    gap = info.rel_gap;
+    if (st == PDAS_OPTIMAL_EXACT) {
+      result = st;
+      ++k;
+      break;
+    }
+    if (gap < tol) {
+      result = PDAS_OPTIMAL;
+      ++k;
+      break;
+    }
+    small = info.theta < h->opt.stall_theta ? small + 1 : 0;
+    if (small >= h->opt.stall_count) {
+      result = PDAS_STALLED;
+      ++k;
+      break;
+    }
+  }
+  if (iters_out) *iters_out = k;
+  if (rel_gap_out) *rel_gap_out = gap;
+  return result;
+}
+
+pdas_status pdas_backward(pdas_handle h, const double* dL_dx, double* dL_dA, double* dL_db, double* dL_dc) {
+  (void)h; (void)dL_dx; (void)dL_dA; (void)dL_db; (void)dL_dc;
+  return PDAS_ERR_UNSUPPORTED;
+}
+
+// ---- components ------------------------------------------------------------
+pdas_status pdas_form_normal(pdas_handle h, const void* A, const double* x, const double* s) {
+  if (!h || check_vec_args(A, x, s) != PDAS_OK) return PDAS_ERR_ARG;
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+  if ((st = form_normal(h, A)) != PDAS_OK) return st;
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  return device_status(h);
+}
+
+pdas_status pdas_copy_matrix(pdas_handle h, void* dst, int* dtype_out) {
+  if (!h || !dst) return PDAS_ERR_ARG;
+  const size_t es = h->cur_f64 ? sizeof(double) : sizeof(float);
+  const void* src = h->cur_f64 ? (const void*)h->M64 : (const void*)h->M32;
+  if (!src) return PDAS_ERR_ARG;
+  CK(cudaMemcpy2DAsync(dst, es * h->m, src, es * h->ldm, es * h->m, h->m, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (dtype_out) *dtype_out = h->cur_f64 ? PDAS_A_F64 : PDAS_A_F32;
+  return PDAS_OK;
+}
+
+pdas_status pdas_load_matrix(pdas_handle h, const void* src, int dtype) {
+  if (!h || !src || (dtype != PDAS_A_F64 && dtype != PDAS_A_F32)) return PDAS_ERR_ARG;
+  if (!h->cur_f64 && !h->M32) return PDAS_ERR_ARG;
+  void* dst = h->cur_f64 ? (void*)h->M64 : (void*)h->M32;
+  if (!dst) return PDAS_ERR_ARG;
+  KL(launch_convert_matrix(h->st, h->m, h->m, src, dtype == PDAS_A_F64, h->ldm, dst, h->cur_f64), 1);
+  CK(cudaStreamSynchronize(h->st));
+  return PDAS_OK;
+}
+
+pdas_status pdas_factor(pdas_handle h) {
+  if (!h) return PDAS_ERR_ARG;
+  h->err_index = -1;
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  if ((st = factor(h)) != PDAS_OK) return st;
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  return device_status(h);
+}
+
+pdas_status pdas_factor_solve(pdas_handle h, const double* rhs, double* out) {
+  if (!h || !rhs || !out) return PDAS_ERR_ARG;
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  if ((st = factor_solve(h, rhs, h->delta)) != PDAS_OK) return st;
+  CK(cudaMemcpyAsync(out, h->delta, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  return device_status(h);
+}
+
+pdas_status pdas_gemv(pdas_handle h, const void* A, const double* v, double* out) {
+  if (!h || !A || !v || !out) return PDAS_ERR_ARG;
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  if ((st = gemv(h, A, v, nullptr, out, -1)) != PDAS_OK) return st;
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  return device_status(h);
+}
+
+pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* out) {
+  if (!h || !A || !u || !out) return PDAS_ERR_ARG;
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  if ((st = gemv_t(h, A, u, 0, nullptr, out, nullptr, nullptr)) != PDAS_OK) return st;
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  return device_status(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,371 @@
+// chol.cu -- blocked right-looking Cholesky M = L L' of the normal matrix and
+// the two triangular solves L z = r, L' dy = z: the symmetric positive
+// definite solve of (A D A') dy = A x (Section V-A names Cholesky as the
+// usual route; here it is blocked so the O(m^3) work is a rank-64 update).
+//
+// Per 64-column panel k0:
+//   k_chol_panel  -- every block factors the 64 x 64 diagonal block in shared
+//                    memory; block 0 writes it back, blocks >= 1 each solve 64
+//                    panel rows X L11' = B with four threads per row;
+//   k_chol_update -- trailing lower tiles C -= P P' (the SIMT tile core).
+// A pivot that is not positive (or not finite) sets PDAS_ERR_NOT_SPD with its
+// index in the device status; later launches see the status and do nothing.
+//
+// The triangular solves are one launch each.  Blocks take row blocks in
+// order from a ticket counter; block b waits (bounded, ~2 s) for the flags of
+// the blocks it depends on, so a block only waits on blocks that were handed
+// out earlier and are running or done -- no deadlock.  On a timeout it sets
+// PDAS_ERR_TIMEOUT and returns.
+#include "tile_core.cuh"
+
+namespace pdas {
+
+namespace {
+
+__device__ __forceinline__ bool dev_failed(const Scalars* sc) { return *(volatile const int*)&sc->status != 0; }
+
+template <typename T>
+__device__ __forceinline__ bool pivot_bad(T d) {
+  return !(d > T(0)) || !isfinite(d);
+}
+
+// Factor the kb x kb diagonal block held in shared memory (lower triangle).
+// Returns -1 or the local index of the failing pivot (same in all threads).
+template <typename T>
+__device__ int factor_diag(T (*Ld)[kTile + 1], int kb) {
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = -1;
+  __syncthreads();
+  for (int c = 0; c < kb; ++c) {
+    if (threadIdx.x == 0) {
+      const T d = Ld[c][c];
+      if (pivot_bad(d)) fail = c;
+      else Ld[c][c] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail >= 0) return fail;
+    const T piv = Ld[c][c];
+    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) Ld[r][c] /= piv;
+    __syncthreads();
+    const int w = kb - c - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int i = c + 1 + e / w, j = c + 1 + e % w;
+      if (j <= i) Ld[i][j] -= Ld[i][c] * Ld[j][c];
+    }
+    __syncthreads();
+  }
+  return -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm, T* M, int64_t k0, int kb,
+                                                         Scalars* sc) {
+  __shared__ T Ld[kTile][kTile + 1];
+  if (dev_failed(sc)) return;
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Ld[i][j] = j <= i ? M[(k0 + i) * ldm + k0 + j] : T(0);
+  }
+  __syncthreads();
+  const int fail = factor_diag<T>(Ld, kb);
+  if (fail >= 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && atomicCAS(&sc->status, 0, (int)PDAS_ERR_NOT_SPD) == 0)
+      sc->fail_index = (int)(k0 + fail);
+    return;
+  }
+  if (blockIdx.x == 0) {
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int i = e / kb, j = e % kb;
+      if (j <= i) M[(k0 + i) * ldm + k0 + j] = Ld[i][j];
+    }
+    return;
+  }
+  // Panel rows: X L11' = B, right-looking over columns; thread (row, part)
+  // owns columns part, part+4, ... of its row in registers.
+  const int row = threadIdx.x >> 2, part = threadIdx.x & 3;
+  const int64_t i = k0 + kb + (int64_t)(blockIdx.x - 1) * kTile + row;
+  const bool live = i < m;
+  T b[kTile / 4];
+#pragma unroll
+  for (int k = 0; k < kTile / 4; ++k) {
+    const int c = part + 4 * k;
+    b[k] = (live && c < kb) ? M[i * ldm + k0 + c] : T(0);
+  }
+#pragma unroll
+  for (int c = 0; c < kTile; ++c) {
+    if (c < kb) {
+      const int owner = c & 3;
+      T xc = (part == owner) ? b[c >> 2] / Ld[c][c] : T(0);
+      xc = __shfl_sync(0xffffffffu, xc, (threadIdx.x & 31 & ~3) | owner);
+      if (part == owner) b[c >> 2] = xc;
+#pragma unroll
+      for (int k = 0; k < kTile / 4; ++k) {
+        const int cp = part + 4 * k;
+        if (cp > c && cp < kb) b[k] -= xc * Ld[cp][c];
+      }
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int k = 0; k < kTile / 4; ++k) {
+      const int c = part + 4 * k;
+      if (c < kb) M[i * ldm + k0 + c] = b[k];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_chol_update(int64_t m, int64_t ldm, T* M, int64_t k0, int kb,
+                                                          const Scalars* sc) {
+  __shared__ TileSmem<T, T> sm;
+  if (dev_failed(sc)) return;
+  int64_t ti, tj;
+  lower_tile(blockIdx.x, ti, tj);
+  const int64_t s0 = k0 + kb;
+  const int64_t p0 = s0 + ti * kTile, q0 = s0 + tj * kTile;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  // rows of the panel: P[i][c] = M[i][k0 + c], c < kb
+  tile_rank_k<T, T>(M + k0, ldm, p0, m, M + k0, ldm, q0, m, kb, nullptr, sm, acc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t p = p0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t q = q0 + tx + 16 * j;
+      if (p < m && q <= p) M[p * ldm + q] -= acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Thread 0 waits for flags[j] != 0; the block learns the outcome.
+__device__ bool block_wait(const int* flags, int64_t j, Scalars* sc) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = global_ns();
+    int res = 1;
+    while (ld_acquire(flags + j) == 0) {
+      if (dev_failed(sc)) { res = 0; break; }
+      if (global_ns() - t0 > kWaitLimitNs) {
+        atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+        res = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    ok = res;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// L z = v.  Block row b (64 rows): z_b = L_bb^{-1} (v_b - sum_{j<b} L_bj z_j).
+// Warp w owns rows 8w..8w+7 of the block; lane l owns columns l, l+32.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm, const T* __restrict__ L,
+                                                         const double* __restrict__ v, double* z, int* flags,
+                                                         unsigned* ticket, Scalars* sc) {
+  __shared__ double Ld[kTile][kTile + 1];
+  __shared__ double zj[kTile];
+  __shared__ double acc[kTile];
+  __shared__ int sbi;
+  if (threadIdx.x == 0) sbi = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  if (dev_failed(sc)) return;
+  const int64_t b = sbi;
+  const int64_t r0 = b * kTile;
+  const int rb = (int)(m - r0 < kTile ? m - r0 : kTile);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int i = e / kTile, j = e % kTile;
+    Ld[i][j] = (i < rb && j <= i) ? widen(L[(r0 + i) * ldm + r0 + j]) : 0.0;
+  }
+  double part[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) part[i] = 0.0;
+  for (int64_t jb = 0; jb < b; ++jb) {
+    double l0[8], l1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = 8 * w + i;
+      const T* row = L + (r0 + r) * ldm + jb * kTile;
+      l0[i] = r < rb ? widen(row[lane]) : 0.0;
+      l1[i] = r < rb ? widen(row[lane + 32]) : 0.0;
+    }
+    if (!block_wait(flags, jb, sc)) return;
+    if (threadIdx.x < kTile) zj[threadIdx.x] = __ldcg(z + jb * kTile + threadIdx.x);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) part[i] = fma(l0[i], zj[lane], fma(l1[i], zj[lane + 32], part[i]));
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    double t = part[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const int r = 8 * w + i;
+    if (lane == 0) acc[r] = r < rb ? v[r0 + r] - t : 0.0;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double a0 = acc[lane], a1 = acc[lane + 32];
+    for (int c = 0; c < rb; ++c) {
+      const double own = c < 32 ? a0 : a1;
+      const double zc = __shfl_sync(0xffffffffu, own, c & 31) / Ld[c][c];
+      if (lane == (c & 31)) {
+        if (c < 32) a0 = zc; else a1 = zc;
+      }
+      if (lane > c) a0 -= Ld[lane][c] * zc;
+      if (lane + 32 > c) a1 -= Ld[lane + 32][c] * zc;
+    }
+    if (lane < rb) z[r0 + lane] = a0;
+    if (lane + 32 < rb) z[r0 + lane + 32] = a1;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(flags + b, 1);
+  }
+}
+
+// L' y = z.  Row block b of L' is column block b of L; blocks go from the
+// last to the first.  For each later block kb, thread (w, lane) adds
+// L[k][r] y_k for rows k = 8w..8w+7 of that block and columns r = lane, lane+32.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ldm, const T* __restrict__ L,
+                                                           const double* __restrict__ zin, double* y, int* flags,
+                                                           unsigned* ticket, Scalars* sc) {
+  __shared__ double Ld[kTile][kTile + 1];
+  __shared__ double yk[kTile];
+  __shared__ double red[8][kTile];
+  __shared__ int sbi;
+  const int64_t nblk = (m + kTile - 1) / kTile;
+  if (threadIdx.x == 0) sbi = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  if (dev_failed(sc)) return;
+  const int64_t b = nblk - 1 - sbi;
+  const int64_t r0 = b * kTile;
+  const int rb = (int)(m - r0 < kTile ? m - r0 : kTile);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int i = e / kTile, j = e % kTile;
+    Ld[i][j] = (i < rb && j <= i) ? widen(L[(r0 + i) * ldm + r0 + j]) : 0.0;
+  }
+  double p0 = 0.0, p1 = 0.0;
+  for (int64_t kb = nblk - 1; kb > b; --kb) {
+    const int64_t k0 = kb * kTile;
+    const int kr = (int)(m - k0 < kTile ? m - k0 : kTile);
+    double l0[8], l1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = 8 * w + i;
+      const T* row = L + (k0 + k) * ldm + r0;
+      l0[i] = (k < kr && lane < rb) ? widen(row[lane]) : 0.0;
+      l1[i] = (k < kr && lane + 32 < rb) ? widen(row[lane + 32]) : 0.0;
+    }
+    if (!block_wait(flags, kb, sc)) return;
+    if (threadIdx.x < kTile) yk[threadIdx.x] = threadIdx.x < kr ? __ldcg(y + k0 + threadIdx.x) : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      p0 = fma(l0[i], yk[8 * w + i], p0);
+      p1 = fma(l1[i], yk[8 * w + i], p1);
+    }
+    __syncthreads();
+  }
+  red[w][lane] = p0;
+  red[w][lane + 32] = p1;
+  __syncthreads();
+  if (w == 0) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      a0 += red[i][lane];
+      a1 += red[i][lane + 32];
+    }
+    a0 = lane < rb ? zin[r0 + lane] - a0 : 0.0;
+    a1 = lane + 32 < rb ? zin[r0 + lane + 32] - a1 : 0.0;
+    for (int c = rb - 1; c >= 0; --c) {
+      const double own = c < 32 ? a0 : a1;
+      const double yc = __shfl_sync(0xffffffffu, own, c & 31) / Ld[c][c];
+      if (lane == (c & 31)) {
+        if (c < 32) a0 = yc; else a1 = yc;
+      }
+      if (lane < c) a0 -= Ld[c][lane] * yc;
+      if (lane + 32 < c) a1 -= Ld[c][lane + 32] * yc;
+    }
+    if (lane < rb) y[r0 + lane] = a0;
+    if (lane + 32 < rb) y[r0 + lane + 32] = a1;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(flags + b, 1);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, Scalars* sc) {
+  for (int64_t k0 = 0; k0 < m; k0 += kTile) {
+    const int kb = (int)(m - k0 < kTile ? m - k0 : kTile);
+    const int64_t rest = m - k0 - kb;
+    const int64_t t = (rest + kTile - 1) / kTile;
+    k_chol_panel<T><<<(unsigned)(1 + t), kThreads, 0, st>>>(m, ldm, M, k0, kb, sc);
+    if (t > 0) k_chol_update<T><<<(unsigned)(t * (t + 1) / 2), kThreads, 0, st>>>(m, ldm, M, k0, kb, sc);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* v, double* z, int* flags,
+                       unsigned* tickets, Scalars* sc) {
+  const int64_t nblk = (m + kTile - 1) / kTile;
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tickets + T_TRSV, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_trsv_lower<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, v, z, flags, tickets + T_TRSV, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* z, double* y,
+                         int* flags, unsigned* tickets, Scalars* sc) {
+  const int64_t nblk = (m + kTile - 1) / kTile;
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tickets + T_TRSV, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_trsv_upper_t<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, z, y, flags, tickets + T_TRSV, sc);
+  return cudaGetLastError();
+}
+
+template cudaError_t cholesky<double>(cudaStream_t, int64_t, int64_t, double*, Scalars*);
+template cudaError_t cholesky<float>(cudaStream_t, int64_t, int64_t, float*, Scalars*);
+template cudaError_t trsv_lower<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, double*, int*,
+                                        unsigned*, Scalars*);
+template cudaError_t trsv_lower<float>(cudaStream_t, int64_t, int64_t, const float*, const double*, double*, int*,
+                                       unsigned*, Scalars*);
+template cudaError_t trsv_upper_t<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, double*,
+                                          int*, unsigned*, Scalars*);
+template cudaError_t trsv_upper_t<float>(cudaStream_t, int64_t, int64_t, const float*, const double*, double*, int*,
+                                         unsigned*, Scalars*);
+
+}  // namespace pdas

@@ -1,0 +1,100 @@
+// pdas_internal.cuh -- shared declarations of the libpdas CUDA sources.
+//
+// Layout in HBM (all row-major, all resident for the life of a handle):
+//   A       m x n, caller-owned, in its storage dtype (f64 / f32 / bf16);
+//   M, L    m x m with leading dimension ldm = round_up(m, 16), lower
+//           triangle only; L overwrites M in place;
+//   vectors D, r, dy, w, ... in FP64.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdas.h"
+#include "pdas_components.h"
+
+namespace pdas {
+
+constexpr int kThreads = 256;   // threads of every elementwise / reduction kernel
+constexpr int kTile = 64;       // SIMT SYRK / Cholesky tile edge
+constexpr int kPartMax = 65536;  // capacity of the reduction-partials buffer (blocks)
+
+// Scalars written by the device reductions; the host reads the whole struct
+// once per iteration.
+struct Scalars {
+  double dmax, dmin;   // max, min of D = x/s
+  double psi, theta;   // ratio test and step length
+  double cx, by, xs;   // c'x, b'y, x's after the step
+  double rel_gap;      // (c'x - b'y)/(1+|c'x|)
+  double rnorm;        // ||A x||_inf
+  double rho_norm;     // ||A x - M dy||_inf of the latest residual
+  double dot_a, dot_b; // dot products of the refinement Krylov steps
+  int status;          // 0, or a pdas_status error detected on the device
+  int fail_index;      // failing pivot for PDAS_ERR_NOT_SPD
+  int bad_iterate;     // nonzero if some x_j <= 0 or s_j <= 0 (or not finite)
+  int pad;
+};
+
+// Counters for the "last block finishes the reduction" pattern and the
+// triangular-solve tickets.
+enum Ticket { T_SCALING = 0, T_PSI, T_STEP, T_NORM, T_NORM2, T_DOT, T_TRSV, T_COUNT = 8 };
+
+// ---- exact widening of the stored A ---------------------------------------
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return (double)v; }
+__device__ __forceinline__ double widen(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ float widen32(double v) { return (float)v; }
+__device__ __forceinline__ float widen32(float v) { return v; }
+__device__ __forceinline__ float widen32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---- launch helpers (host) ------------------------------------------------
+// Each returns cudaGetLastError() of its launch.
+template <typename T>
+cudaError_t launch_gemv(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* v, const double* base,
+                        double* out, double* part, unsigned* tickets, Scalars* sc, int norm_slot);
+template <typename T>
+cudaError_t launch_gemv_t(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* u, double* part,
+                          int chunks, int64_t rows_per_chunk);
+// w = sum of the gemv_t partials; then per mode:
+//   0: out0 = w
+//   1: direction: out0 = dx = D w - x, out1 = ds = -w, out2 = w (may be null)
+//   2: scaled:    out0 = D w, out2 = w (may be null)
+//   3: direction from a w already in out2 (chunks, part unused)
+cudaError_t launch_gemv_t_finish(cudaStream_t st, int64_t n, int chunks, const double* part, int mode,
+                                 const double* x, const double* D, double* out0, double* out1, double* out2,
+                                 const Scalars* sc);
+cudaError_t launch_scaling(cudaStream_t st, int64_t n, const double* x, const double* s, double* D, double* part,
+                           unsigned* tickets, Scalars* sc);
+cudaError_t launch_psi(cudaStream_t st, int64_t n, const double* x, const double* s, const double* dx,
+                       const double* ds, double alpha, double* part, unsigned* tickets, Scalars* sc);
+cudaError_t launch_step(cudaStream_t st, int64_t m, int64_t n, const double* b, const double* c, double* x,
+                        double* y, double* s, const double* dx, const double* dy, const double* ds, double* part,
+                        unsigned* tickets, Scalars* sc);
+cudaError_t launch_axpy(cudaStream_t st, int64_t n, double a, const double* xv, double* yv, const Scalars* sc);
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const double* a, const double* b, double* part,
+                       unsigned* tickets, Scalars* sc, int slot);
+// x-update of one Krylov step: out = base + coef * p where coef = sc->dot_a / sc->dot_b
+// (sign < 0 subtracts); see the refinement driver.
+cudaError_t launch_krylov_update(cudaStream_t st, int64_t n, const double* base, const double* p, double* out,
+                                 int sign, const Scalars* sc);
+cudaError_t launch_krylov_direction(cudaStream_t st, int64_t n, const double* z, double* p, double beta_num,
+                                    const Scalars* sc);
+
+template <typename T>
+cudaError_t launch_syrk_simt(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, double* M64,
+                             float* M32, int64_t ldm, const Scalars* sc);
+
+template <typename T>
+cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, Scalars* sc);
+template <typename T>
+cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* v, double* z,
+                       int* flags, unsigned* tickets, Scalars* sc);
+template <typename T>
+cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* z, double* y,
+                         int* flags, unsigned* tickets, Scalars* sc);
+
+cudaError_t launch_convert_matrix(cudaStream_t st, int64_t m, int64_t ld_src, const void* src, int src_f64,
+                                  int64_t ld_dst, void* dst, int dst_f64);
+
+}  // namespace pdas

@@ -1,0 +1,513 @@
+// vec_kernels.cu -- the bandwidth-bound steps of one PDAS iteration:
+//   scaling D = S^{-1} X (Eq. 4), the right-hand side r = A x and the
+//   refinement residual r - A(D(A' dy)) (Section V), the direction
+//   ds = -A' dy, dx = D(-ds) - x (Section V), the psi ratio test and the step
+//   (algorithm of Section III).
+//
+// All sums are deterministic: every thread accumulates a fixed strided slice,
+// blocks reduce with a fixed shuffle tree, and the last block to finish
+// (ticket counter, no float atomics) combines the per-block partials in block
+// order.  The grid of each reduction depends on the sizes only, so results
+// are bit-identical from run to run.
+#include "pdas_internal.cuh"
+
+namespace pdas {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// op: 0 sum, 1 max, 2 min.  Result valid in thread 0.
+template <int OP>
+__device__ double block_reduce(double v, double* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = OP == 0 ? warp_sum(v) : OP == 1 ? warp_max(v) : warp_min(v);
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  double t = OP == 0 ? 0.0 : OP == 1 ? -INFINITY : INFINITY;
+  if (w == 0) {
+    if (lane < nw) t = sm[lane];
+    t = OP == 0 ? warp_sum(t) : OP == 1 ? warp_max(t) : warp_min(t);
+  }
+  return t;
+}
+
+// True in every thread of the block that finishes last.  Partials written
+// before the call are visible to that block.
+__device__ bool last_block(unsigned* ticket) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  return last;
+}
+
+// Combine nparts partials in index order by one block (fixed order).
+template <int OP>
+__device__ double combine(const double* part, int nparts, double* sm) {
+  double v = OP == 0 ? 0.0 : OP == 1 ? -INFINITY : INFINITY;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    double p = __ldcg(part + i);
+    v = OP == 0 ? v + p : OP == 1 ? fmax(v, p) : fmin(v, p);
+  }
+  return block_reduce<OP>(v, sm);
+}
+
+__device__ __forceinline__ bool failed(const Scalars* sc) { return *(volatile const int*)&sc->status != 0; }
+
+int grid_for(int64_t n, int per_thread = 1) {
+  int64_t g = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+  if (g < 1) g = 1;
+  if (g > 1184) g = 1184;  // 8 blocks per SM on 148+ SMs; strided loops cover the rest
+  return (int)g;
+}
+
+// ---- vector loads of VEC consecutive elements of A, widened to double ----
+template <typename T>
+struct Vec;
+template <>
+struct Vec<double> {
+  static constexpr int N = 2;
+  __device__ static void load(const double* p, double* o) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <>
+struct Vec<float> {
+  static constexpr int N = 4;
+  __device__ static void load(const float* p, double* o) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct Vec<__nv_bfloat16> {
+  static constexpr int N = 8;
+  __device__ static void load(const __nv_bfloat16* p, double* o) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[2 * i] = (double)__uint_as_float(w[i] << 16);
+      o[2 * i + 1] = (double)__uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// a1: D = x/s, with max/min of D and the interior check.
+__global__ void __launch_bounds__(kThreads) k_scaling(int64_t n, const double* __restrict__ x,
+                                                      const double* __restrict__ s, double* __restrict__ D,
+                                                      double* part, unsigned* tickets, Scalars* sc) {
+  __shared__ double sm[32];
+  double mx = -INFINITY, mn = INFINITY;
+  int bad = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double xj = x[j], sj = s[j];
+    if (!(xj > 0.0) || !(sj > 0.0) || !isfinite(xj) || !isfinite(sj)) bad = 1;
+    const double d = xj / sj;
+    D[j] = d;
+    mx = fmax(mx, d);
+    mn = fmin(mn, d);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->bad_iterate, 1);
+  double bmx = block_reduce<1>(mx, sm);
+  double bmn = block_reduce<2>(mn, sm);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = bmx;
+    part[2 * blockIdx.x + 1] = bmn;
+  }
+  if (!last_block(tickets + T_SCALING)) return;
+  double gmx = -INFINITY, gmn = INFINITY;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    gmx = fmax(gmx, __ldcg(part + 2 * i));
+    gmn = fmin(gmn, __ldcg(part + 2 * i + 1));
+  }
+  gmx = block_reduce<1>(gmx, sm);
+  gmn = block_reduce<2>(gmn, sm);
+  if (threadIdx.x == 0) {
+    sc->dmax = gmx;
+    sc->dmin = gmn;
+    if (sc->bad_iterate && sc->status == 0) sc->status = PDAS_ERR_NOT_INTERIOR;
+    tickets[T_SCALING] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2 / a6: out_p = A_p. v  (base == null)  or  out_p = base_p - A_p. v.
+// ROWS rows per block; FP64 accumulation of exactly widened A.  With
+// norm_slot >= 0 also reduces max_p |out_p| into sc->rnorm (slot 0) or
+// sc->rho_norm (slot 1).
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(kThreads) k_gemv(int64_t m, int64_t n, const T* __restrict__ A,
+                                                   const double* __restrict__ v, const double* __restrict__ base,
+                                                   double* __restrict__ out, int vec_ok, double* part,
+                                                   unsigned* tickets, Scalars* sc, int norm_slot) {
+  __shared__ double sm[32];
+  __shared__ double rowsum[ROWS];
+  if (failed(sc)) return;
+  constexpr int VN = Vec<T>::N;
+  const int64_t p0 = (int64_t)blockIdx.x * ROWS;
+  double acc[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) acc[r] = 0.0;
+  if (vec_ok) {
+    for (int64_t j = (int64_t)threadIdx.x * VN; j < n; j += (int64_t)blockDim.x * VN) {
+      double vv[VN];
+#pragma unroll
+      for (int k = 0; k < VN; ++k) vv[k] = __ldg(v + j + k);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        if (p0 + r < m) {
+          double a[VN];
+          Vec<T>::load(A + (p0 + r) * n + j, a);
+#pragma unroll
+          for (int k = 0; k < VN; ++k) acc[r] = fma(a[k], vv[k], acc[r]);
+        }
+      }
+    }
+  } else {
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double vj = __ldg(v + j);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+        if (p0 + r < m) acc[r] = fma(widen(A[(p0 + r) * n + j]), vj, acc[r]);
+    }
+  }
+  double amax = 0.0;
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    double t = block_reduce<0>(acc[r], sm);
+    if (threadIdx.x == 0) rowsum[r] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < ROWS && p0 + threadIdx.x < m) {
+    const int64_t p = p0 + threadIdx.x;
+    const double o = base ? base[p] - rowsum[threadIdx.x] : rowsum[threadIdx.x];
+    out[p] = o;
+    amax = fabs(o);
+    if (!isfinite(o)) amax = INFINITY;
+  }
+  if (norm_slot < 0) return;
+  double bm = block_reduce<1>(amax, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = bm;
+  if (!last_block(tickets + T_NORM)) return;
+  double g = combine<1>(part, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    if (norm_slot == 0) sc->rnorm = g; else sc->rho_norm = g;
+    tickets[T_NORM] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7 (first half): partial column sums part[c][j] = sum_{p in chunk c} A_pj u_p.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gemv_t_part(int64_t m, int64_t n, const T* __restrict__ A,
+                                                          const double* __restrict__ u, double* __restrict__ part,
+                                                          int64_t rows_per_chunk, int vec_ok) {
+  constexpr int VN = Vec<T>::N;
+  const int64_t pbeg = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t pend = pbeg + rows_per_chunk < m ? pbeg + rows_per_chunk : m;
+  double* dst = part + (int64_t)blockIdx.y * n;
+  if (vec_ok) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN;
+    if (j >= n) return;
+    double acc[VN];
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = 0.0;
+    for (int64_t p = pbeg; p < pend; ++p) {
+      double a[VN];
+      Vec<T>::load(A + p * n + j, a);
+      const double up = __ldg(u + p);
+#pragma unroll
+      for (int k = 0; k < VN; ++k) acc[k] = fma(a[k], up, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < VN; ++k) dst[j + k] = acc[k];
+  } else {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double acc = 0.0;
+    for (int64_t p = pbeg; p < pend; ++p) acc = fma(widen(A[p * n + j]), __ldg(u + p), acc);
+    dst[j] = acc;
+  }
+}
+
+// a7 (second half): w_j = sum_c part[c][j] in chunk order, then the mode's
+// elementwise outputs.
+__global__ void __launch_bounds__(kThreads) k_gemv_t_finish(int64_t n, int chunks, const double* __restrict__ part,
+                                                            int mode, const double* __restrict__ x,
+                                                            const double* __restrict__ D, double* out0,
+                                                            double* out1, double* out2, const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double w = 0.0;
+    if (mode == 3) w = out2[j];
+    else
+      for (int c = 0; c < chunks; ++c) w += __ldcg(part + (int64_t)c * n + j);
+    if (mode == 0) {
+      out0[j] = w;
+    } else if (mode == 1 || mode == 3) {
+      const double ds = -w;
+      out0[j] = D[j] * (-ds) - x[j];  // dx = D(-ds) - x
+      out1[j] = ds;
+      if (out2 && mode == 1) out2[j] = w;
+    } else {
+      out0[j] = D[j] * w;
+      if (out2) out2[j] = w;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a8: psi = max_j max(-dx_j/x_j, -ds_j/s_j); theta = alpha/psi, or 1 if psi <= 1.
+__global__ void __launch_bounds__(kThreads) k_psi(int64_t n, const double* __restrict__ x,
+                                                  const double* __restrict__ s, const double* __restrict__ dx,
+                                                  const double* __restrict__ ds, double alpha, double* part,
+                                                  unsigned* tickets, Scalars* sc) {
+  __shared__ double sm[32];
+  if (failed(sc)) return;
+  double mx = -INFINITY;
+  int bad = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double u = -dx[j] / x[j];
+    const double v = -ds[j] / s[j];
+    if (!isfinite(u) || !isfinite(v)) bad = 1;
+    mx = fmax(mx, fmax(u, v));
+  }
+  bad = __syncthreads_or(bad);
+  double bm = block_reduce<1>(mx, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = bad ? NAN : bm;
+  if (!last_block(tickets + T_PSI)) return;
+  double g = -INFINITY;
+  int gbad = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    const double p = __ldcg(part + i);
+    if (p != p) gbad = 1;
+    g = fmax(g, p);
+  }
+  gbad = __syncthreads_or(gbad);
+  g = block_reduce<1>(g, sm);
+  if (threadIdx.x == 0) {
+    sc->psi = g;
+    sc->theta = g <= 1.0 ? 1.0 : alpha / g;
+    if (gbad) sc->status = PDAS_ERR_NONFINITE;
+    tickets[T_PSI] = 0;
+  }
+}
+
+// a9: (x,y,s) += theta (dx,dy,ds); then c'x, b'y, x's and the relative gap.
+__global__ void __launch_bounds__(kThreads) k_step(int64_t m, int64_t n, const double* __restrict__ b,
+                                                   const double* __restrict__ c, double* x, double* y, double* s,
+                                                   const double* __restrict__ dx, const double* __restrict__ dy,
+                                                   const double* __restrict__ ds, double* part, unsigned* tickets,
+                                                   Scalars* sc) {
+  __shared__ double sm[32];
+  if (failed(sc)) return;
+  const double th = sc->theta;
+  double cx = 0.0, by = 0.0, xs = 0.0;
+  const int64_t len = n > m ? n : m;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    if (j < n) {
+      const double xn = x[j] + th * dx[j];
+      const double sn = s[j] + th * ds[j];
+      x[j] = xn;
+      s[j] = sn;
+      cx = fma(c[j], xn, cx);
+      xs = fma(xn, sn, xs);
+    }
+    if (j < m) {
+      const double yn = y[j] + th * dy[j];
+      y[j] = yn;
+      by = fma(b[j], yn, by);
+    }
+  }
+  cx = block_reduce<0>(cx, sm);
+  by = block_reduce<0>(by, sm);
+  xs = block_reduce<0>(xs, sm);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = cx;
+    part[3 * blockIdx.x + 1] = by;
+    part[3 * blockIdx.x + 2] = xs;
+  }
+  if (!last_block(tickets + T_STEP)) return;
+  double gc = 0.0, gb = 0.0, gx = 0.0;
+  // one thread combines in block order: the partial count is small
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)gridDim.x; ++i) {
+      gc += __ldcg(part + 3 * i);
+      gb += __ldcg(part + 3 * i + 1);
+      gx += __ldcg(part + 3 * i + 2);
+    }
+    sc->cx = gc;
+    sc->by = gb;
+    sc->xs = gx;
+    sc->rel_gap = (gc - gb) / (1.0 + fabs(gc));
+    tickets[T_STEP] = 0;
+  }
+}
+
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ xv, double* yv, const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    yv[j] += a * xv[j];
+}
+
+// dot product into sc->dot_a (slot 0) or sc->dot_b (slot 1); fixed order.
+__global__ void __launch_bounds__(kThreads) k_dot(int64_t n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, double* part, unsigned* tickets,
+                                                  Scalars* sc, int slot) {
+  __shared__ double sm[32];
+  if (failed(sc)) return;
+  double acc = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(a[j], b[j], acc);
+  acc = block_reduce<0>(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (!last_block(tickets + T_DOT)) return;
+  if (threadIdx.x == 0) {
+    double g = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) g += __ldcg(part + i);
+    if (slot == 0) sc->dot_a = g; else sc->dot_b = g;
+    tickets[T_DOT] = 0;
+  }
+}
+
+__global__ void k_krylov_update(int64_t n, const double* base, const double* __restrict__ p, double* out, int sign,
+                                const Scalars* sc) {
+  if (failed(sc)) return;
+  const double coef = sc->dot_a / sc->dot_b;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = sign > 0 ? base[j] + coef * p[j] : base[j] - coef * p[j];
+}
+
+// p = z + (dot_a / beta_num) p
+__global__ void k_krylov_direction(int64_t n, const double* __restrict__ z, double* p, double beta_den,
+                                   const Scalars* sc) {
+  if (failed(sc)) return;
+  const double beta = sc->dot_a / beta_den;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    p[j] = z[j] + beta * p[j];
+}
+
+__global__ void k_convert_matrix(int64_t m, int64_t ld_src, const void* src, int src_f64, int64_t ld_dst, void* dst,
+                                 int dst_f64) {
+  for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+      const double v = src_f64 ? ((const double*)src)[i * ld_src + j] : (double)((const float*)src)[i * ld_src + j];
+      if (dst_f64) ((double*)dst)[i * ld_dst + j] = v;
+      else ((float*)dst)[i * ld_dst + j] = (float)v;
+    }
+}
+
+template <typename T>
+bool vec_aligned(const T* A, int64_t n) {
+  return ((uintptr_t)A % 16 == 0) && ((n * (int64_t)sizeof(T)) % 16 == 0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_gemv(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* v, const double* base,
+                        double* out, double* part, unsigned* tickets, Scalars* sc, int norm_slot) {
+  constexpr int ROWS = 4;
+  const int64_t grid = (m + ROWS - 1) / ROWS;
+  if (norm_slot >= 0 && grid > kPartMax) return cudaErrorInvalidConfiguration;
+  k_gemv<T, ROWS><<<(unsigned)grid, kThreads, 0, st>>>(m, n, A, v, base, out, vec_aligned(A, n) ? 1 : 0, part,
+                                                         tickets, sc, norm_slot);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gemv_t(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* u, double* part,
+                          int chunks, int64_t rows_per_chunk) {
+  const bool vok = vec_aligned(A, n);
+  const int64_t cols_per_block = (int64_t)kThreads * (vok ? Vec<T>::N : 1);
+  dim3 grid((unsigned)((n + cols_per_block - 1) / cols_per_block), (unsigned)chunks);
+  k_gemv_t_part<T><<<grid, kThreads, 0, st>>>(m, n, A, u, part, rows_per_chunk, vok ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_t_finish(cudaStream_t st, int64_t n, int chunks, const double* part, int mode,
+                                 const double* x, const double* D, double* out0, double* out1, double* out2,
+                                 const Scalars* sc) {
+  k_gemv_t_finish<<<grid_for(n), kThreads, 0, st>>>(n, chunks, part, mode, x, D, out0, out1, out2, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scaling(cudaStream_t st, int64_t n, const double* x, const double* s, double* D, double* part,
+                           unsigned* tickets, Scalars* sc) {
+  const int g = grid_for(n, 4);
+  k_scaling<<<g, kThreads, 0, st>>>(n, x, s, D, part, tickets, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi(cudaStream_t st, int64_t n, const double* x, const double* s, const double* dx,
+                       const double* ds, double alpha, double* part, unsigned* tickets, Scalars* sc) {
+  k_psi<<<grid_for(n, 4), kThreads, 0, st>>>(n, x, s, dx, ds, alpha, part, tickets, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(cudaStream_t st, int64_t m, int64_t n, const double* b, const double* c, double* x,
+                        double* y, double* s, const double* dx, const double* dy, const double* ds, double* part,
+                        unsigned* tickets, Scalars* sc) {
+  k_step<<<grid_for(n > m ? n : m, 4), kThreads, 0, st>>>(m, n, b, c, x, y, s, dx, dy, ds, part, tickets, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(cudaStream_t st, int64_t n, double a, const double* xv, double* yv, const Scalars* sc) {
+  k_axpy<<<grid_for(n), kThreads, 0, st>>>(n, a, xv, yv, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const double* a, const double* b, double* part,
+                       unsigned* tickets, Scalars* sc, int slot) {
+  k_dot<<<grid_for(n, 4), kThreads, 0, st>>>(n, a, b, part, tickets, sc, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_krylov_update(cudaStream_t st, int64_t n, const double* base, const double* p, double* out,
+                                 int sign, const Scalars* sc) {
+  k_krylov_update<<<grid_for(n), kThreads, 0, st>>>(n, base, p, out, sign, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_krylov_direction(cudaStream_t st, int64_t n, const double* z, double* p, double beta_den,
+                                    const Scalars* sc) {
+  k_krylov_direction<<<grid_for(n), kThreads, 0, st>>>(n, z, p, beta_den, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_matrix(cudaStream_t st, int64_t m, int64_t ld_src, const void* src, int src_f64,
+                                  int64_t ld_dst, void* dst, int dst_f64) {
+  dim3 grid((unsigned)((m + kThreads - 1) / kThreads), (unsigned)(m < 4096 ? m : 4096));
+  k_convert_matrix<<<grid, kThreads, 0, st>>>(m, ld_src, src, src_f64, ld_dst, dst, dst_f64);
+  return cudaGetLastError();
+}
+
+#define PDAS_INST(T)                                                                                          \
+  template cudaError_t launch_gemv<T>(cudaStream_t, int64_t, int64_t, const T*, const double*, const double*, \
+                                      double*, double*, unsigned*, Scalars*, int);                            \
+  template cudaError_t launch_gemv_t<T>(cudaStream_t, int64_t, int64_t, const T*, const double*, double*, int, \
+                                        int64_t);
+PDAS_INST(double)
+PDAS_INST(float)
+PDAS_INST(__nv_bfloat16)
+#undef PDAS_INST
+
+}  // namespace pdas

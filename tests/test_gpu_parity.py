@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances come from the arithmetic:
+  * a dot product of length n summed in two different orders in FP64 differs
+    by at most 2 gamma_n sum|terms|, gamma_n = n u / (1 - n u), u = 2^-53
+    (FP32: u = 2^-24) -- used elementwise for A v, A' u and M = A D A';
+  * Cholesky factors and triangular solves of well-conditioned matrices agree
+    to ~cond * u; 1e-11 relative leaves room on the test matrices;
+  * whole iterates: the normwise 1e-9 relative agreement that the FP64 form
+    must keep with the oracle at every iteration, and the optimal objective
+    to 1e-8 relative for every form.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+def gamma(n, u):
+    return n * u / (1 - n * u)
+
+
+@pytest.fixture(scope="module")
+def pdas():
+    from paper_1502_03543_gb300 import build as B
+    B.build()
+    import paper_1502_03543_gb300 as P
+    assert torch.cuda.is_available()
+    return P
+
+
+TORCH_DT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+
+def dev_A(lp):
+    if lp.storage == "bf16":
+        return torch.from_numpy(lp.A_store.view(np.int16).copy()).view(torch.bfloat16).cuda()
+    return torch.from_numpy(np.ascontiguousarray(lp.A_store)).cuda()
+
+
+def dv(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+SHAPES = [(1, 2), (5, 37), (64, 128), (130, 520), (67, 301)]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_gemv_and_gemv_t(pdas, storage, m, n):
+    lp = lpgen.generate(m, n, seed=m + n, storage=storage, scaled=storage == "bf16")
+    A = dev_A(lp)
+    rng = np.random.default_rng(1)
+    v, u = rng.standard_normal(n), rng.standard_normal(m)
+    with pdas.Solver(m, n, "fp64", TORCH_DT[storage]) as S:
+        r = host(S.gemv(A, dv(v)))
+        w = host(S.gemv_t(A, dv(u)))
+    ref_r, ref_w = oracle.gemv(lp.A64, v), oracle.gemv_t(lp.A64, u)
+    bound_r = 2 * gamma(n, U64) * (np.abs(lp.A64) @ np.abs(v))
+    bound_w = 2 * gamma(m, U64) * (np.abs(lp.A64).T @ np.abs(u))
+    assert np.all(np.abs(r - ref_r) <= bound_r + 1e-300)
+    assert np.all(np.abs(w - ref_w) <= bound_w + 1e-300)
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_normal_matrix_fp64(pdas, storage, m, n):
+    lp = lpgen.generate(m, n, seed=7 * m + n, storage=storage, scaled=storage == "bf16")
+    rng = np.random.default_rng(2)
+    x, s = rng.uniform(0.01, 10, n), rng.uniform(0.01, 10, n)
+    with pdas.Solver(m, n, "fp64", TORCH_DT[storage]) as S:
+        S.form_normal(dev_A(lp), dv(x), dv(s))
+        M = host(S.copy_matrix())
+    D = oracle.scaling(x, s)
+    ref = oracle.normal_matrix(lp.A64, D)
+    bound = 2 * gamma(n + 2, U64) * ((np.abs(lp.A64) * D) @ np.abs(lp.A64).T)
+    low = np.tril_indices(m)
+    assert np.all(np.abs(M[low] - ref[low]) <= bound[low])
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_normal_matrix_fp32_simt(pdas, m, n):
+    lp = lpgen.generate(m, n, seed=3 * m + n, storage="f32")
+    rng = np.random.default_rng(3)
+    x, s = rng.uniform(0.1, 10, n), rng.uniform(0.1, 10, n)
+    with pdas.Solver(m, n, "fp32_ir", torch.float32) as S:
+        S.form_normal(dev_A(lp), dv(x), dv(s))
+        M = host(S.copy_matrix()).astype(np.float64)
+    D = oracle.scaling(x, s)
+    ref = oracle.normal_matrix(lp.A64, D)
+    # operands rounded to FP32 (A D and A exact), products and sums in FP32
+    bound = 2 * gamma(n + 3, U32) * ((np.abs(lp.A64) * D) @ np.abs(lp.A64).T)
+    low = np.tril_indices(m)
+    assert np.all(np.abs(M[low] - ref[low]) <= bound[low])
+
+
+def spd_matrix(m, seed):
+    lp = lpgen.generate(m, 3 * m + 1, seed=seed)
+    D = oracle.scaling(lp.x0, lp.s0)
+    return oracle.normal_matrix(lp.A64, D)
+
+
+@pytest.mark.parametrize("m", [1, 7, 64, 65, 200])
+def test_cholesky_and_solves_fp64(pdas, m):
+    M = spd_matrix(m, seed=m)
+    Lo, fail = oracle.cholesky(M)
+    assert fail == -1
+    with pdas.Solver(m, m + 1, "fp64") as S:
+        S.load_matrix(dv(M))
+        S.factor()
+        L = np.tril(host(S.copy_matrix()))
+        rhs = np.random.default_rng(4).standard_normal(m)
+        x = host(S.factor_solve(dv(rhs)))
+    assert np.linalg.norm(L - Lo) <= 1e-11 * np.linalg.norm(Lo)
+    # the triangular solves against the oracle's substitutions on the GPU's factor
+    xo = oracle.backward(L, oracle.forward(L, rhs))
+    assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("m", [7, 65, 200])
+def test_cholesky_fp32(pdas, m):
+    M = spd_matrix(m, seed=100 + m)
+    Lo, _ = oracle.cholesky(M)
+    with pdas.Solver(m, m + 1, "fp32_ir", torch.float32) as S:
+        S.load_matrix(dv(M))
+        S.factor()
+        L = np.tril(host(S.copy_matrix()).astype(np.float64))
+        rhs = np.random.default_rng(5).standard_normal(m)
+        x = host(S.factor_solve(dv(rhs)))
+    # FP32 factor of a well-conditioned matrix: backward error ~ m u32
+    assert np.abs(L @ L.T - M).max() <= 4 * m * U32 * np.abs(M).max()
+    xo = oracle.backward(L, oracle.forward(L, rhs))
+    assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("form,dt", [("fp64", torch.float64), ("fp32_ir", torch.float32)])
+def test_not_spd_reports_pivot(pdas, form, dt):
+    m = 150
+    M = np.eye(m)
+    M[97, 97] = -1.0
+    with pdas.Solver(m, m + 1, form, dt) as S:
+        S.load_matrix(dv(M).to(dt))
+        st = S.factor(raise_on_error=False)
+        assert st == -3 and S.last_error_index() == 97
+
+
+def test_direction_matches_oracle(pdas):
+    lp = lpgen.workload("dense_64x128_f64", 0)
+    res = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, keep_iterates=True)
+    n, m = lp.n, lp.m
+    pts = [(lp.x0, lp.s0)] + [(r[:n], r[n + m:]) for r in res["iterates"][:-1]]
+    with pdas.Solver(m, n, "fp64") as S:
+        A = dev_A(lp)
+        for k in (0, 1, 5, 10, len(pts) - 1):
+            x, s = pts[k]
+            d = oracle.direction(lp.A64, x, s)
+            dx, dy, ds, _ = S.direction(A, dv(x), dv(s))
+            for g, o in ((host(dx), d["dx"]), (host(dy), d["dy"]), (host(ds), d["ds"])):
+                assert np.linalg.norm(g - o) <= 1e-9 * np.linalg.norm(o), k
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fp64_iterates_match_oracle_every_iteration(pdas, seed):
+    lp = lpgen.workload("dense_64x128_f64", seed)
+    ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, keep_iterates=True)
+    n, m = lp.n, lp.m
+    A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    worst = 0.0
+    with pdas.Solver(m, n, "fp64") as S:
+        for k in range(ref["iters"]):
+            st, info = S.step(A, b, c, x, y, s, alpha=0.95)
+            it = ref["iterates"][k]
+            for g, o in ((x, it[:n]), (y, it[n:n + m]), (s, it[n + m:])):
+                err = np.linalg.norm(host(g) - o) / np.linalg.norm(o)
+                worst = max(worst, err)
+                assert err <= 1e-9, (k, err)
+            assert abs(info["psi"] - ref["trace"][k, 0]) <= 1e-9 * abs(ref["trace"][k, 0])
+        assert info["rel_gap"] < 1e-8  # same stop iteration as the oracle
+        prev_gap = ref["trace"][ref["iters"] - 2, 2]
+        assert prev_gap >= 1e-8
+    obj, obj_ref = float(lp.c @ host(x)), float(lp.c @ ref["x"])
+    assert abs(obj - obj_ref) <= 1e-8 * abs(obj_ref)
+
+
+def test_solve_entry_point_c1(pdas):
+    lp = lpgen.workload("dense_64x128_f64", 0)
+    ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    with pdas.Solver(lp.m, lp.n, "fp64") as S:
+        out = S.solve(dev_A(lp), dv(lp.b), dv(lp.c), x, y, s, alpha=0.95, tol=1e-8)
+    assert out["status"] == 1 and out["iters"] == ref["iters"]
+    assert abs(float(lp.c @ host(x)) - float(lp.c @ ref["x"])) <= 1e-8 * abs(float(lp.c @ ref["x"]))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fp32_ir_objective_and_iterations(pdas, seed):
+    lp = lpgen.generate(64, 128, seed=seed, storage="f32")
+    ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    with pdas.Solver(lp.m, lp.n, "fp32_ir", torch.float32, dspread_refactor=0.0) as S:
+        out = S.solve(dev_A(lp), dv(lp.b), dv(lp.c), x, y, s, alpha=0.95, tol=1e-8)
+    assert out["status"] == 1
+    obj_ref = float(lp.c @ ref["x"])
+    assert abs(float(lp.c @ host(x)) - obj_ref) <= 1e-8 * abs(obj_ref)
+    assert out["iters"] == ref["iters"]
+
+
+def test_edge_cases(pdas):
+    # m = 1 and n = m + 1
+    for (m, n) in [(1, 2), (1, 9), (5, 6)]:
+        lp = lpgen.generate(m, n, seed=11)
+        ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+        x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+        with pdas.Solver(m, n, "fp64") as S:
+            out = S.solve(dev_A(lp), dv(lp.b), dv(lp.c), x, y, s)
+        assert out["status"] == ref["status"] and out["iters"] == ref["iters"]
+        assert abs(float(lp.c @ host(x)) - float(lp.c @ ref["x"])) <= 1e-8 * (1 + abs(float(lp.c @ ref["x"])))
+    lp = lpgen.generate(6, 14, seed=12)
+    with pdas.Solver(6, 14, "fp64") as S:
+        A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+        # not interior: nothing modified
+        x0 = lp.x0.copy()
+        x0[3] = 0.0
+        x, y, s = dv(x0), dv(lp.y0), dv(lp.s0)
+        out = S.solve(A, b, c, x, y, s)
+        assert out["status"] == -2 and np.array_equal(host(x), x0) and np.array_equal(host(y), lp.y0)
+        # alpha outside (0, 1)
+        x = dv(lp.x0)
+        st, _ = S.step(A, b, c, x, y, s, alpha=1.0, raise_on_error=False)
+        assert st == -1 and np.array_equal(host(x), lp.x0)
+    # rank-deficient A: a zero row -> reported, iterate untouched
+    A0 = lp.A64.copy()
+    A0[2] = 0.0
+    with pdas.Solver(6, 14, "fp64") as S:
+        x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+        out = S.solve(dv(A0), dv(A0 @ lp.x0), dv(A0.T @ lp.y0 + lp.s0), x, y, s)
+        assert out["status"] == -3 and S.last_error_index() == 2
+        assert np.array_equal(host(x), lp.x0)
+
+
+def test_full_step_lp_is_exact(pdas):
+    from conftest import load_fixture
+    g = load_fixture("lp_2x4_one_step.txt")
+    A = np.array(g["A"]).reshape(2, 4)
+    x, y, s = dv(g["x0"]), dv(g["y0"]), dv(g["s0"])
+    with pdas.Solver(2, 4, "fp64") as S:
+        out = S.solve(dv(A), dv(g["b"]), dv(g["c"]), x, y, s)
+    assert out["status"] == 2 and out["iters"] == 1
+    assert np.array_equal(host(x), g["x_opt"]) and np.array_equal(host(y), g["y_opt"])
+    assert np.array_equal(host(s), g["s_opt"])
+
+
+def test_fp64_c2_first_iterations(pdas):
+    """2048 x 8192 FP64: the first two iterates against the oracle."""
+    lp = lpgen.workload("dense_2048x8192_f64", 0)
+    n, m = lp.n, lp.m
+    A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    xo, yo, so = lp.x0.copy(), lp.y0.copy(), lp.s0.copy()
+    with pdas.Solver(m, n, "fp64") as S:
+        for k in range(2):
+            S.step(A, b, c, x, y, s, alpha=0.95)
+            d = oracle.direction(lp.A64, xo, so)
+            th = oracle.theta(oracle.psi(xo, so, d["dx"], d["ds"]), 0.95)
+            xo, yo, so = oracle.step(xo, yo, so, d["dx"], d["dy"], d["ds"], th)
+            for g, o in ((x, xo), (y, yo), (s, so)):
+                assert np.linalg.norm(host(g) - o) <= 1e-9 * np.linalg.norm(o), k
+
+
+def test_full_size_sampled_normal_matrix(pdas):
+    """8192 x 32768 BF16-stored, column-scaled A: sampled entries of the FP64
+    normal matrix and of A x against the oracle computed one by one."""
+    lp = lpgen.workload("dense_8192x32768_bf16_colscaled", 0)
+    m, n = lp.m, lp.n
+    rng = np.random.default_rng(6)
+    with pdas.Solver(m, n, "fp64", torch.bfloat16) as S:
+        A = dev_A(lp)
+        S.form_normal(A, dv(lp.x0), dv(lp.s0))
+        M = S.copy_matrix()
+        r = host(S.gemv(A, dv(lp.x0)))
+        pairs = [(int(p), int(q)) for p, q in zip(rng.integers(0, m, 64), rng.integers(0, m, 64))]
+        pairs = [(max(p, q), min(p, q)) for p, q in pairs] + [(m - 1, m - 1), (m - 1, 0), (0, 0)]
+        got = {pq: float(M[pq[0], pq[1]]) for pq in pairs}
+    D = lp.x0 / lp.s0
+    for (p, q), g in got.items():
+        o = oracle.normal_entry(lp.A64, D, p, q)
+        bound = 2 * gamma(n + 2, U64) * float(np.abs(lp.A64[p]) * D @ np.abs(lp.A64[q]))
+        assert abs(g - o) <= bound, (p, q)
+    rows = rng.integers(0, m, 32)
+    for p in rows:
+        o = float(lp.A64[p] @ lp.x0)  # reference magnitude only
+        bound = 2 * gamma(n, U64) * float(np.abs(lp.A64[p]) @ np.abs(lp.x0))
+        assert abs(r[p] - oracle.gemv(lp.A64[p:p + 1], lp.x0)[0]) <= bound and np.isfinite(o)
