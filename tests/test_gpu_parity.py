@@ -200,8 +200,11 @@ def test_fp64_iterates_match_oracle_every_iteration(pdas, seed):
     lp = lpgen.workload("dense_64x128_f64", seed)
     ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, keep_iterates=True)
     n, m = lp.n, lp.m
-    spread = iterate_spread(ref["iterates"], lapack_trajectory(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0,
-                                                               ref["iters"]), n, m)
+    traj = lapack_trajectory(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, ref["iters"])
+    spread = iterate_spread(ref["iterates"], traj, n, m)
+    # psi is a max of componentwise ratios -dx_j/x_j: its drift follows the
+    # componentwise error of dx, measured the same way
+    psi_spread = np.array([abs(t[3] - ref["trace"][k, 0]) / ref["trace"][k, 0] for k, t in enumerate(traj)])
     A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
     x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
     first_above = None
@@ -215,7 +218,8 @@ def test_fp64_iterates_match_oracle_every_iteration(pdas, seed):
             assert err <= bound, (k, err, spread[k])
             if err > 1e-9 and first_above is None:
                 first_above = k
-            assert abs(info["psi"] - ref["trace"][k, 0]) <= bound * abs(ref["trace"][k, 0])
+            psi_bound = max(1e-9, 4 * psi_spread[: k + 1].max())
+            assert abs(info["psi"] - ref["trace"][k, 0]) <= psi_bound * ref["trace"][k, 0], k
         assert info["rel_gap"] < 1e-8  # the oracle stops at this same iteration
     print("seed %d: first iteration above 1e-9: %s (LAPACK drift max %.1e)" % (seed, first_above, spread.max()))
     obj, obj_ref = float(lp.c @ host(x)), float(lp.c @ ref["x"])
