@@ -55,6 +55,28 @@ pdas_status pdas_gemv(pdas_handle h, const void* A, const double* v, double* out
 /* out (n) = A' u (m), FP64 accumulation: the product behind ds = -A' dy. */
 pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* out);
 
+/* Size of the fixed device scratch behind pdas_gemv_t_noalloc: 8 MiB. */
+#define PDAS_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* out (n) = A' u (m) like pdas_gemv_t, but with no handle and no device
+ * allocation, for callers that cannot call cudaMalloc: code running while
+ * another component captures the stream into a CUDA graph, processes whose
+ * device memory belongs to another framework's pool, real-time loops that
+ * forbid allocation after start-up.  The paper has no counterpart; this is a
+ * deployment convenience.
+ *   A: m x n row-major device array of dtype a_dtype (pdas_dtype); u: m
+ *   doubles; out: n doubles (device, caller-owned); stream: cudaStream_t or
+ *   NULL.  Results agree with pdas_gemv_t to FP64 summation-order rounding.
+ * Scratch is one file-scope device array of PDAS_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until exit; n may be at most
+ * (PDAS_NOALLOC_SCRATCH_BYTES - 256) / 8 = 1048544, else PDAS_ERR_ARG.  All
+ * calls share that array, so calls that overlap on the GPU race: serialise
+ * them.  The first call on a device fetches the array's device address
+ * (with that device current) and loads the kernels; make it before any
+ * stream capture.  Returns PDAS_OK, PDAS_ERR_ARG or PDAS_ERR_CUDA. */
+pdas_status pdas_gemv_t_noalloc(int64_t m, int64_t n, int a_dtype, const void* A, const double* u, double* out,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif
