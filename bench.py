@@ -196,6 +196,43 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_normal_only(args):
+    """Times the normal-matrix stage alone (pdas_form_normal: D = x/s and
+    M = A D A' at the seeded start), for kernel profiles and the roofline."""
+    import torch
+
+    import paper_1502_03543_gb300 as P
+    from paper_1502_03543_gb300 import build as B
+
+    B.build()
+    lp = lpgen.workload(args.workload, seed=0)
+    a_dtype = torch.bfloat16 if lp.storage == "bf16" else {"f64": torch.float64, "f32": torch.float32}[lp.storage]
+    if lp.storage == "bf16":
+        A = torch.from_numpy(lp.A_store.view(np.int16)).view(torch.bfloat16).cuda()
+    else:
+        A = torch.from_numpy(np.ascontiguousarray(lp.A_store)).cuda()
+    x = torch.from_numpy(lp.x0).cuda()
+    s = torch.from_numpy(lp.s0).cuda()
+    opts = {"splits": args.splits} if args.splits else {}
+    S = P.Solver(lp.m, lp.n, args.form, a_dtype, **opts)
+    for _ in range(args.warmup):
+        S.form_normal(A, x, s)
+    torch.cuda.synchronize()
+    S.profile_enable(True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.form_normal(A, x, s)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    prof = S.profile_read()
+    S.close()
+    ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
+    splits = args.splits or 2
+    roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, load_peaks())
+    print(json.dumps(dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits,
+                          ms_per_launch=ms, launches=prof["launches"], wall_s=wall, roofline=roof)))
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -353,11 +390,15 @@ def main():
     ap.add_argument("--dspread", type=float, default=None, help="dspread_refactor option (<= 0 disables)")
     ap.add_argument("--time-to-gap", action="store_true", help="also time one full solve to the gap tolerance")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["step", "normal"], default="step",
+                    help="normal: time only the normal-matrix stage (for profiles)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernel == "normal":
+        run_normal_only(args)
     else:
         run_ours(args)
 

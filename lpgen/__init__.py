@@ -111,6 +111,8 @@ WORKLOADS = {
     "dense_64x128_f64": dict(m=64, n=128, storage="f64", scaled=False, tol=1e-8),
     "dense_2048x8192_f64": dict(m=2048, n=8192, storage="f64", scaled=False, tol=1e-8),
     "dense_8192x32768_bf16_colscaled": dict(m=8192, n=32768, storage="bf16", scaled=True, tol=1e-8),
+    # a mid-size case of the same family, for kernel profiles (A is 134 MB, larger than L2)
+    "dense_4096x16384_bf16_colscaled": dict(m=4096, n=16384, storage="bf16", scaled=True, tol=1e-8),
 }
 
 

@@ -1,20 +1,440 @@
-// syrk_tc.cu -- tensor-core normal-matrix builder (not built yet).
+// syrk_tc.cu -- the normal matrix M = A D A' (Section V) on the tcgen05
+// tensor cores, for the BF16 mixed-precision form.
+//
+// D is folded into one operand: B = D.*A (row q: B_qj = A_qj D_j) is split
+// into `splits` BF16 terms B = B_0 + B_1 (+ B_2), each carrying the next 8
+// bits of the FP32 product, so A B_t' is exact per product and
+//     M ~= sum_t A B_t'      (FP32 accumulation in tensor memory).
+// A (BF16, exact) is read in place by TMA when its rows are 16-byte aligned.
+//
+// Kernel k_syrk_tc: one CTA per 128 x 256 tile of the lower triangle
+// (tiles whose rows p all lie above their columns q are skipped), 6 warps:
+//   warp 0      TMA producer: per K step (64 elements = one 128-byte swizzle
+//               row) loads the A tile (128 x 64) and one B_t tile (256 x 64)
+//               into a 4-stage ring (48 KB per stage);
+//   warp 1      allocates 256 TMEM columns; one lane issues
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16) and
+//               releases each stage with tcgen05.commit;
+//   warps 2..5  wait for the accumulator, read it with tcgen05.ld
+//               (warp w reads TMEM lanes 32*(w%4)..), write rows p >= q.
+// Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
+// PDAS_ERR_TIMEOUT, drains its in-flight copies, frees TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
 #include "syrk_tc.cuh"
 
 namespace pdas {
 
-cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int splits, int64_t m, int64_t n) {
-  (void)w; (void)form; (void)a_dtype; (void)splits; (void)m; (void)n;
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;
+constexpr int STAGES = 4;
+constexpr int UMMA_K = 16;
+constexpr uint32_t A_BYTES = BM * BK * 2;
+constexpr uint32_t B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr int NUM_THREADS = 192;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+constexpr uint64_t kWaitNs = 2000000000ull;       // one pipeline wait
+constexpr uint64_t kEpilogueWaitNs = 60000000000ull; // whole main loop; the pipeline waits bound it first
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when another role aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit_ns = kWaitNs) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 63) == 0) {
+      if (abort_flag && *abort_flag) return false;
+      if (now_ns() - t0 > limit_ns) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::
+          "r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-void tc_workspace_destroy(TcWorkspace* w) { (void)w; }
+// Shared-memory matrix descriptor: K-major operand tile, rows of 128 bytes
+// (64 BF16) written by TMA with 128-byte swizzle; 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                             // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: one 8-row group
+  d |= (uint64_t)1 << 46;                             // descriptor version
+  d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN.
+constexpr uint32_t kIdescBf16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+              const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
+              const int2* __restrict__ tiles, int nk, int splits, int64_t m, int64_t ldm, float* __restrict__ M,
+              Scalars* sc) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + STAGES + s); };
+  const uint32_t tmem_full = smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 tile = tiles[blockIdx.x];
+  const int p0 = tile.x * BM, q0 = tile.y * BN;
+  const int total = nk * splits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(tmem_full, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < total; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int kb = it / splits, t = it % splits;
+        const CUtensorMap* mb = t == 0 ? &tmB0 : (t == 1 ? &tmB1 : &tmB2);
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        tma_load_2d(sbase + s * STAGE_BYTES, &tmA, kb * BK, p0, full(s));
+        tma_load_2d(sbase + s * STAGE_BYTES + A_BYTES, mb, kb * BK, q0, full(s));
+        issued = it + 1;
+      }
+      if (*abort_flag) {  // let every issued copy land before the CTA can exit
+        for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it)
+          mbar_wait(full(it % STAGES), (uint32_t)(it / STAGES) & 1u, nullptr);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int it = 0; it < total; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(full(s), ph, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = sdesc_sw128(sbase + s * STAGE_BYTES);
+        const uint64_t bd = sdesc_sw128(sbase + s * STAGE_BYTES + A_BYTES);
+#pragma unroll
+        for (int k = 0; k < BK / UMMA_K; ++k)  // advance 32 bytes (16 BF16) along K per MMA
+          umma_f16(tmem, ad + 2 * k, bd + 2 * k, kIdescBf16, (it > 0 || k > 0) ? 1u : 0u);
+        umma_commit(empty(s));
+      }
+      umma_commit(tmem_full);  // fires once every MMA issued above has completed
+      if (*abort_flag) mbar_wait(tmem_full, 0, nullptr);  // nothing of ours still writes TMEM
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3;  // TMEM lanes this warp may read
+    int ready = 0;
+    if (lane == 0) ready = mbar_wait(tmem_full, 0, abort_flag, kEpilogueWaitNs) && !*abort_flag;
+    ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform for tcgen05.ld
+    tc_fence_after();
+    if (ready) {
+      const int64_t p = p0 + quarter * 32 + lane;
+      const uint32_t row_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(row_addr + (uint32_t)c, r);
+        if (p < m) {
+          float* dst = M + p * ldm;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t q = (int64_t)q0 + c + j;
+            if (q <= p) dst[q] = __uint_as_float(r[j]);
+          }
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// D32 = (float) D.
+__global__ void k_d32(int64_t n, const double* __restrict__ D, float* __restrict__ D32) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    D32[j] = (float)D[j];
+}
+
+// Split B = D.*A into BF16 terms: v = A_pj * D_j in FP32; B_0 = bf16(v),
+// B_1 = bf16(v - B_0), B_2 = bf16(v - B_0 - B_1) (each difference exact in
+// FP32).  opb holds `splits` planes of m rows x kpad; opa, if given, receives
+// a copy of A with row stride kpad (rows of A not 16-byte aligned).
+__global__ void k_fold_split(int64_t m, int64_t n, int64_t kpad, const __nv_bfloat16* __restrict__ A,
+                             const float* __restrict__ D32, int splits, __nv_bfloat16* __restrict__ opb,
+                             __nv_bfloat16* __restrict__ opa, int vec) {
+  const int64_t plane = m * kpad;
+  if (vec) {
+    const int64_t groups_per_row = n / 8;
+    const int64_t total = m * groups_per_row;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t p = g / groups_per_row, j = (g % groups_per_row) * 8;
+      const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A + p * n + j));
+      const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+      const float4 d0 = __ldg(reinterpret_cast<const float4*>(D32 + j));
+      const float4 d1 = __ldg(reinterpret_cast<const float4*>(D32 + j + 4));
+      const float dd[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+      uint32_t out[3][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float v[2] = {__uint_as_float(w[i] << 16) * dd[2 * i], __uint_as_float(w[i] & 0xffff0000u) * dd[2 * i + 1]};
+        uint16_t h[3][2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          float rest = v[e];
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(rest);
+            h[t][e] = __bfloat16_as_ushort(b);
+            rest = rest - __bfloat162float(b);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) out[t][i] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
+      }
+      for (int t = 0; t < splits; ++t)
+        *reinterpret_cast<uint4*>(opb + t * plane + p * kpad + j) = make_uint4(out[t][0], out[t][1], out[t][2],
+                                                                               out[t][3]);
+      if (opa) *reinterpret_cast<uint4*>(opa + p * kpad + j) = raw;
+    }
+  } else {
+    const int64_t total = m * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t p = e / n, j = e % n;
+      const __nv_bfloat16 a = A[e];
+      float rest = __bfloat162float(a) * D32[j];
+      for (int t = 0; t < splits; ++t) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(rest);
+        opb[t * plane + p * kpad + j] = b;
+        rest = rest - __bfloat162float(b);
+      }
+      if (opa) opa[p * kpad + j] = a;
+    }
+  }
+}
+
+// ---- host side ---------------------------------------------------------------
+struct TcHost {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  CUtensorMap mapB[3];
+  CUtensorMap mapA_copy;
+  int2* tiles = nullptr;
+  int ntiles = 0;
+  float* D32 = nullptr;
+  bool smem_attr_set = false;
+};
+
+cudaError_t get_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  *out = fn;
+  return cudaSuccess;
+}
+
+// 2D BF16 tensor map: dims {n (K, innermost), m}, row stride in elements,
+// box {BK, box_rows}, 128-byte swizzle, zero fill out of bounds.
+cudaError_t encode_bf16(TcHost* hs, CUtensorMap* map, const void* base, int64_t m, int64_t n, int64_t row_stride,
+                        int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)(row_stride * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = hs->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int splits, int64_t m, int64_t n) {
+  if (form != PDAS_BF16_IR || a_dtype != PDAS_A_BF16) return cudaErrorNotSupported;
+  if (m > ((int64_t)1 << 30) / BM || n > ((int64_t)1 << 31) - BK) return cudaErrorNotSupported;
+  w->form = form;
+  w->a_dtype = a_dtype;
+  w->splits = splits > 0 ? splits : 2;
+  w->m = m;
+  w->n = n;
+  w->kpad = (n + BK - 1) / BK * BK;
+  w->mpad = (m + BN - 1) / BN * BN;
+  TcHost* hs = new (std::nothrow) TcHost();
+  if (!hs) return cudaErrorMemoryAllocation;
+  w->host = hs;
+  cudaError_t e = get_encoder(&hs->encode);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&w->opb, sizeof(__nv_bfloat16) * (size_t)w->splits * m * w->kpad);
+  if (e == cudaSuccess && n % 8 != 0) e = cudaMalloc(&w->opa, sizeof(__nv_bfloat16) * (size_t)m * w->kpad);
+  if (e == cudaSuccess) e = cudaMalloc(&hs->D32, sizeof(float) * (size_t)((n + 7) / 8 * 8));
+  // lower-triangle tile list: (I, J) with some row p >= some column q
+  std::vector<int2> tl;
+  const int64_t nI = (m + BM - 1) / BM, nJ = (m + BN - 1) / BN;
+  for (int64_t I = 0; I < nI; ++I)
+    for (int64_t J = 0; J < nJ && J * BN <= I * BM + BM - 1; ++J) tl.push_back(make_int2((int)I, (int)J));
+  hs->ntiles = (int)tl.size();
+  if (e == cudaSuccess) e = cudaMalloc(&hs->tiles, sizeof(int2) * tl.size());
+  if (e == cudaSuccess) e = cudaMemcpy(hs->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+  for (int t = 0; e == cudaSuccess && t < 3; ++t) {
+    const int tt = t < w->splits ? t : 0;  // unused maps alias term 0
+    e = encode_bf16(hs, &hs->mapB[t], (const __nv_bfloat16*)w->opb + (size_t)tt * m * w->kpad, m, n, w->kpad, BN);
+  }
+  if (e == cudaSuccess && w->opa) e = encode_bf16(hs, &hs->mapA_copy, w->opa, m, n, w->kpad, BM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  return e;
+}
+
+void tc_workspace_destroy(TcWorkspace* w) {
+  if (w->opa) cudaFree(w->opa);
+  if (w->opb) cudaFree(w->opb);
+  TcHost* hs = static_cast<TcHost*>(w->host);
+  if (hs) {
+    if (hs->tiles) cudaFree(hs->tiles);
+    if (hs->D32) cudaFree(hs->D32);
+    delete hs;
+  }
+  *w = TcWorkspace{};
+}
 
 cudaError_t tc_form_normal(cudaStream_t st, TcWorkspace* w, int form, int a_dtype, const void* A, const double* D,
                            int64_t m, int64_t n, float* M32, int64_t ldm, const Scalars* sc, int* launches) {
   *launches = 0;
-  (void)st; (void)w; (void)form; (void)a_dtype; (void)A; (void)D; (void)m; (void)n; (void)M32; (void)ldm; (void)sc;
-  return cudaErrorNotSupported;
+  if (form != PDAS_BF16_IR || a_dtype != PDAS_A_BF16 || m != w->m || n != w->n) return cudaErrorNotSupported;
+  if (reinterpret_cast<uintptr_t>(A) % 16 != 0) return cudaErrorInvalidValue;
+  TcHost* hs = static_cast<TcHost*>(w->host);
+  const bool direct = (n % 8 == 0);
+  k_d32<<<(unsigned)((n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184), 256, 0, st>>>(n, D, hs->D32);
+  const int64_t work = direct ? m * (n / 8) : m * n;
+  unsigned grid = (unsigned)((work + 255) / 256 < 4736 ? (work + 255) / 256 : 4736);
+  if (grid < 1) grid = 1;
+  k_fold_split<<<grid, 256, 0, st>>>(m, n, w->kpad, static_cast<const __nv_bfloat16*>(A), hs->D32, w->splits,
+                                     static_cast<__nv_bfloat16*>(w->opb),
+                                     direct ? nullptr : static_cast<__nv_bfloat16*>(w->opa), direct ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mapA;
+  if (direct) {
+    e = encode_bf16(hs, &mapA, A, m, n, n, BM);
+    if (e != cudaSuccess) return e;
+  } else {
+    mapA = hs->mapA_copy;
+  }
+  const int nk = (int)((n + BK - 1) / BK);
+  k_syrk_tc<<<(unsigned)hs->ntiles, NUM_THREADS, SMEM_BYTES, st>>>(mapA, hs->mapB[0], hs->mapB[1], hs->mapB[2],
+                                                                   hs->tiles, nk, w->splits, m, ldm, M32,
+                                                                   const_cast<Scalars*>(sc));
+  *launches = 3;
+  return cudaGetLastError();
 }
 
 }  // namespace pdas
