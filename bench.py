@@ -227,7 +227,7 @@ def run_normal_only(args):
     prof = S.profile_read()
     S.close()
     ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
-    splits = args.splits or 2
+    splits = args.splits or 3
     roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, load_peaks())
     print(json.dumps(dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits,
                           ms_per_launch=ms, launches=prof["launches"], wall_s=wall, roofline=roof)))
@@ -265,7 +265,7 @@ def run_ours(args):
     if args.dspread is not None:
         opts["dspread_refactor"] = args.dspread
     S = P.Solver(m, n, args.form, a_dtype, stream=stream, **opts)
-    splits = S.options.splits or 2
+    splits = S.options.splits or 3
 
     def restart():
         x.copy_(x0)

@@ -71,14 +71,17 @@ typedef struct {
   int a_dtype;             /* pdas_dtype of A                                      (PDAS_A_F64) */
   int max_iter;            /* iteration cap of pdas_solve                                 (500) */
   double refine_tol;       /* refinement stops when ||Ax - M dy||_inf <= refine_tol ||Ax||_inf (1e-14) */
-  int refine_max;          /* cap on refinement sweeps per direction                       (10) */
+  int refine_max;          /* cap on refinement (preconditioned CG) steps per direction     (40) */
   double dspread_refactor; /* mixed forms: re-form and re-factor in FP64 for this and every later
                               iteration once max(D)/min(D) exceeds this; <= 0 disables     (1e8) */
   void* stream;            /* cudaStream_t for all work; NULL = the legacy default stream      */
   int splits;              /* tensor-core forms: number of low-precision terms of D.*A (1..3);
-                              0 = form default (2)                                              */
+                              0 = form default (3)                                              */
   double stall_theta;      /* step length below which a step counts as stalled          (1e-12) */
   int stall_count;         /* consecutive stalled steps that end pdas_solve                  (5) */
+  double refine_be;        /* refinement also stops when the normwise backward error
+                              ||Ax - M dy||_inf / (max_p M_pp ||dy||_inf + ||Ax||_inf) <= refine_be;
+                              0 disables                                                  (1e-14) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */
@@ -91,6 +94,9 @@ typedef struct {
   double refine_resid;  /* final ||Ax - M dy||_inf / ||Ax||_inf (mixed forms; 0 for FP64) */
   int refine_sweeps;    /* refinement sweeps taken (mixed forms)                */
   int used_fp64;        /* 1 if M was formed and factored in FP64 this iteration */
+  int fp64_reason;      /* why a mixed form is in FP64: 0 not, 1 max(D)/min(D) rule,
+                           2 low-precision factor not positive definite,
+                           3 refinement did not reach its tolerance            */
 } pdas_iter_info;
 
 /* Stages of one iteration, for pdas_profile. */
@@ -101,7 +107,8 @@ enum {
   PDAS_STAGE_SOLVE = 3,  /* triangular solves and FP64 refinement of dy           */
   PDAS_STAGE_DIR = 4,    /* ds = -A'dy, dx = D(-ds) - x                            */
   PDAS_STAGE_STEP = 5,   /* psi, theta and the step                                */
-  PDAS_STAGE_COUNT = 6
+  PDAS_STAGE_FOLD = 6,   /* tensor-core forms: D.*A split into low-precision terms */
+  PDAS_STAGE_COUNT = 7
 };
 
 /* Device time per stage, summed over the iterations since profiling was

@@ -32,6 +32,7 @@ class Options(ctypes.Structure):
         ("splits", ctypes.c_int),
         ("stall_theta", ctypes.c_double),
         ("stall_count", ctypes.c_int),
+        ("refine_be", ctypes.c_double),
     ]
 
 
@@ -48,17 +49,18 @@ class IterInfo(ctypes.Structure):
         ("refine_resid", ctypes.c_double),
         ("refine_sweeps", ctypes.c_int),
         ("used_fp64", ctypes.c_int),
+        ("fp64_reason", ctypes.c_int),
     ]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
-STAGES = ("rhs", "normal", "factor", "solve", "direction", "step")
+STAGES = ("rhs", "normal", "factor", "solve", "direction", "step", "fold")
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("calls", ctypes.c_int64 * 6), ("launches", ctypes.c_int64)]
+    _fields_ = [("ms", ctypes.c_double * 7), ("calls", ctypes.c_int64 * 7), ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return dict(ms={k: self.ms[i] for i, k in enumerate(STAGES)},

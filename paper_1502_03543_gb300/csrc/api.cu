@@ -42,9 +42,12 @@ struct pdas_ctx {
   Scalars* sc_host = nullptr;  // pinned
   double* M64 = nullptr;
   float* M32 = nullptr;
+  double* dinv64 = nullptr;  // reciprocals of the pivots of the FP64 / FP32 factor
+  float* dinv32 = nullptr;
   TcWorkspace tc{};
   int cur_f64 = 1;     // the workspace matrix in use is M64
   int refactored = 0;  // a mixed form switched to FP64 for good
+  int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
   char errmsg[256] = {0};
   // diagnostics of the last direction
@@ -201,6 +204,7 @@ pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const 
 
 pdas_status ensure_m64(pdas_ctx* h) {
   if (!h->M64) CK(cudaMalloc(&h->M64, sizeof(double) * h->ldm * h->m));
+  if (!h->dinv64) CK(cudaMalloc(&h->dinv64, sizeof(double) * h->m));
   return PDAS_OK;
 }
 
@@ -227,25 +231,30 @@ pdas_status form_normal(pdas_ctx* h, const void* A) {
     });
   }
   int k = 0;
-  CK(tc_form_normal(h->st, &h->tc, h->opt.form, h->opt.a_dtype, A, h->D, h->m, h->n, h->M32, h->ldm, h->sc, &k));
+  if (h->prof && h->open_stage >= 0) h->open_stage = PDAS_STAGE_FOLD;  // the open interval starts the fold
+  CK(tc_prepare(h->st, &h->tc, A, h->D, &k));
+  h->launches += k;
+  STAGE_END(h);
+  STAGE(h, PDAS_STAGE_NORMAL);
+  CK(tc_syrk(h->st, &h->tc, A, h->M32, h->ldm, h->sc, &k));
   h->launches += k;
   return PDAS_OK;
 }
 
 pdas_status factor(pdas_ctx* h) {
-  if (h->cur_f64) KL(cholesky<double>(h->st, h->m, h->ldm, h->M64, h->sc), chol_launches(h->m));
-  else KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->sc), chol_launches(h->m));
+  if (h->cur_f64) KL(cholesky<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->sc), chol_launches(h->m));
+  else KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->sc), chol_launches(h->m));
   return PDAS_OK;
 }
 
 // out = (L L')^{-1} rhs with the current factor (via h->z).
 pdas_status factor_solve(pdas_ctx* h, const double* rhs, double* out) {
   if (h->cur_f64) {
-    KL(trsv_lower<double>(h->st, h->m, h->ldm, h->M64, rhs, h->z, h->flags, h->tickets, h->sc), 1);
-    KL(trsv_upper_t<double>(h->st, h->m, h->ldm, h->M64, h->z, out, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_lower<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, rhs, h->z, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_upper_t<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->z, out, h->flags, h->tickets, h->sc), 1);
   } else {
-    KL(trsv_lower<float>(h->st, h->m, h->ldm, h->M32, rhs, h->z, h->flags, h->tickets, h->sc), 1);
-    KL(trsv_upper_t<float>(h->st, h->m, h->ldm, h->M32, h->z, out, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_lower<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, rhs, h->z, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_upper_t<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->z, out, h->flags, h->tickets, h->sc), 1);
   }
   return PDAS_OK;
 }
@@ -264,74 +273,79 @@ pdas_status apply_normal(pdas_ctx* h, const void* A, const double* v, double* ou
   return gemv(h, A, h->u, nullptr, out, -1);
 }
 
-// FP64 refinement of dy for the mixed forms (a6).  Plain sweeps
-// dy += (LL')^{-1}(r - M dy) while each cuts ||rho|| at least in half; if a
-// sweep does not, conjugate gradients on M dy = r preconditioned by (LL')^{-1}
-// take over from the best iterate.  Returns PDAS_OK with h->w = A' dy for
-// the final dy, or PDAS_ERR_NOT_SPD-like failure codes through the status.
-// *ok = 0 when neither reached the tolerance (the caller re-factors in FP64).
+// FP64 refinement of dy for the mixed forms (a6): conjugate gradients on
+// M dy = r with the factor as preconditioner, started from dy = (L L')^{-1} r.
+// M is applied matrix-free in FP64 (A(D(A' v))), so the result is as
+// accurate as FP64 arithmetic allows whatever the precision of the factor.
+// The recurrence residual is confirmed against the true residual r - M dy
+// before acceptance and every 10 steps (and replaces it when they differ).
+// Accepted when ||r - M dy||_inf <= refine_tol ||r||_inf, or when the
+// normwise backward error ||r - M dy||_inf / (max_p M_pp ||dy||_inf +
+// ||r||_inf) <= refine_be.  On return h->w = A' dy of the final dy;
+// *ok = 0 if neither test passed within refine_max steps.
 pdas_status refine(pdas_ctx* h, const void* A, int* ok) {
   *ok = 0;
-  const double tol = h->opt.refine_tol;
+  const double tol = h->opt.refine_tol, be_tol = h->opt.refine_be;
   const int cap = h->opt.refine_max;
-  pdas_status s = residual(h, A, h->dy);
-  if (s != PDAS_OK) return s;
-  if ((s = read_scalars(h)) != PDAS_OK) return s;
-  if ((s = device_status(h)) != PDAS_OK) return s;
-  const double rn = h->sc_host->rnorm > 0 ? h->sc_host->rnorm : 1.0;
-  double res = h->sc_host->rho_norm / rn;
-  int sweeps = 0;
-  bool krylov = false;
-  while (res > tol && sweeps < cap) {
-    if ((s = factor_solve(h, h->rho, h->delta)) != PDAS_OK) return s;
-    KL(launch_axpy(h->st, h->m, 1.0, h->delta, h->dy, h->sc), 1);
-    ++sweeps;
-    if ((s = residual(h, A, h->dy)) != PDAS_OK) return s;
-    if ((s = read_scalars(h)) != PDAS_OK) return s;
-    if ((s = device_status(h)) != PDAS_OK) return s;
-    const double nres = h->sc_host->rho_norm / rn;
-    if (!(nres <= 0.5 * res)) {
-      res = nres;
-      krylov = true;
-      break;
-    }
-    res = nres;
-  }
-  if (krylov && res > tol) {
-    // Preconditioned CG from the current dy: rho = r - M dy (in h->rho).
-    if ((s = factor_solve(h, h->rho, h->kz)) != PDAS_OK) return s;
+  pdas_status s;
+  auto true_residual = [&]() -> pdas_status {
+    pdas_status t = residual(h, A, h->dy);  // rho, ||rho||, w = A'dy
+    if (t != PDAS_OK) return t;
+    KL(launch_absmax(h->st, h->m, h->dy, h->part, h->tickets, h->sc, 2), 1);
+    if ((t = read_scalars(h)) != PDAS_OK) return t;
+    return device_status(h);
+  };
+  auto restart = [&](double* rz) -> pdas_status {  // z = P^{-1} rho, p = z, rz = rho'z
+    pdas_status t = factor_solve(h, h->rho, h->kz);
+    if (t != PDAS_OK) return t;
     CK(cudaMemcpyAsync(h->kp, h->kz, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
     KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1);
-    if ((s = read_scalars(h)) != PDAS_OK) return s;
-    double rz = h->sc_host->dot_a;
-    double best = res;
-    while (sweeps < 3 * cap && res > tol) {
-      if ((s = apply_normal(h, A, h->kp, h->kq)) != PDAS_OK) return s;
-      KL(launch_dot(h->st, h->m, h->kp, h->kq, h->part, h->tickets, h->sc, 1), 1);  // dot_b = p'Mp
-      KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1); // dot_a = rho'z
-      KL(launch_krylov_update(h->st, h->m, h->dy, h->kp, h->dy, +1, h->sc), 1);  // dy += a p
-      ++sweeps;
-      // true residual every step (FP64, matrix-free): keeps the recursion honest
-      if ((s = residual(h, A, h->dy)) != PDAS_OK) return s;
+    if ((t = read_scalars(h)) != PDAS_OK) return t;
+    *rz = h->sc_host->dot_a;
+    return device_status(h);
+  };
+  if ((s = true_residual()) != PDAS_OK) return s;
+  const double rn = h->sc_host->rnorm > 0 ? h->sc_host->rnorm : 1.0;
+  const double mn = h->sc_host->mnorm;
+  auto accepted = [&](double res, double dyn) { return res <= tol * rn || res <= be_tol * (mn * dyn + rn); };
+  double res = h->sc_host->rho_norm, dyn = h->sc_host->dynorm;
+  int its = 0;
+  if (accepted(res, dyn)) {
+    *ok = 1;
+  } else {
+    double rz = 0.0;
+    if ((s = restart(&rz)) != PDAS_OK) return s;
+    while (its < cap && rz > 0.0 && isfinite(rz)) {
+      if ((s = apply_normal(h, A, h->kp, h->kq)) != PDAS_OK) return s;                 // q = M p
+      KL(launch_dot(h->st, h->m, h->kp, h->kq, h->part, h->tickets, h->sc, 1), 1);       // p'q
+      KL(launch_krylov_update(h->st, h->m, h->dy, h->kp, h->dy, +1, h->sc), 1);          // dy += a p
+      KL(launch_krylov_update(h->st, h->m, h->rho, h->kq, h->rho, -1, h->sc), 1);        // rho -= a q
+      ++its;
+      KL(launch_absmax(h->st, h->m, h->rho, h->part, h->tickets, h->sc, 1), 1);
+      KL(launch_absmax(h->st, h->m, h->dy, h->part, h->tickets, h->sc, 2), 1);
+      if ((s = factor_solve(h, h->rho, h->kz)) != PDAS_OK) return s;                    // z = P^{-1} rho
+      KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1);      // new rho'z
+      KL(launch_krylov_direction(h->st, h->m, h->kz, h->kp, rz, h->sc), 1);              // p = z + b p
       if ((s = read_scalars(h)) != PDAS_OK) return s;
       if ((s = device_status(h)) != PDAS_OK) return s;
-      res = h->sc_host->rho_norm / rn;
-      if (res <= tol) break;
-      if (!(res < 4.0 * best) || !isfinite(res)) break;  // diverging: give up
-      if (res < best) best = res;
-      if ((s = factor_solve(h, h->rho, h->kz)) != PDAS_OK) return s;
-      KL(launch_dot(h->st, h->m, h->rho, h->kz, h->part, h->tickets, h->sc, 0), 1);
-      KL(launch_krylov_direction(h->st, h->m, h->kz, h->kp, rz, h->sc), 1);
-      if ((s = read_scalars(h)) != PDAS_OK) return s;
+      if (!(h->sc_host->dot_b > 0.0)) break;  // the preconditioned operator lost definiteness
       rz = h->sc_host->dot_a;
+      res = h->sc_host->rho_norm;
+      dyn = h->sc_host->dynorm;
+      if (accepted(res, dyn) || its % 10 == 0 || its == cap) {
+        if ((s = true_residual()) != PDAS_OK) return s;
+        res = h->sc_host->rho_norm;
+        dyn = h->sc_host->dynorm;
+        if (accepted(res, dyn)) {
+          *ok = 1;
+          break;
+        }
+        if ((s = restart(&rz)) != PDAS_OK) return s;
+      }
     }
   }
-  h->last_sweeps = sweeps;
-  h->last_resid = res;
-  // refine_tol is the target; a direction whose residual stalled at the FP64
-  // rounding floor of the matrix-free product is still accepted up to
-  // kRefineAccept (relative to ||A x||_inf).
-  *ok = res <= tol || res <= kRefineAccept;
+  h->last_sweeps = its;
+  h->last_resid = res / rn;
   return PDAS_OK;
 }
 
@@ -346,19 +360,26 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
   if (is_mixed(h) && !h->refactored && h->opt.dspread_refactor > 0) {
     if ((st = read_scalars(h)) != PDAS_OK) return st;
     if ((st = device_status(h)) != PDAS_OK) return st;
-    if (h->sc_host->dmax / h->sc_host->dmin > h->opt.dspread_refactor) h->refactored = 1;
+    if (h->sc_host->dmax / h->sc_host->dmin > h->opt.dspread_refactor) {
+      h->refactored = 1;
+      h->switch_reason = 1;
+    }
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
     STAGE(h, PDAS_STAGE_NORMAL);
     if ((st = form_normal(h, A)) != PDAS_OK) return st;
     STAGE_END(h);
+    if (is_mixed(h)) {  // max_p M_pp for the backward-error test of the refinement
+      if (h->cur_f64) KL(launch_diag_max<double>(h->st, h->m, h->ldm, h->M64, h->part, h->tickets, h->sc), 1);
+      else KL(launch_diag_max<float>(h->st, h->m, h->ldm, h->M32, h->part, h->tickets, h->sc), 1);
+    }
     STAGE(h, PDAS_STAGE_FACTOR);
     if ((st = factor(h)) != PDAS_OK) return st;
     STAGE_END(h);
     STAGE(h, PDAS_STAGE_SOLVE);
     if ((st = factor_solve(h, h->r, h->dy)) != PDAS_OK) return st;
     h->last_fp64 = h->cur_f64;
-    if (h->cur_f64) {
+    if (!is_mixed(h)) {  // the plain FP64 form: the direct solve of Section V-A, unrefined
       STAGE_END(h);
       h->last_sweeps = 0;
       h->last_resid = 0.0;
@@ -372,6 +393,7 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
     if (st == PDAS_ERR_NOT_SPD) {  // low-precision factor broke down: FP64 from now on
       STAGE_END(h);
       h->refactored = 1;
+      h->switch_reason = 2;
       if ((st = reset_status(h)) != PDAS_OK) return st;
       KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
       if ((st = gemv(h, A, x, nullptr, h->r, 0)) != PDAS_OK) return st;
@@ -381,14 +403,16 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
     int ok = 0;
     if ((st = refine(h, A, &ok)) != PDAS_OK) return st;
     STAGE_END(h);
-    if (ok) {
-      // w = A' dy of the accepted dy is in h->w: dx = D w - x, ds = -w
+    if (ok || h->cur_f64) {
+      // w = A' dy of the accepted dy is in h->w: dx = D w - x, ds = -w.  (An
+      // FP64 factor is the last tier: its refined direction is used as is.)
       STAGE(h, PDAS_STAGE_DIR);
       KL(launch_gemv_t_finish(h->st, h->n, 0, nullptr, 3, x, h->D, h->dx, h->ds, h->w, h->sc), 1);
       STAGE_END(h);
       return PDAS_OK;
     }
     h->refactored = 1;  // refinement failed: re-form and re-factor in FP64
+    h->switch_reason = 3;
   }
   return PDAS_ERR_NOT_SPD;
 }
@@ -407,6 +431,7 @@ void fill_info(pdas_ctx* h, pdas_iter_info* info, bool stepped) {
   info->refine_sweeps = h->last_sweeps;
   info->refine_resid = h->last_resid;
   info->used_fp64 = h->last_fp64;
+  info->fp64_reason = (h->last_fp64 && is_mixed(h)) ? h->switch_reason : 0;
   if (stepped) {
     info->psi = s.psi;
     info->theta = s.theta;
@@ -429,7 +454,8 @@ void pdas_default_options(pdas_options* opt) {
   opt->a_dtype = PDAS_A_F64;
   opt->max_iter = 500;
   opt->refine_tol = 1e-14;
-  opt->refine_max = 10;
+  opt->refine_max = 40;
+  opt->refine_be = 1e-14;
   opt->dspread_refactor = 1e8;
   opt->stream = nullptr;
   opt->splits = 0;
@@ -465,7 +491,8 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (m < 1 || n <= m || m > (int64_t)1 << 20 || n > (int64_t)1 << 31) return PDAS_ERR_ARG;
   if (opt.form < PDAS_FP64 || opt.form > PDAS_FP32_IR) return PDAS_ERR_ARG;
   if (opt.a_dtype < PDAS_A_F64 || opt.a_dtype > PDAS_A_BF16) return PDAS_ERR_ARG;
-  if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || opt.splits < 0 || opt.splits > 3 ||
+  if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) || opt.splits < 0 ||
+      opt.splits > 3 ||
       opt.stall_count < 1 || !(opt.stall_theta >= 0))
     return PDAS_ERR_ARG;
   if (opt.form == PDAS_BF16_IR && opt.a_dtype != PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
@@ -510,8 +537,13 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   al((void**)&h->sc, sizeof(Scalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->sc_host, sizeof(Scalars));
   if (e == cudaSuccess) {
-    if (opt.form == PDAS_FP64) al((void**)&h->M64, sizeof(double) * h->ldm * m);
-    else al((void**)&h->M32, sizeof(float) * h->ldm * m);
+    if (opt.form == PDAS_FP64) {
+      al((void**)&h->M64, sizeof(double) * h->ldm * m);
+      al((void**)&h->dinv64, sizeof(double) * m);
+    } else {
+      al((void**)&h->M32, sizeof(float) * h->ldm * m);
+      al((void**)&h->dinv32, sizeof(float) * m);
+    }
   }
   if (e == cudaSuccess && (opt.form == PDAS_BF16_IR || opt.form == PDAS_TF32_IR)) {
     e = tc_workspace_create(&h->tc, opt.form, opt.a_dtype, opt.splits, m, n);
@@ -542,6 +574,8 @@ void pdas_destroy(pdas_handle h) {
   for (double* p : vecs)
     if (p) cudaFree(p);
   if (h->M32) cudaFree(h->M32);
+  if (h->dinv64) cudaFree(h->dinv64);
+  if (h->dinv32) cudaFree(h->dinv32);
   if (h->tickets) cudaFree(h->tickets);
   if (h->flags) cudaFree(h->flags);
   if (h->sc) cudaFree(h->sc);
@@ -624,6 +658,7 @@ pdas_status pdas_solve(pdas_handle h, const void* A, const double* b, const doub
   if (!(alpha > 0.0 && alpha < 1.0) || !(tol > 0.0)) return PDAS_ERR_ARG;
   h->err_index = -1;
   h->refactored = 0;
+  h->switch_reason = 0;
   // interior check before anything is modified
   pdas_status st = reset_status(h);
   if (st != PDAS_OK) return st;
@@ -674,7 +709,9 @@ pdas_status pdas_form_normal(pdas_handle h, const void* A, const double* x, cons
   pdas_status st = reset_status(h);
   if (st != PDAS_OK) return st;
   KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+  STAGE(h, PDAS_STAGE_NORMAL);
   if ((st = form_normal(h, A)) != PDAS_OK) return st;
+  STAGE_END(h);
   if ((st = read_scalars(h)) != PDAS_OK) return st;
   return device_status(h);
 }

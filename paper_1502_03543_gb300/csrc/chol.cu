@@ -58,7 +58,7 @@ __device__ int factor_diag(T (*Ld)[kTile + 1], int kb) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm, T* M, int64_t k0, int kb,
+__global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm, T* M, T* dinv, int64_t k0, int kb,
                                                          Scalars* sc) {
   __shared__ T Ld[kTile][kTile + 1];
   if (dev_failed(sc)) return;
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm,
       const int i = e / kb, j = e % kb;
       if (j <= i) M[(k0 + i) * ldm + k0 + j] = Ld[i][j];
     }
+    if (threadIdx.x < kb) dinv[k0 + threadIdx.x] = T(1) / Ld[threadIdx.x][threadIdx.x];
     return;
   }
   // Panel rows: X L11' = B, right-looking over columns; thread (row, part)
@@ -181,14 +182,18 @@ __device__ bool block_wait(const int* flags, int64_t j, Scalars* sc) {
 }
 
 // L z = v.  Block row b (64 rows): z_b = L_bb^{-1} (v_b - sum_{j<b} L_bj z_j).
-// Warp w owns rows 8w..8w+7 of the block; lane l owns columns l, l+32.
+// Arithmetic in T (the factor's precision; the FP32 factor of the mixed forms
+// is a preconditioner, refined in FP64 afterwards); v, z in FP64.  Warp w
+// owns rows 8w..8w+7 of the block, lane l owns columns l, l+32; the diagonal
+// block is solved by warp 0 with the reciprocals of the pivots.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm, const T* __restrict__ L,
-                                                         const double* __restrict__ v, double* z, int* flags,
-                                                         unsigned* ticket, Scalars* sc) {
-  __shared__ double Ld[kTile][kTile + 1];
-  __shared__ double zj[kTile];
-  __shared__ double acc[kTile];
+                                                         const T* __restrict__ dinv, const double* __restrict__ v,
+                                                         double* z, int* flags, unsigned* ticket, Scalars* sc) {
+  __shared__ T Ld[kTile][kTile + 1];
+  __shared__ T zj[kTile];
+  __shared__ T acc[kTile];
+  __shared__ T rcp[kTile];
   __shared__ int sbi;
   if (threadIdx.x == 0) sbi = (int)atomicAdd(ticket, 1u);
   __syncthreads();
@@ -199,22 +204,23 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int i = e / kTile, j = e % kTile;
-    Ld[i][j] = (i < rb && j <= i) ? widen(L[(r0 + i) * ldm + r0 + j]) : 0.0;
+    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] : T(0);
   }
-  double part[8];
+  if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
+  T part[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) part[i] = 0.0;
+  for (int i = 0; i < 8; ++i) part[i] = T(0);
   for (int64_t jb = 0; jb < b; ++jb) {
-    double l0[8], l1[8];
+    T l0[8], l1[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = 8 * w + i;
       const T* row = L + (r0 + r) * ldm + jb * kTile;
-      l0[i] = r < rb ? widen(row[lane]) : 0.0;
-      l1[i] = r < rb ? widen(row[lane + 32]) : 0.0;
+      l0[i] = r < rb ? row[lane] : T(0);
+      l1[i] = r < rb ? row[lane + 32] : T(0);
     }
     if (!block_wait(flags, jb, sc)) return;
-    if (threadIdx.x < kTile) zj[threadIdx.x] = __ldcg(z + jb * kTile + threadIdx.x);
+    if (threadIdx.x < kTile) zj[threadIdx.x] = (T)__ldcg(z + jb * kTile + threadIdx.x);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 8; ++i) part[i] = fma(l0[i], zj[lane], fma(l1[i], zj[lane + 32], part[i]));
@@ -222,25 +228,25 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    double t = part[i];
+    T t = part[i];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     const int r = 8 * w + i;
-    if (lane == 0) acc[r] = r < rb ? v[r0 + r] - t : 0.0;
+    if (lane == 0) acc[r] = r < rb ? (T)v[r0 + r] - t : T(0);
   }
   __syncthreads();
   if (w == 0) {
-    double a0 = acc[lane], a1 = acc[lane + 32];
+    T a0 = acc[lane], a1 = acc[lane + 32];
     for (int c = 0; c < rb; ++c) {
-      const double own = c < 32 ? a0 : a1;
-      const double zc = __shfl_sync(0xffffffffu, own, c & 31) / Ld[c][c];
+      const T own = c < 32 ? a0 : a1;
+      const T zc = __shfl_sync(0xffffffffu, own, c & 31) * rcp[c];
       if (lane == (c & 31)) {
         if (c < 32) a0 = zc; else a1 = zc;
       }
       if (lane > c) a0 -= Ld[lane][c] * zc;
       if (lane + 32 > c) a1 -= Ld[lane + 32][c] * zc;
     }
-    if (lane < rb) z[r0 + lane] = a0;
-    if (lane + 32 < rb) z[r0 + lane + 32] = a1;
+    if (lane < rb) z[r0 + lane] = (double)a0;
+    if (lane + 32 < rb) z[r0 + lane + 32] = (double)a1;
     __threadfence();
     __syncwarp();
     if (lane == 0) st_release(flags + b, 1);
@@ -252,11 +258,13 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
 // L[k][r] y_k for rows k = 8w..8w+7 of that block and columns r = lane, lane+32.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ldm, const T* __restrict__ L,
+                                                           const T* __restrict__ dinv,
                                                            const double* __restrict__ zin, double* y, int* flags,
                                                            unsigned* ticket, Scalars* sc) {
-  __shared__ double Ld[kTile][kTile + 1];
-  __shared__ double yk[kTile];
-  __shared__ double red[8][kTile];
+  __shared__ T Ld[kTile][kTile + 1];
+  __shared__ T yk[kTile];
+  __shared__ T red[8][kTile];
+  __shared__ T rcp[kTile];
   __shared__ int sbi;
   const int64_t nblk = (m + kTile - 1) / kTile;
   if (threadIdx.x == 0) sbi = (int)atomicAdd(ticket, 1u);
@@ -268,22 +276,23 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int i = e / kTile, j = e % kTile;
-    Ld[i][j] = (i < rb && j <= i) ? widen(L[(r0 + i) * ldm + r0 + j]) : 0.0;
+    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] : T(0);
   }
-  double p0 = 0.0, p1 = 0.0;
+  if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
+  T p0 = T(0), p1 = T(0);
   for (int64_t kb = nblk - 1; kb > b; --kb) {
     const int64_t k0 = kb * kTile;
     const int kr = (int)(m - k0 < kTile ? m - k0 : kTile);
-    double l0[8], l1[8];
+    T l0[8], l1[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = 8 * w + i;
       const T* row = L + (k0 + k) * ldm + r0;
-      l0[i] = (k < kr && lane < rb) ? widen(row[lane]) : 0.0;
-      l1[i] = (k < kr && lane + 32 < rb) ? widen(row[lane + 32]) : 0.0;
+      l0[i] = (k < kr && lane < rb) ? row[lane] : T(0);
+      l1[i] = (k < kr && lane + 32 < rb) ? row[lane + 32] : T(0);
     }
     if (!block_wait(flags, kb, sc)) return;
-    if (threadIdx.x < kTile) yk[threadIdx.x] = threadIdx.x < kr ? __ldcg(y + k0 + threadIdx.x) : 0.0;
+    if (threadIdx.x < kTile) yk[threadIdx.x] = threadIdx.x < kr ? (T)__ldcg(y + k0 + threadIdx.x) : T(0);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -296,25 +305,25 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
   red[w][lane + 32] = p1;
   __syncthreads();
   if (w == 0) {
-    double a0 = 0.0, a1 = 0.0;
+    T a0 = T(0), a1 = T(0);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       a0 += red[i][lane];
       a1 += red[i][lane + 32];
     }
-    a0 = lane < rb ? zin[r0 + lane] - a0 : 0.0;
-    a1 = lane + 32 < rb ? zin[r0 + lane + 32] - a1 : 0.0;
+    a0 = lane < rb ? (T)zin[r0 + lane] - a0 : T(0);
+    a1 = lane + 32 < rb ? (T)zin[r0 + lane + 32] - a1 : T(0);
     for (int c = rb - 1; c >= 0; --c) {
-      const double own = c < 32 ? a0 : a1;
-      const double yc = __shfl_sync(0xffffffffu, own, c & 31) / Ld[c][c];
+      const T own = c < 32 ? a0 : a1;
+      const T yc = __shfl_sync(0xffffffffu, own, c & 31) * rcp[c];
       if (lane == (c & 31)) {
         if (c < 32) a0 = yc; else a1 = yc;
       }
       if (lane < c) a0 -= Ld[c][lane] * yc;
       if (lane + 32 < c) a1 -= Ld[c][lane + 32] * yc;
     }
-    if (lane < rb) y[r0 + lane] = a0;
-    if (lane + 32 < rb) y[r0 + lane + 32] = a1;
+    if (lane < rb) y[r0 + lane] = (double)a0;
+    if (lane + 32 < rb) y[r0 + lane + 32] = (double)a1;
     __threadfence();
     __syncwarp();
     if (lane == 0) st_release(flags + b, 1);
@@ -324,48 +333,48 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
 }  // namespace
 
 template <typename T>
-cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, Scalars* sc) {
+cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Scalars* sc) {
   for (int64_t k0 = 0; k0 < m; k0 += kTile) {
     const int kb = (int)(m - k0 < kTile ? m - k0 : kTile);
     const int64_t rest = m - k0 - kb;
     const int64_t t = (rest + kTile - 1) / kTile;
-    k_chol_panel<T><<<(unsigned)(1 + t), kThreads, 0, st>>>(m, ldm, M, k0, kb, sc);
+    k_chol_panel<T><<<(unsigned)(1 + t), kThreads, 0, st>>>(m, ldm, M, dinv, k0, kb, sc);
     if (t > 0) k_chol_update<T><<<(unsigned)(t * (t + 1) / 2), kThreads, 0, st>>>(m, ldm, M, k0, kb, sc);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* v, double* z, int* flags,
-                       unsigned* tickets, Scalars* sc) {
+cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* v, double* z,
+                       int* flags, unsigned* tickets, Scalars* sc) {
   const int64_t nblk = (m + kTile - 1) / kTile;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets + T_TRSV, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_trsv_lower<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, v, z, flags, tickets + T_TRSV, sc);
+  k_trsv_lower<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, v, z, flags, tickets + T_TRSV, sc);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* z, double* y,
-                         int* flags, unsigned* tickets, Scalars* sc) {
+cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* z,
+                         double* y, int* flags, unsigned* tickets, Scalars* sc) {
   const int64_t nblk = (m + kTile - 1) / kTile;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets + T_TRSV, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_trsv_upper_t<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, z, y, flags, tickets + T_TRSV, sc);
+  k_trsv_upper_t<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, z, y, flags, tickets + T_TRSV, sc);
   return cudaGetLastError();
 }
 
-template cudaError_t cholesky<double>(cudaStream_t, int64_t, int64_t, double*, Scalars*);
-template cudaError_t cholesky<float>(cudaStream_t, int64_t, int64_t, float*, Scalars*);
-template cudaError_t trsv_lower<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, double*, int*,
-                                        unsigned*, Scalars*);
-template cudaError_t trsv_lower<float>(cudaStream_t, int64_t, int64_t, const float*, const double*, double*, int*,
-                                       unsigned*, Scalars*);
-template cudaError_t trsv_upper_t<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, double*,
-                                          int*, unsigned*, Scalars*);
-template cudaError_t trsv_upper_t<float>(cudaStream_t, int64_t, int64_t, const float*, const double*, double*, int*,
-                                         unsigned*, Scalars*);
+template cudaError_t cholesky<double>(cudaStream_t, int64_t, int64_t, double*, double*, Scalars*);
+template cudaError_t cholesky<float>(cudaStream_t, int64_t, int64_t, float*, float*, Scalars*);
+template cudaError_t trsv_lower<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, const double*,
+                                        double*, int*, unsigned*, Scalars*);
+template cudaError_t trsv_lower<float>(cudaStream_t, int64_t, int64_t, const float*, const float*, const double*,
+                                       double*, int*, unsigned*, Scalars*);
+template cudaError_t trsv_upper_t<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, const double*,
+                                          double*, int*, unsigned*, Scalars*);
+template cudaError_t trsv_upper_t<float>(cudaStream_t, int64_t, int64_t, const float*, const float*, const double*,
+                                         double*, int*, unsigned*, Scalars*);
 
 }  // namespace pdas

@@ -30,6 +30,8 @@ struct Scalars {
   double rnorm;        // ||A x||_inf
   double rho_norm;     // ||A x - M dy||_inf of the latest residual
   double dot_a, dot_b; // dot products of the refinement Krylov steps
+  double mnorm;        // max_p M_pp of the formed normal matrix (a lower bound on ||M||)
+  double dynorm;       // ||dy||_inf
   int status;          // 0, or a pdas_status error detected on the device
   int fail_index;      // failing pivot for PDAS_ERR_NOT_SPD
   int bad_iterate;     // nonzero if some x_j <= 0 or s_j <= 0 (or not finite)
@@ -85,14 +87,23 @@ template <typename T>
 cudaError_t launch_syrk_simt(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, double* M64,
                              float* M32, int64_t ldm, const Scalars* sc);
 
+// Blocked Cholesky in place; dinv (m) receives the reciprocals of the pivots.
 template <typename T>
-cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, Scalars* sc);
+cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Scalars* sc);
 template <typename T>
-cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* v, double* z,
-                       int* flags, unsigned* tickets, Scalars* sc);
+cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* v,
+                       double* z, int* flags, unsigned* tickets, Scalars* sc);
 template <typename T>
-cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const double* z, double* y,
-                         int* flags, unsigned* tickets, Scalars* sc);
+cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* z,
+                         double* y, int* flags, unsigned* tickets, Scalars* sc);
+
+// sc->mnorm = max_p M[p][p] (before the factorization overwrites it).
+template <typename T>
+cudaError_t launch_diag_max(cudaStream_t st, int64_t m, int64_t ldm, const T* M, double* part, unsigned* tickets,
+                            Scalars* sc);
+// max_j |v_j| into sc->rho_norm (slot 1) or sc->dynorm (slot 2).
+cudaError_t launch_absmax(cudaStream_t st, int64_t n, const double* v, double* part, unsigned* tickets, Scalars* sc,
+                          int slot);
 
 cudaError_t launch_convert_matrix(cudaStream_t st, int64_t m, int64_t ld_src, const void* src, int src_f64,
                                   int64_t ld_dst, void* dst, int dst_f64);

@@ -3,22 +3,30 @@
 //
 // D is folded into one operand: B = D.*A (row q: B_qj = A_qj D_j) is split
 // into `splits` BF16 terms B = B_0 + B_1 (+ B_2), each carrying the next 8
-// bits of the FP32 product, so A B_t' is exact per product and
-//     M ~= sum_t A B_t'      (FP32 accumulation in tensor memory).
+// bits of the FP32 product, so every product A_pj B_t,qj is exact and
+//     M ~= sum_t A B_t'.
 // A (BF16, exact) is read in place by TMA when its rows are 16-byte aligned.
 //
-// Kernel k_syrk_tc: one CTA per 128 x 256 tile of the lower triangle
-// (tiles whose rows p all lie above their columns q are skipped), 6 warps:
-//   warp 0      TMA producer: per K step (64 elements = one 128-byte swizzle
-//               row) loads the A tile (128 x 64) and one B_t tile (256 x 64)
-//               into a 4-stage ring (48 KB per stage);
+// Accumulation.  The tensor core's FP32 accumulator rounds toward zero, so
+// its error grows with the number of accumulation steps in one direction
+// (measured on GB300: 1.5e-4 relative at K = 32768 against 1e-6 for an IEEE
+// FP32 dot product).  The K loop is therefore cut into chunks of KC = 128
+// elements: each chunk is summed on the tensor core into a fresh TMEM buffer
+// (two buffers alternate), and the epilogue warps add the chunk sums, with
+// round-to-nearest FP32, into a master accumulator held in registers.
+//
+// Kernel k_syrk_tc<S>: one CTA per 128 x 128 lower-triangle tile, 6 warps:
+//   warp 0      TMA producer: per K step of 64 (one 128-byte swizzle row) the
+//               A tile and the S tiles of B_t, 128 x 64 each, into a ring of
+//               STAGES (= 192 KB / (16 KB (1 + S))) stages;
 //   warp 1      allocates 256 TMEM columns; one lane issues
-//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16) and
-//               releases each stage with tcgen05.commit;
-//   warps 2..5  wait for the accumulator, read it with tcgen05.ld
-//               (warp w reads TMEM lanes 32*(w%4)..), write rows p >= q.
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
+//               into the current chunk buffer and commits chunk and stage;
+//   warps 2..5  warp w owns TMEM lanes 32*(w%4)..: drains each chunk
+//               (tcgen05.ld) into its 128-float master row, frees the
+//               buffer, and finally writes the rows p >= q of M.
 // Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
-// PDAS_ERR_TIMEOUT, drains its in-flight copies, frees TMEM and exits.
+// PDAS_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM, exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -33,18 +41,22 @@ namespace pdas {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 256;
+constexpr int BN = 128;
 constexpr int BK = 64;
-constexpr int STAGES = 4;
+constexpr int KC_BLOCKS = 2;  // K steps of BK per accumulation chunk (KC = 128)
 constexpr int UMMA_K = 16;
-constexpr uint32_t A_BYTES = BM * BK * 2;
-constexpr uint32_t B_BYTES = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TILE_BYTES = BM * BK * 2;  // one 128 x 64 BF16 tile (A and each B_t)
+constexpr uint32_t RING_BYTES = 192 * 1024;
+constexpr uint32_t TMEM_COLS = 256;           // two chunk buffers of BN columns
 constexpr int NUM_THREADS = 192;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
-constexpr uint64_t kWaitNs = 2000000000ull;       // one pipeline wait
-constexpr uint64_t kEpilogueWaitNs = 60000000000ull; // whole main loop; the pipeline waits bound it first
+constexpr size_t SMEM_BYTES = 1024 + (size_t)RING_BYTES + 512;
+constexpr uint64_t kWaitNs = 2000000000ull;  // one pipeline wait
+
+template <int S>
+struct Ring {
+  static constexpr uint32_t STAGE_BYTES = TILE_BYTES * (1 + S);
+  static constexpr int STAGES = (int)(RING_BYTES / STAGE_BYTES);
+};
 
 // ---- PTX wrappers ----------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -137,32 +149,45 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 constexpr uint32_t kIdescBf16 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int S>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
               const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
-              const int2* __restrict__ tiles, int nk, int splits, int64_t m, int64_t ldm, float* __restrict__ M,
-              Scalars* sc) {
+              const int2* __restrict__ tiles, int nk, int64_t m, int64_t ldm, float* __restrict__ M, Scalars* sc) {
+  constexpr uint32_t STAGE_BYTES = Ring<S>::STAGE_BYTES;
+  constexpr int STAGES = Ring<S>::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
+  // bars: full[STAGES] | empty[STAGES] | chunk_full[2] | chunk_free[2] | done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + STAGES + s); };
-  const uint32_t tmem_full = smem_u32(bars + 2 * STAGES);
+  auto chunk_full = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
+  auto chunk_free = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
+  const uint32_t done_bar = smem_u32(bars + 2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int2 tile = tiles[blockIdx.x];
   const int p0 = tile.x * BM, q0 = tile.y * BN;
-  const int total = nk * splits;
+  const int nchunks = (nk + KC_BLOCKS - 1) / KC_BLOCKS;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    mbar_init(tmem_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(chunk_full(b), 1);
+      mbar_init(chunk_free(b), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(done_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -176,69 +201,95 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
-      for (int it = 0; it < total; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
         if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
           *abort_flag = 1;
           break;
         }
-        const int kb = it / splits, t = it % splits;
-        const CUtensorMap* mb = t == 0 ? &tmB0 : (t == 1 ? &tmB1 : &tmB2);
+        const uint32_t dst = sbase + s * STAGE_BYTES;
         mbar_expect_tx(full(s), STAGE_BYTES);
-        tma_load_2d(sbase + s * STAGE_BYTES, &tmA, kb * BK, p0, full(s));
-        tma_load_2d(sbase + s * STAGE_BYTES + A_BYTES, mb, kb * BK, q0, full(s));
-        issued = it + 1;
+        tma_load_2d(dst, &tmA, kb * BK, p0, full(s));
+        tma_load_2d(dst + TILE_BYTES, &tmB0, kb * BK, q0, full(s));
+        if (S > 1) tma_load_2d(dst + 2 * TILE_BYTES, &tmB1, kb * BK, q0, full(s));
+        if (S > 2) tma_load_2d(dst + 3 * TILE_BYTES, &tmB2, kb * BK, q0, full(s));
+        issued = kb + 1;
       }
       if (*abort_flag) {  // let every issued copy land before the CTA can exit
-        for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it)
-          mbar_wait(full(it % STAGES), (uint32_t)(it / STAGES) & 1u, nullptr);
+        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+          mbar_wait(full(kb % STAGES), (uint32_t)(kb / STAGES) & 1u, nullptr);
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      for (int it = 0; it < total; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag)) {
+      for (int kb = 0; kb < nk && !*abort_flag; ++kb) {
+        const int c = kb / KC_BLOCKS, buf = c & 1;
+        const bool chunk_start = (kb % KC_BLOCKS) == 0;
+        if (chunk_start && c >= 2 &&
+            !mbar_wait(chunk_free(buf), (uint32_t)((c >> 1) - 1) & 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int s = kb % STAGES;
+        if (!mbar_wait(full(s), (uint32_t)(kb / STAGES) & 1u, abort_flag)) {
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
         const uint64_t ad = sdesc_sw128(sbase + s * STAGE_BYTES);
-        const uint64_t bd = sdesc_sw128(sbase + s * STAGE_BYTES + A_BYTES);
 #pragma unroll
-        for (int k = 0; k < BK / UMMA_K; ++k)  // advance 32 bytes (16 BF16) along K per MMA
-          umma_f16(tmem, ad + 2 * k, bd + 2 * k, kIdescBf16, (it > 0 || k > 0) ? 1u : 0u);
+        for (int t = 0; t < S; ++t) {
+          const uint64_t bd = sdesc_sw128(sbase + s * STAGE_BYTES + (1 + t) * TILE_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / UMMA_K; ++k)  // advance 32 bytes (16 BF16) along K per MMA
+            umma_f16(d, ad + 2 * k, bd + 2 * k, kIdescBf16, (chunk_start && t == 0 && k == 0) ? 0u : 1u);
+        }
         umma_commit(empty(s));
+        if ((kb % KC_BLOCKS) == KC_BLOCKS - 1 || kb == nk - 1) umma_commit(chunk_full(buf));
       }
-      umma_commit(tmem_full);  // fires once every MMA issued above has completed
-      if (*abort_flag) mbar_wait(tmem_full, 0, nullptr);  // nothing of ours still writes TMEM
+      umma_commit(done_bar);  // fires once every MMA issued above has completed
+      mbar_wait(done_bar, 0, nullptr);
     }
     __syncwarp();
   } else {
     const int quarter = warp & 3;  // TMEM lanes this warp may read
-    int ready = 0;
-    if (lane == 0) ready = mbar_wait(tmem_full, 0, abort_flag, kEpilogueWaitNs) && !*abort_flag;
-    ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform for tcgen05.ld
-    tc_fence_after();
-    if (ready) {
-      const int64_t p = p0 + quarter * 32 + lane;
-      const uint32_t row_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(row_addr + (uint32_t)c, r);
-        if (p < m) {
-          float* dst = M + p * ldm;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    float acc[BN];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t q = (int64_t)q0 + c + j;
-            if (q <= p) dst[q] = __uint_as_float(r[j]);
-          }
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    int ok = 1;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      if (lane == 0) ok = mbar_wait(chunk_full(buf), (uint32_t)(c >> 1) & 1u, abort_flag) && !*abort_flag;
+      ok = __shfl_sync(0xffffffffu, ok, 0);  // warp-uniform for tcgen05.ld
+      if (!ok) break;
+      tc_fence_after();
+#pragma unroll
+      for (int g = 0; g < BN / 32; ++g) {
+        uint32_t r[32];
+        tmem_ld32(lane_addr + (uint32_t)(buf * BN + g * 32), r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[g * 32 + j] += __uint_as_float(r[j]);  // round to nearest
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(chunk_free(buf));
+    }
+    if (ok) {
+      const int64_t p = p0 + quarter * 32 + lane;
+      if (p < m) {
+        float* dst = M + p * ldm;
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+          const int64_t q = (int64_t)q0 + j;
+          if (q <= p) dst[q] = acc[j];
         }
       }
+    } else if (lane == 0) {
+      *abort_flag = 1;
     }
   }
   if (threadIdx.x == 0 && *abort_flag) atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
@@ -363,7 +414,7 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   if (m > ((int64_t)1 << 30) / BM || n > ((int64_t)1 << 31) - BK) return cudaErrorNotSupported;
   w->form = form;
   w->a_dtype = a_dtype;
-  w->splits = splits > 0 ? splits : 2;
+  w->splits = splits > 0 ? splits : 3;
   w->m = m;
   w->n = n;
   w->kpad = (n + BK - 1) / BK * BK;
@@ -389,8 +440,9 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
     e = encode_bf16(hs, &hs->mapB[t], (const __nv_bfloat16*)w->opb + (size_t)tt * m * w->kpad, m, n, w->kpad, BN);
   }
   if (e == cudaSuccess && w->opa) e = encode_bf16(hs, &hs->mapA_copy, w->opa, m, n, w->kpad, BM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   return e;
 }
 
@@ -406,12 +458,11 @@ void tc_workspace_destroy(TcWorkspace* w) {
   *w = TcWorkspace{};
 }
 
-cudaError_t tc_form_normal(cudaStream_t st, TcWorkspace* w, int form, int a_dtype, const void* A, const double* D,
-                           int64_t m, int64_t n, float* M32, int64_t ldm, const Scalars* sc, int* launches) {
+cudaError_t tc_prepare(cudaStream_t st, TcWorkspace* w, const void* A, const double* D, int* launches) {
   *launches = 0;
-  if (form != PDAS_BF16_IR || a_dtype != PDAS_A_BF16 || m != w->m || n != w->n) return cudaErrorNotSupported;
   if (reinterpret_cast<uintptr_t>(A) % 16 != 0) return cudaErrorInvalidValue;
   TcHost* hs = static_cast<TcHost*>(w->host);
+  const int64_t m = w->m, n = w->n;
   const bool direct = (n % 8 == 0);
   k_d32<<<(unsigned)((n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184), 256, 0, st>>>(n, D, hs->D32);
   const int64_t work = direct ? m * (n / 8) : m * n;
@@ -420,20 +471,35 @@ cudaError_t tc_form_normal(cudaStream_t st, TcWorkspace* w, int form, int a_dtyp
   k_fold_split<<<grid, 256, 0, st>>>(m, n, w->kpad, static_cast<const __nv_bfloat16*>(A), hs->D32, w->splits,
                                      static_cast<__nv_bfloat16*>(w->opb),
                                      direct ? nullptr : static_cast<__nv_bfloat16*>(w->opa), direct ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  *launches = 2;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_syrk(cudaStream_t st, TcWorkspace* w, const void* A, float* M32, int64_t ldm, const Scalars* sc,
+                    int* launches) {
+  *launches = 0;
+  TcHost* hs = static_cast<TcHost*>(w->host);
+  const int64_t m = w->m, n = w->n;
   CUtensorMap mapA;
-  if (direct) {
-    e = encode_bf16(hs, &mapA, A, m, n, n, BM);
+  if (n % 8 == 0) {
+    cudaError_t e = encode_bf16(hs, &mapA, A, m, n, n, BM);
     if (e != cudaSuccess) return e;
   } else {
     mapA = hs->mapA_copy;
   }
   const int nk = (int)((n + BK - 1) / BK);
-  k_syrk_tc<<<(unsigned)hs->ntiles, NUM_THREADS, SMEM_BYTES, st>>>(mapA, hs->mapB[0], hs->mapB[1], hs->mapB[2],
-                                                                   hs->tiles, nk, w->splits, m, ldm, M32,
-                                                                   const_cast<Scalars*>(sc));
-  *launches = 3;
+  Scalars* scw = const_cast<Scalars*>(sc);
+  const dim3 grid((unsigned)hs->ntiles);
+  if (w->splits == 1)
+    k_syrk_tc<1><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, hs->mapB[0], hs->mapB[1], hs->mapB[2], hs->tiles, nk,
+                                                        m, ldm, M32, scw);
+  else if (w->splits == 2)
+    k_syrk_tc<2><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, hs->mapB[0], hs->mapB[1], hs->mapB[2], hs->tiles, nk,
+                                                        m, ldm, M32, scw);
+  else
+    k_syrk_tc<3><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, hs->mapB[0], hs->mapB[1], hs->mapB[2], hs->tiles, nk,
+                                                        m, ldm, M32, scw);
+  *launches = 1;
   return cudaGetLastError();
 }
 

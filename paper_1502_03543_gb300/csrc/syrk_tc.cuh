@@ -24,9 +24,13 @@ struct TcWorkspace {
 cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int splits, int64_t m, int64_t n);
 void tc_workspace_destroy(TcWorkspace* w);
 
+// Writes the split terms (D.*A)_t (and a padded copy of A if its rows are
+// not 16-byte aligned).  *launches receives the kernels started.
+cudaError_t tc_prepare(cudaStream_t st, TcWorkspace* w, const void* A, const double* D, int* launches);
+
 // Lower triangle of M32 (leading dimension ldm) = sum over the split terms of
-// A (D.*A)_t', FP32 accumulation.  *launches receives the kernels started.
-cudaError_t tc_form_normal(cudaStream_t st, TcWorkspace* w, int form, int a_dtype, const void* A, const double* D,
-                           int64_t m, int64_t n, float* M32, int64_t ldm, const Scalars* sc, int* launches);
+// A (D.*A)_t', FP32 accumulation (after tc_prepare).
+cudaError_t tc_syrk(cudaStream_t st, TcWorkspace* w, const void* A, float* M32, int64_t ldm, const Scalars* sc,
+                    int* launches);
 
 }  // namespace pdas

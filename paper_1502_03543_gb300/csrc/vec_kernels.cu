@@ -387,6 +387,42 @@ __global__ void __launch_bounds__(kThreads) k_dot(int64_t n, const double* __res
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_diag_max(int64_t m, int64_t ldm, const T* __restrict__ M, double* part,
+                                                       unsigned* tickets, Scalars* sc) {
+  __shared__ double sm[32];
+  double mx = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs((double)M[p * ldm + p]));
+  mx = block_reduce<1>(mx, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = mx;
+  if (!last_block(tickets + T_NORM2)) return;
+  double g = combine<1>(part, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    sc->mnorm = g;
+    tickets[T_NORM2] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_absmax(int64_t n, const double* __restrict__ v, double* part,
+                                                     unsigned* tickets, Scalars* sc, int slot) {
+  __shared__ double sm[32];
+  if (failed(sc)) return;
+  double mx = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double a = fabs(v[j]);
+    mx = (a == a) ? fmax(mx, a) : INFINITY;
+  }
+  mx = block_reduce<1>(mx, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = mx;
+  if (!last_block(tickets + T_NORM2)) return;
+  double g = combine<1>(part, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    if (slot == 1) sc->rho_norm = g; else sc->dynorm = g;
+    tickets[T_NORM2] = 0;
+  }
+}
+
 __global__ void k_krylov_update(int64_t n, const double* base, const double* __restrict__ p, double* out, int sign,
                                 const Scalars* sc) {
   if (failed(sc)) return;
@@ -490,6 +526,23 @@ cudaError_t launch_krylov_update(cudaStream_t st, int64_t n, const double* base,
 cudaError_t launch_krylov_direction(cudaStream_t st, int64_t n, const double* z, double* p, double beta_den,
                                     const Scalars* sc) {
   k_krylov_direction<<<grid_for(n), kThreads, 0, st>>>(n, z, p, beta_den, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diag_max(cudaStream_t st, int64_t m, int64_t ldm, const T* M, double* part, unsigned* tickets,
+                            Scalars* sc) {
+  k_diag_max<T><<<grid_for(m, 4), kThreads, 0, st>>>(m, ldm, M, part, tickets, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_diag_max<double>(cudaStream_t, int64_t, int64_t, const double*, double*, unsigned*,
+                                             Scalars*);
+template cudaError_t launch_diag_max<float>(cudaStream_t, int64_t, int64_t, const float*, double*, unsigned*,
+                                            Scalars*);
+
+cudaError_t launch_absmax(cudaStream_t st, int64_t n, const double* v, double* part, unsigned* tickets, Scalars* sc,
+                          int slot) {
+  k_absmax<<<grid_for(n, 4), kThreads, 0, st>>>(n, v, part, tickets, sc, slot);
   return cudaGetLastError();
 }
 
