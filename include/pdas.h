@@ -82,6 +82,10 @@ typedef struct {
   double refine_be;        /* refinement also stops when the normwise backward error
                               ||Ax - M dy||_inf / (max_p M_pp ||dy||_inf + ||Ax||_inf) <= refine_be;
                               0 disables                                                  (1e-14) */
+  double drop_tol;         /* mixed forms in FP64: the factor is formed from the columns with
+                              D_j >= drop_tol max(D) only (refinement still applies the whole
+                              A D A'); 0 keeps every column                               (1e-10) */
+  double drop_keep;        /* ... but never fewer than drop_keep * m columns (the largest D_j)  (1.25) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */
@@ -97,6 +101,7 @@ typedef struct {
   int fp64_reason;      /* why a mixed form is in FP64: 0 not, 1 max(D)/min(D) rule,
                            2 low-precision factor not positive definite,
                            3 refinement did not reach its tolerance            */
+  int64_t factor_columns; /* columns of A that formed the factor (n unless dropped) */
 } pdas_iter_info;
 
 /* Stages of one iteration, for pdas_profile. */

@@ -33,6 +33,8 @@ class Options(ctypes.Structure):
         ("stall_theta", ctypes.c_double),
         ("stall_count", ctypes.c_int),
         ("refine_be", ctypes.c_double),
+        ("drop_tol", ctypes.c_double),
+        ("drop_keep", ctypes.c_double),
     ]
 
 
@@ -50,6 +52,7 @@ class IterInfo(ctypes.Structure):
         ("refine_sweeps", ctypes.c_int),
         ("used_fp64", ctypes.c_int),
         ("fp64_reason", ctypes.c_int),
+        ("factor_columns", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -47,6 +48,14 @@ struct pdas_ctx {
   TcWorkspace tc{};
   int cur_f64 = 1;     // the workspace matrix in use is M64
   int refactored = 0;  // a mixed form switched to FP64 for good
+  // column dropping for the FP64 factor of the mixed forms
+  void* akept = nullptr;        // m x n elements of A's dtype (lazily allocated)
+  double* dkept = nullptr;      // n
+  int* kidx = nullptr;          // n
+  std::vector<double> dhost;
+  std::vector<int> idx_host;
+  int64_t last_kept = 0;        // columns in the last FP64 factor of a mixed form
+  bool no_drop_once = false;    // the dropped factor failed: use every column this time
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
   char errmsg[256] = {0};
@@ -66,8 +75,6 @@ struct pdas_ctx {
 };
 
 namespace {
-
-constexpr double kRefineAccept = 1e-12;
 
 bool is_mixed(const pdas_ctx* h) { return h->opt.form != PDAS_FP64; }
 
@@ -210,15 +217,60 @@ pdas_status ensure_m64(pdas_ctx* h) {
 
 bool want_fp64(const pdas_ctx* h) { return !is_mixed(h) || h->refactored; }
 
+size_t dtype_size(int dt) { return dt == PDAS_A_F64 ? 8 : dt == PDAS_A_F32 ? 4 : 2; }
+
+// Columns for the FP64 factor of a mixed form: those with D_j >= drop_tol
+// max D, at least drop_keep m of them (the largest D_j).  Returns the count
+// (n = keep all; then idx is not built).
+pdas_status select_columns(pdas_ctx* h, int64_t* kept) {
+  const int64_t n = h->n;
+  *kept = n;
+  if (!(h->opt.drop_tol > 0) || h->no_drop_once) return PDAS_OK;
+  h->dhost.resize(n);
+  CK(cudaMemcpyAsync(h->dhost.data(), h->D, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  double dmax = 0.0;
+  for (double d : h->dhost) dmax = std::max(dmax, d);
+  double t = h->opt.drop_tol * dmax;
+  int64_t count = 0;
+  for (double d : h->dhost) count += d >= t;
+  int64_t kmin = (int64_t)std::ceil(h->opt.drop_keep * (double)h->m);
+  kmin = std::min(std::max<int64_t>(kmin, h->m), n);
+  if (count < kmin) {  // lower the threshold to the kmin-th largest D
+    std::vector<double> tmp(h->dhost);
+    std::nth_element(tmp.begin(), tmp.begin() + (kmin - 1), tmp.end(), std::greater<double>());
+    t = tmp[kmin - 1];
+  }
+  h->idx_host.clear();
+  for (int64_t j = 0; j < n; ++j)
+    if (h->dhost[j] >= t) h->idx_host.push_back((int)j);
+  const int64_t k = (int64_t)h->idx_host.size();
+  if (k >= n) return PDAS_OK;
+  if (!h->akept) CK(cudaMalloc(&h->akept, dtype_size(h->opt.a_dtype) * h->m * n));
+  if (!h->dkept) CK(cudaMalloc(&h->dkept, sizeof(double) * n));
+  if (!h->kidx) CK(cudaMalloc(&h->kidx, sizeof(int) * n));
+  CK(cudaMemcpyAsync(h->kidx, h->idx_host.data(), sizeof(int) * k, cudaMemcpyHostToDevice, h->st));
+  *kept = k;
+  return PDAS_OK;
+}
+
 // a3: the normal matrix in the current precision.
 pdas_status form_normal(pdas_ctx* h, const void* A) {
   if (want_fp64(h)) {
     pdas_status s = ensure_m64(h);
     if (s != PDAS_OK) return s;
     h->cur_f64 = 1;
+    int64_t kept = h->n;
+    if (is_mixed(h) && (s = select_columns(h, &kept)) != PDAS_OK) return s;
+    h->last_kept = kept;
     return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
       using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
-      KL(launch_syrk_simt<T>(h->st, h->m, h->n, (const T*)A, h->D, h->M64, nullptr, h->ldm, h->sc), 1);
+      if (kept < h->n) {
+        KL(launch_gather_columns<T>(h->st, h->m, h->n, (const T*)A, h->D, kept, h->kidx, (T*)h->akept, h->dkept), 1);
+        KL(launch_syrk_simt<T>(h->st, h->m, kept, (const T*)h->akept, h->dkept, h->M64, nullptr, h->ldm, h->sc), 1);
+      } else {
+        KL(launch_syrk_simt<T>(h->st, h->m, h->n, (const T*)A, h->D, h->M64, nullptr, h->ldm, h->sc), 1);
+      }
       return PDAS_OK;
     });
   }
@@ -365,7 +417,8 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
       h->switch_reason = 1;
     }
   }
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  h->no_drop_once = false;
+  for (int attempt = 0; attempt < 3; ++attempt) {
     STAGE(h, PDAS_STAGE_NORMAL);
     if ((st = form_normal(h, A)) != PDAS_OK) return st;
     STAGE_END(h);
@@ -392,8 +445,12 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
     st = device_status(h);
     if (st == PDAS_ERR_NOT_SPD) {  // low-precision factor broke down: FP64 from now on
       STAGE_END(h);
+      if (h->cur_f64) {
+        if (h->last_kept >= h->n) return st;  // the whole FP64 matrix is not SPD
+        h->no_drop_once = true;               // the factor from the kept columns was singular
+      }
+      if (!h->refactored) h->switch_reason = 2;
       h->refactored = 1;
-      h->switch_reason = 2;
       if ((st = reset_status(h)) != PDAS_OK) return st;
       KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
       if ((st = gemv(h, A, x, nullptr, h->r, 0)) != PDAS_OK) return st;
@@ -432,6 +489,7 @@ void fill_info(pdas_ctx* h, pdas_iter_info* info, bool stepped) {
   info->refine_resid = h->last_resid;
   info->used_fp64 = h->last_fp64;
   info->fp64_reason = (h->last_fp64 && is_mixed(h)) ? h->switch_reason : 0;
+  info->factor_columns = (h->last_fp64 && is_mixed(h)) ? h->last_kept : h->n;
   if (stepped) {
     info->psi = s.psi;
     info->theta = s.theta;
@@ -456,6 +514,8 @@ void pdas_default_options(pdas_options* opt) {
   opt->refine_tol = 1e-14;
   opt->refine_max = 40;
   opt->refine_be = 1e-14;
+  opt->drop_tol = 1e-10;
+  opt->drop_keep = 1.25;
   opt->dspread_refactor = 1e8;
   opt->stream = nullptr;
   opt->splits = 0;
@@ -491,7 +551,8 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (m < 1 || n <= m || m > (int64_t)1 << 20 || n > (int64_t)1 << 31) return PDAS_ERR_ARG;
   if (opt.form < PDAS_FP64 || opt.form > PDAS_FP32_IR) return PDAS_ERR_ARG;
   if (opt.a_dtype < PDAS_A_F64 || opt.a_dtype > PDAS_A_BF16) return PDAS_ERR_ARG;
-  if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) || opt.splits < 0 ||
+  if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) ||
+      !(opt.drop_tol >= 0) || !(opt.drop_keep >= 1.0) || opt.splits < 0 ||
       opt.splits > 3 ||
       opt.stall_count < 1 || !(opt.stall_theta >= 0))
     return PDAS_ERR_ARG;
@@ -574,6 +635,9 @@ void pdas_destroy(pdas_handle h) {
   for (double* p : vecs)
     if (p) cudaFree(p);
   if (h->M32) cudaFree(h->M32);
+  if (h->akept) cudaFree(h->akept);
+  if (h->dkept) cudaFree(h->dkept);
+  if (h->kidx) cudaFree(h->kidx);
   if (h->dinv64) cudaFree(h->dinv64);
   if (h->dinv32) cudaFree(h->dinv32);
   if (h->tickets) cudaFree(h->tickets);

@@ -105,6 +105,11 @@ cudaError_t launch_diag_max(cudaStream_t st, int64_t m, int64_t ldm, const T* M,
 cudaError_t launch_absmax(cudaStream_t st, int64_t n, const double* v, double* part, unsigned* tickets, Scalars* sc,
                           int slot);
 
+// Akept (m x k, row-major) = the columns idx[0..k) of A; Dkept = D[idx].
+template <typename T>
+cudaError_t launch_gather_columns(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, int64_t k,
+                                  const int* idx, T* Akept, double* Dkept);
+
 cudaError_t launch_convert_matrix(cudaStream_t st, int64_t m, int64_t ld_src, const void* src, int src_f64,
                                   int64_t ld_dst, void* dst, int dst_f64);
 

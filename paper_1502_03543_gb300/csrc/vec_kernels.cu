@@ -423,6 +423,18 @@ __global__ void __launch_bounds__(kThreads) k_absmax(int64_t n, const double* __
   }
 }
 
+template <typename T>
+__global__ void k_gather_columns(int64_t m, int64_t n, const T* __restrict__ A, const double* __restrict__ D, int64_t k,
+                                 const int* __restrict__ idx, T* __restrict__ Akept, double* __restrict__ Dkept) {
+  const int64_t total = m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / k, i = e % k;
+    const int64_t j = idx[i];
+    Akept[e] = A[p * n + j];
+    if (p == 0) Dkept[i] = D[j];
+  }
+}
+
 __global__ void k_krylov_update(int64_t n, const double* base, const double* __restrict__ p, double* out, int sign,
                                 const Scalars* sc) {
   if (failed(sc)) return;
@@ -539,6 +551,19 @@ template cudaError_t launch_diag_max<double>(cudaStream_t, int64_t, int64_t, con
                                              Scalars*);
 template cudaError_t launch_diag_max<float>(cudaStream_t, int64_t, int64_t, const float*, double*, unsigned*,
                                             Scalars*);
+
+template <typename T>
+cudaError_t launch_gather_columns(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, int64_t k,
+                                  const int* idx, T* Akept, double* Dkept) {
+  k_gather_columns<T><<<grid_for(m * k, 4) * 4, kThreads, 0, st>>>(m, n, A, D, k, idx, Akept, Dkept);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gather_columns<double>(cudaStream_t, int64_t, int64_t, const double*, const double*,
+                                                   int64_t, const int*, double*, double*);
+template cudaError_t launch_gather_columns<float>(cudaStream_t, int64_t, int64_t, const float*, const double*, int64_t,
+                                                  const int*, float*, double*);
+template cudaError_t launch_gather_columns<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const __nv_bfloat16*,
+                                                          const double*, int64_t, const int*, __nv_bfloat16*, double*);
 
 cudaError_t launch_absmax(cudaStream_t st, int64_t n, const double* v, double* part, unsigned* tickets, Scalars* sc,
                           int slot) {
