@@ -215,13 +215,24 @@ def run_normal_only(args):
     s = torch.from_numpy(lp.s0).cuda()
     opts = {"splits": args.splits} if args.splits else {}
     S = P.Solver(lp.m, lp.n, args.form, a_dtype, **opts)
+    factor = args.kernel == "factor"
     for _ in range(args.warmup):
         S.form_normal(A, x, s)
+        if factor:
+            S.factor()
     torch.cuda.synchronize()
+    fms = 0.0
     S.profile_enable(True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         S.form_normal(A, x, s)
+        if factor:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            S.factor()
+            e1.record()
+            torch.cuda.synchronize()
+            fms += e0.elapsed_time(e1)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     prof = S.profile_read()
@@ -229,8 +240,12 @@ def run_normal_only(args):
     ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
     splits = args.splits or 3
     roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, load_peaks())
-    print(json.dumps(dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits,
-                          ms_per_launch=ms, launches=prof["launches"], wall_s=wall, roofline=roof)))
+    out = dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits, ms_per_launch=ms,
+               launches=prof["launches"], wall_s=wall, roofline=roof)
+    if factor:
+        out["factor_ms"] = fms / args.steps
+        out["factor_tflops"] = lp.m ** 3 / 3 / (fms / args.steps * 1e-3) / 1e12
+    print(json.dumps(out))
 
 
 def run_ours(args):
@@ -390,14 +405,14 @@ def main():
     ap.add_argument("--dspread", type=float, default=None, help="dspread_refactor option (<= 0 disables)")
     ap.add_argument("--time-to-gap", action="store_true", help="also time one full solve to the gap tolerance")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["step", "normal"], default="step",
-                    help="normal: time only the normal-matrix stage (for profiles)")
+    ap.add_argument("--kernel", choices=["step", "normal", "factor"], default="step",
+                    help="normal: time only the normal-matrix stage; factor: also the Cholesky (for profiles)")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
+    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step":
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
-    elif args.kernel == "normal":
+    elif args.kernel in ("normal", "factor"):
         run_normal_only(args)
     else:
         run_ours(args)

@@ -73,7 +73,8 @@ typedef struct {
   double refine_tol;       /* refinement stops when ||Ax - M dy||_inf <= refine_tol ||Ax||_inf (1e-14) */
   int refine_max;          /* cap on refinement (preconditioned CG) steps per direction     (40) */
   double dspread_refactor; /* mixed forms: re-form and re-factor in FP64 for this and every later
-                              iteration once max(D)/min(D) exceeds this; <= 0 disables     (1e8) */
+                              iteration once max(D)/min(D) exceeds this (e.g. 1e8); <= 0 disables
+                              the rule, leaving the switch to factor or refinement failure    (0) */
   void* stream;            /* cudaStream_t for all work; NULL = the legacy default stream      */
   int splits;              /* tensor-core forms: number of low-precision terms of D.*A (1..3);
                               0 = form default (3)                                              */

@@ -516,7 +516,7 @@ void pdas_default_options(pdas_options* opt) {
   opt->refine_be = 1e-14;
   opt->drop_tol = 1e-10;
   opt->drop_keep = 1.25;
-  opt->dspread_refactor = 1e8;
+  opt->dspread_refactor = 0.0;
   opt->stream = nullptr;
   opt->splits = 0;
   opt->stall_theta = 1e-12;

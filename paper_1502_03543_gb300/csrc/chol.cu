@@ -30,30 +30,30 @@ __device__ __forceinline__ bool pivot_bad(T d) {
 }
 
 // Factor the kb x kb diagonal block held in shared memory (lower triangle).
+// Right-looking by columns with two barriers per column: every thread reads
+// the updated pivot d_c = Ld[c][c] itself (no thread writes the diagonal
+// during the loop; it is replaced by sqrt(d_c) at the end), scales column c
+// below the diagonal, then updates the trailing block.  Thread (ti, tj) =
+// (tid / 16, tid % 16) updates rows ti + 16 k and columns tj + 16 l.
 // Returns -1 or the local index of the failing pivot (same in all threads).
 template <typename T>
 __device__ int factor_diag(T (*Ld)[kTile + 1], int kb) {
-  __shared__ int fail;
-  if (threadIdx.x == 0) fail = -1;
-  __syncthreads();
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
   for (int c = 0; c < kb; ++c) {
-    if (threadIdx.x == 0) {
-      const T d = Ld[c][c];
-      if (pivot_bad(d)) fail = c;
-      else Ld[c][c] = sqrt(d);
+    __syncthreads();  // the trailing update of column c - 1 is complete
+    const T d = Ld[c][c];
+    if (pivot_bad(d)) return c;
+    const T rp = T(1) / sqrt(d);
+    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) Ld[r][c] *= rp;
+    __syncthreads();  // column c is scaled
+    for (int i = c + 1 + ti; i < kb; i += 16) {
+      const T lic = Ld[i][c];
+      for (int j = c + 1 + tj; j <= i; j += 16) Ld[i][j] -= lic * Ld[j][c];
     }
-    __syncthreads();
-    if (fail >= 0) return fail;
-    const T piv = Ld[c][c];
-    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) Ld[r][c] /= piv;
-    __syncthreads();
-    const int w = kb - c - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int i = c + 1 + e / w, j = c + 1 + e % w;
-      if (j <= i) Ld[i][j] -= Ld[i][c] * Ld[j][c];
-    }
-    __syncthreads();
   }
+  __syncthreads();
+  if (threadIdx.x < kb) Ld[threadIdx.x][threadIdx.x] = sqrt(Ld[threadIdx.x][threadIdx.x]);
+  __syncthreads();
   return -1;
 }
 
@@ -115,30 +115,65 @@ __global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm,
   }
 }
 
+// Trailing update C -= P P' over 128 x 128 lower tiles of the trailing matrix
+// (P = the kb <= 64 panel columns).  Every load is issued up front -- the C
+// tile straight into the accumulators, both 128 x kb panels into shared
+// memory (transposed, so the products read broadcasts and consecutive
+// words) -- then the kb rank-1 steps run from shared memory.  Thread
+// (tx, ty) owns rows ty + 16 i and columns tx + 16 j of the tile.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_chol_update(int64_t m, int64_t ldm, T* M, int64_t k0, int kb,
+constexpr size_t update_smem_bytes() {
+  return 2 * sizeof(T) * kTile * (kBig + 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k_chol_update(int64_t m, int64_t ldm, T* M, int64_t k0, int kb,
                                                           const Scalars* sc) {
-  __shared__ TileSmem<T, T> sm;
+  extern __shared__ __align__(16) unsigned char update_smem[];
+  T(*Ps)[kBig + 1] = reinterpret_cast<T(*)[kBig + 1]>(update_smem);
+  T(*Qs)[kBig + 1] = reinterpret_cast<T(*)[kBig + 1]>(update_smem + sizeof(T) * kTile * (kBig + 1));
   if (dev_failed(sc)) return;
   int64_t ti, tj;
   lower_tile(blockIdx.x, ti, tj);
   const int64_t s0 = k0 + kb;
-  const int64_t p0 = s0 + ti * kTile, q0 = s0 + tj * kTile;
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  // rows of the panel: P[i][c] = M[i][k0 + c], c < kb
-  tile_rank_k<T, T>(M + k0, ldm, p0, m, M + k0, ldm, q0, m, kb, nullptr, sm, acc);
+  const int64_t p0 = s0 + ti * kBig, q0 = s0 + tj * kBig;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[8][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     const int64_t p = p0 + ty + 16 * i;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 8; ++j) {
       const int64_t q = q0 + tx + 16 * j;
-      if (p < m && q <= p) M[p * ldm + q] -= acc[i][j];
+      acc[i][j] = (p < m && q <= p) ? M[p * ldm + q] : T(0);
+    }
+  }
+#pragma unroll 4
+  for (int e = threadIdx.x; e < kBig * kTile; e += kThreads) {
+    const int r = e / kTile, c = e % kTile;  // a warp reads 32 consecutive panel columns of one row
+    const bool cin = c < kb;
+    Ps[c][r] = (cin && p0 + r < m) ? M[(p0 + r) * ldm + k0 + c] : T(0);
+    Qs[c][r] = (cin && q0 + r < m) ? M[(q0 + r) * ldm + k0 + c] : T(0);
+  }
+  __syncthreads();
+  for (int c = 0; c < kb; ++c) {
+    T a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = Ps[c][ty + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = Qs[c][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t p = p0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t q = q0 + tx + 16 * j;
+      if (p < m && q <= p) M[p * ldm + q] = acc[i][j];
     }
   }
 }
@@ -334,12 +369,22 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
 
 template <typename T>
 cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Scalars* sc) {
+  static bool attr_set = false;  // per process; the attribute is per function
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)update_smem_bytes<T>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   for (int64_t k0 = 0; k0 < m; k0 += kTile) {
     const int kb = (int)(m - k0 < kTile ? m - k0 : kTile);
     const int64_t rest = m - k0 - kb;
     const int64_t t = (rest + kTile - 1) / kTile;
+    const int64_t tu = (rest + kBig - 1) / kBig;
     k_chol_panel<T><<<(unsigned)(1 + t), kThreads, 0, st>>>(m, ldm, M, dinv, k0, kb, sc);
-    if (t > 0) k_chol_update<T><<<(unsigned)(t * (t + 1) / 2), kThreads, 0, st>>>(m, ldm, M, k0, kb, sc);
+    if (tu > 0)
+      k_chol_update<T><<<(unsigned)(tu * (tu + 1) / 2), kThreads, update_smem_bytes<T>(), st>>>(m, ldm, M, k0, kb,
+                                                                                              sc);
   }
   return cudaGetLastError();
 }

@@ -36,6 +36,34 @@ __global__ void __launch_bounds__(kThreads) k_syrk_simt(int64_t m, int64_t n, co
   }
 }
 
+// FP32 normal matrix on 128 x 128 tiles (8 x 8 per thread).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_syrk_simt128(int64_t m, int64_t n, const T* __restrict__ A,
+                                                           const double* __restrict__ D, float* __restrict__ M,
+                                                           int64_t ldm, const Scalars* sc) {
+  __shared__ TileSmem128<float> sm;
+  if (*(volatile const int*)&sc->status != 0) return;
+  int64_t ti, tj;
+  lower_tile(blockIdx.x, ti, tj);
+  const int64_t p0 = ti * kBig, q0 = tj * kBig;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  tile128_rank_k<T, float>(A, n, p0, m, A, n, q0, m, n, D, sm, acc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t p = p0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t q = q0 + tx + 16 * j;
+      if (p < m && q <= p) M[p * ldm + q] = acc[i][j];
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -45,8 +73,10 @@ cudaError_t launch_syrk_simt(cudaStream_t st, int64_t m, int64_t n, const T* A, 
   const int64_t tiles = t * (t + 1) / 2;
   if (M64)
     k_syrk_simt<T, double><<<(unsigned)tiles, kThreads, 0, st>>>(m, n, A, D, M64, ldm, sc);
-  else
-    k_syrk_simt<T, float><<<(unsigned)tiles, kThreads, 0, st>>>(m, n, A, D, M32, ldm, sc);
+  else {
+    const int64_t tb = (m + kBig - 1) / kBig;
+    k_syrk_simt128<T><<<(unsigned)(tb * (tb + 1) / 2), kThreads, 0, st>>>(m, n, A, D, M32, ldm, sc);
+  }
   return cudaGetLastError();
 }
 

@@ -52,7 +52,8 @@ def test_host_side_validation_without_gpu(lib):
     L = N.lib()
     o = N.Options()
     L.pdas_default_options(ctypes.byref(o))
-    assert o.max_iter == 500 and o.refine_tol == 1e-14 and o.dspread_refactor == 1e8 and o.form == N.FP64
+    assert o.max_iter == 500 and o.refine_tol == 1e-14 and o.dspread_refactor == 0.0 and o.form == N.FP64
+    assert o.refine_be == 1e-14 and o.drop_tol == 1e-10 and o.drop_keep == 1.25 and o.refine_max == 40
     h = ctypes.c_void_p()
     # m < n and m >= 1 (Section I)
     assert L.pdas_create(10, 10, ctypes.byref(o), ctypes.byref(h)) == N.ERR_ARG

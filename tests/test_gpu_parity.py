@@ -396,7 +396,7 @@ def test_bf16_ir_solve_matches_oracle(pdas, seed):
 
 
 @pytest.mark.parametrize("dspread", [1e8, 0.0])
-def test_bf16_ir_solve_512x2048(pdas, dspread):
+def test_bf16_ir_solve_512x2048(pdas, dspread):  # with and without the max(D)/min(D) rule
     """A whole solve at 512 x 2048 (column-scaled BF16 A): the mixed form with
     FP64 refinement and the switch to FP64 reaches the oracle's optimal
     objective to 1e-8 in the same number of iterations, and keeps primal and
