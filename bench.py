@@ -168,6 +168,19 @@ def oracle_sample(lp, band_rows=64, chol_m=2048):
     return total, oracle.threads(), desc, {k: round(v, 3) for k, v in t.items()}
 
 
+def replica_rate(local_elapsed, steps, world, device="cpu"):
+    """Whole-job rate of N independent replicas: every rank ran `steps`
+    iterations; the job took as long as the slowest rank (max over ranks).
+    Returns (iterations per second over all ranks, max elapsed seconds)."""
+    import torch
+    t = torch.tensor([float(local_elapsed)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_max = float(t.item())
+    return steps * world / elapsed_max, elapsed_max
+
+
 def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -314,11 +327,7 @@ def run_ours(args):
     prof = S.profile_read()
     S.profile_enable(False)
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_max = float(t.item())
-    value = args.steps * world / elapsed_max
+    value, elapsed_max = replica_rate(elapsed, args.steps, world, device="cuda")
 
     # end to end through the public API with host buffers: per step the
     # iterate goes up from pinned host memory and comes back down.
@@ -340,10 +349,7 @@ def run_ours(args):
         os_.copy_(s, non_blocking=True)
         torch.cuda.synchronize()
     e2e_elapsed = time.perf_counter() - t0
-    t = torch.tensor([e2e_elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = args.steps * world / float(t.item())
+    e2e_value, _ = replica_rate(e2e_elapsed, args.steps, world, device="cuda")
     vec_bytes = 8 * (2 * n + m)
 
     ttg = None
