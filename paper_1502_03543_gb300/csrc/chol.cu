@@ -195,12 +195,13 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-// Thread 0 waits for flags[j] != 0; the block learns the outcome.
-__device__ bool block_wait(const int* flags, int64_t j, Scalars* sc) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
+// Lane 0 of the calling warp waits (bounded) for flags[j] != 0; the warp
+// learns the outcome.  The acquire by lane 0 and the warp barrier order the
+// warp's later loads of the solution block after the producer's release.
+__device__ bool warp_wait(const int* flags, int64_t j, Scalars* sc) {
+  int res = 1;
+  if ((threadIdx.x & 31) == 0) {
     const uint64_t t0 = global_ns();
-    int res = 1;
     while (ld_acquire(flags + j) == 0) {
       if (dev_failed(sc)) { res = 0; break; }
       if (global_ns() - t0 > kWaitLimitNs) {
@@ -208,12 +209,12 @@ __device__ bool block_wait(const int* flags, int64_t j, Scalars* sc) {
         res = 0;
         break;
       }
-      __nanosleep(64);
+      __nanosleep(32);
     }
-    ok = res;
   }
-  __syncthreads();
-  return ok != 0;
+  res = __shfl_sync(0xffffffffu, res, 0);
+  __syncwarp();
+  return res != 0;
 }
 
 // L z = v.  Block row b (64 rows): z_b = L_bb^{-1} (v_b - sum_{j<b} L_bj z_j).
@@ -226,7 +227,6 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
                                                          const T* __restrict__ dinv, const double* __restrict__ v,
                                                          double* z, int* flags, unsigned* ticket, Scalars* sc) {
   __shared__ T Ld[kTile][kTile + 1];
-  __shared__ T zj[kTile];
   __shared__ T acc[kTile];
   __shared__ T rcp[kTile];
   __shared__ int sbi;
@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
   T part[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) part[i] = T(0);
-  for (int64_t jb = 0; jb < b; ++jb) {
+  bool ok = true;
+  for (int64_t jb = 0; jb < b && ok; ++jb) {
     T l0[8], l1[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -254,12 +255,13 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
       l0[i] = r < rb ? row[lane] : T(0);
       l1[i] = r < rb ? row[lane + 32] : T(0);
     }
-    if (!block_wait(flags, jb, sc)) return;
-    if (threadIdx.x < kTile) zj[threadIdx.x] = (T)__ldcg(z + jb * kTile + threadIdx.x);
-    __syncthreads();
+    ok = warp_wait(flags, jb, sc);
+    if (!ok) break;
+    // lane l needs exactly z_{jb*64 + l} and z_{jb*64 + l + 32}
+    const T z0 = (T)__ldcg(z + jb * kTile + lane);
+    const T z1 = (T)__ldcg(z + jb * kTile + lane + 32);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) part[i] = fma(l0[i], zj[lane], fma(l1[i], zj[lane + 32], part[i]));
-    __syncthreads();
+    for (int i = 0; i < 8; ++i) part[i] = fma(l0[i], z0, fma(l1[i], z1, part[i]));
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
     const int r = 8 * w + i;
     if (lane == 0) acc[r] = r < rb ? (T)v[r0 + r] - t : T(0);
   }
-  __syncthreads();
+  if (__syncthreads_or(!ok)) return;  // a wait gave up: the status says why
   if (w == 0) {
     T a0 = acc[lane], a1 = acc[lane + 32];
     for (int c = 0; c < rb; ++c) {
@@ -297,7 +299,6 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
                                                            const double* __restrict__ zin, double* y, int* flags,
                                                            unsigned* ticket, Scalars* sc) {
   __shared__ T Ld[kTile][kTile + 1];
-  __shared__ T yk[kTile];
   __shared__ T red[8][kTile];
   __shared__ T rcp[kTile];
   __shared__ int sbi;
@@ -315,7 +316,8 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
   }
   if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
   T p0 = T(0), p1 = T(0);
-  for (int64_t kb = nblk - 1; kb > b; --kb) {
+  bool ok = true;
+  for (int64_t kb = nblk - 1; kb > b && ok; --kb) {
     const int64_t k0 = kb * kTile;
     const int kr = (int)(m - k0 < kTile ? m - k0 : kTile);
     T l0[8], l1[8];
@@ -326,19 +328,20 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
       l0[i] = (k < kr && lane < rb) ? row[lane] : T(0);
       l1[i] = (k < kr && lane + 32 < rb) ? row[lane + 32] : T(0);
     }
-    if (!block_wait(flags, kb, sc)) return;
-    if (threadIdx.x < kTile) yk[threadIdx.x] = threadIdx.x < kr ? (T)__ldcg(y + k0 + threadIdx.x) : T(0);
-    __syncthreads();
+    ok = warp_wait(flags, kb, sc);
+    if (!ok) break;
+    // warp w needs y_{k0 + 8w .. k0 + 8w + 7}: the same values in every lane
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      p0 = fma(l0[i], yk[8 * w + i], p0);
-      p1 = fma(l1[i], yk[8 * w + i], p1);
+      const int k = 8 * w + i;
+      const T yv = k < kr ? (T)__ldcg(y + k0 + k) : T(0);
+      p0 = fma(l0[i], yv, p0);
+      p1 = fma(l1[i], yv, p1);
     }
-    __syncthreads();
   }
   red[w][lane] = p0;
   red[w][lane + 32] = p1;
-  __syncthreads();
+  if (__syncthreads_or(!ok)) return;  // a wait gave up: the status says why
   if (w == 0) {
     T a0 = T(0), a1 = T(0);
 #pragma unroll

@@ -76,6 +76,24 @@ int grid_for(int64_t n, int per_thread = 1) {
 }
 
 // ---- vector loads of VEC consecutive elements of A, widened to double ----
+// FP32 -> FP64 widening by bit manipulation on the integer pipes: on GB300
+// the FP64 pipe is the bound of every pass over A, and a conversion
+// instruction would occupy it as long as the multiply-add does.  Exact for
+// every FP32 value: normal numbers move their exponent from bias 127 to
+// 1023, zeros keep their sign, Inf/NaN map to exponent 2047; subnormals take
+// the conversion instruction (they do not occur in practice).
+__device__ __forceinline__ double widen_bits(uint32_t u) {
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t mant = u & 0x7fffffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u) {
+    if (mant == 0u) return __longlong_as_double((long long)sign);
+    return (double)__uint_as_float(u);
+  }
+  const unsigned long long e64 = (e == 0xffu) ? 2047ull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)mant << 29)));
+}
+
 template <typename T>
 struct Vec;
 template <>
@@ -90,8 +108,8 @@ template <>
 struct Vec<float> {
   static constexpr int N = 4;
   __device__ static void load(const float* p, double* o) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    o[0] = widen_bits(v.x); o[1] = widen_bits(v.y); o[2] = widen_bits(v.z); o[3] = widen_bits(v.w);
   }
 };
 template <>
@@ -102,8 +120,8 @@ struct Vec<__nv_bfloat16> {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      o[2 * i] = (double)__uint_as_float(w[i] << 16);
-      o[2 * i + 1] = (double)__uint_as_float(w[i] & 0xffff0000u);
+      o[2 * i] = widen_bits(w[i] << 16);
+      o[2 * i + 1] = widen_bits(w[i] & 0xffff0000u);
     }
   }
 };

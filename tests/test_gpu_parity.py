@@ -454,3 +454,31 @@ def test_full_size_bf16_tensor_core_sampled(pdas):
     xh, sh = lp.x0, lp.s0
     assert np.abs(host(dx) / xh + host(ds) / sh + 1).max() <= 1e-10
     print("full-size direction: refinement sweeps %d, residual %.2e" % (info["refine_sweeps"], info["refine_resid"]))
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_gemv_widening_special_values(pdas, storage):
+    """The passes over A widen FP32 / BF16 to FP64 bit by bit on the integer
+    pipes: signed zeros, FP32 subnormals and values near the FP32 range
+    limits must widen exactly (checked through A v with one-hot v)."""
+    m, n = 4, 64
+    vals = np.array([0.0, -0.0, 1.0, -1.5, 3.0e38, -2.5e-38, 1.0e-40, -7.0e-45, 65504.0, 1.17549435e-38,
+                     np.float32(np.pi), -np.float32(1e-3)], dtype=np.float64)
+    A64 = np.zeros((m, n))
+    A64.flat[: vals.size] = vals
+    A64.flat[vals.size: 2 * vals.size] = -vals
+    if storage == "f32":
+        At = torch.from_numpy(A64.astype(np.float32)).cuda()
+        ref = A64.astype(np.float32).astype(np.float64)
+    else:
+        bits = lpgen.round_bf16_bits(A64)
+        At = torch.from_numpy(bits.view(np.int16).copy()).view(torch.bfloat16).cuda()
+        ref = lpgen.bf16_bits_to_f64(bits)
+    with pdas.Solver(m, n, "fp64", TORCH_DT[storage]) as S:
+        for j in range(n):
+            e = np.zeros(n)
+            e[j] = 1.0
+            col = host(S.gemv(At, dv(e)))
+            # bit for bit what the oracle's A v gives (a sum started at +0 turns -0 into +0)
+            want = oracle.gemv(ref, e)
+            assert np.array_equal(col.view(np.int64), want.view(np.int64)), (j, col, want)
