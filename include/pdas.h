@@ -103,6 +103,8 @@ typedef struct {
                            2 low-precision factor not positive definite,
                            3 refinement did not reach its tolerance            */
   int64_t factor_columns; /* columns of A that formed the factor (n unless dropped) */
+  int normal_form;      /* arithmetic of the normal matrix: 0 tcgen05 tensor cores, 1 FP32 SIMT,
+                           2 double-float (FP32 pairs, ~48-bit) on the FP32 pipes, 3 FP64        */
 } pdas_iter_info;
 
 /* Stages of one iteration, for pdas_profile. */

@@ -53,6 +53,7 @@ class IterInfo(ctypes.Structure):
         ("used_fp64", ctypes.c_int),
         ("fp64_reason", ctypes.c_int),
         ("factor_columns", ctypes.c_int64),
+        ("normal_form", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -56,6 +56,9 @@ struct pdas_ctx {
   std::vector<int> idx_host;
   int64_t last_kept = 0;        // columns in the last FP64 factor of a mixed form
   bool no_drop_once = false;    // the dropped factor failed: use every column this time
+  bool no_df_once = false;      // the double-float factor failed: form in FP64 this time
+  float2* d2 = nullptr;         // D as FP32 pairs (double-float formation)
+  int last_normal_form = 3;     // pdas_iter_info.normal_form of the last formation
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
   char errmsg[256] = {0};
@@ -263,18 +266,33 @@ pdas_status form_normal(pdas_ctx* h, const void* A) {
     int64_t kept = h->n;
     if (is_mixed(h) && (s = select_columns(h, &kept)) != PDAS_OK) return s;
     h->last_kept = kept;
+    // A mixed form whose A is exact in FP32 forms this matrix in double-float
+    // on the FP32 pipes (FP64 remains the fallback when that factor fails).
+    const bool df = is_mixed(h) && h->opt.a_dtype != PDAS_A_F64 && !h->no_df_once;
+    if (df && !h->d2) CK(cudaMalloc(&h->d2, sizeof(float2) * h->n));
+    h->last_normal_form = df ? 2 : 3;
     return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
       using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+      const T* Aop = (const T*)A;
+      const double* Dop = h->D;
+      int64_t cols = h->n;
       if (kept < h->n) {
         KL(launch_gather_columns<T>(h->st, h->m, h->n, (const T*)A, h->D, kept, h->kidx, (T*)h->akept, h->dkept), 1);
-        KL(launch_syrk_simt<T>(h->st, h->m, kept, (const T*)h->akept, h->dkept, h->M64, nullptr, h->ldm, h->sc), 1);
+        Aop = (const T*)h->akept;
+        Dop = h->dkept;
+        cols = kept;
+      }
+      if constexpr (std::is_same<T, double>::value) {
+        KL(launch_syrk_simt<T>(h->st, h->m, cols, Aop, Dop, h->M64, nullptr, h->ldm, h->sc), 1);
       } else {
-        KL(launch_syrk_simt<T>(h->st, h->m, h->n, (const T*)A, h->D, h->M64, nullptr, h->ldm, h->sc), 1);
+        if (df) KL(launch_syrk_df<T>(h->st, h->m, cols, Aop, Dop, h->d2, h->M64, h->ldm, h->sc), 2);
+        else KL(launch_syrk_simt<T>(h->st, h->m, cols, Aop, Dop, h->M64, nullptr, h->ldm, h->sc), 1);
       }
       return PDAS_OK;
     });
   }
   h->cur_f64 = 0;
+  h->last_normal_form = h->opt.form == PDAS_FP32_IR ? 1 : 0;
   if (h->opt.form == PDAS_FP32_IR) {
     return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
       using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
@@ -418,7 +436,8 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
     }
   }
   h->no_drop_once = false;
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  h->no_df_once = false;
+  for (int attempt = 0; attempt < 4; ++attempt) {
     STAGE(h, PDAS_STAGE_NORMAL);
     if ((st = form_normal(h, A)) != PDAS_OK) return st;
     STAGE_END(h);
@@ -446,8 +465,9 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
     if (st == PDAS_ERR_NOT_SPD) {  // low-precision factor broke down: FP64 from now on
       STAGE_END(h);
       if (h->cur_f64) {
-        if (h->last_kept >= h->n) return st;  // the whole FP64 matrix is not SPD
-        h->no_drop_once = true;               // the factor from the kept columns was singular
+        if (h->last_normal_form == 2) h->no_df_once = true;       // form it in FP64 next
+        else if (h->last_kept < h->n) h->no_drop_once = true;      // then from every column
+        else return st;                                            // the whole FP64 matrix is not SPD
       }
       if (!h->refactored) h->switch_reason = 2;
       h->refactored = 1;
@@ -490,6 +510,7 @@ void fill_info(pdas_ctx* h, pdas_iter_info* info, bool stepped) {
   info->used_fp64 = h->last_fp64;
   info->fp64_reason = (h->last_fp64 && is_mixed(h)) ? h->switch_reason : 0;
   info->factor_columns = (h->last_fp64 && is_mixed(h)) ? h->last_kept : h->n;
+  info->normal_form = h->last_normal_form;
   if (stepped) {
     info->psi = s.psi;
     info->theta = s.theta;
@@ -638,6 +659,7 @@ void pdas_destroy(pdas_handle h) {
   if (h->akept) cudaFree(h->akept);
   if (h->dkept) cudaFree(h->dkept);
   if (h->kidx) cudaFree(h->kidx);
+  if (h->d2) cudaFree(h->d2);
   if (h->dinv64) cudaFree(h->dinv64);
   if (h->dinv32) cudaFree(h->dinv32);
   if (h->tickets) cudaFree(h->tickets);

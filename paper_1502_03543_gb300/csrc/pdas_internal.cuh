@@ -105,6 +105,12 @@ cudaError_t launch_diag_max(cudaStream_t st, int64_t m, int64_t ldm, const T* M,
 cudaError_t launch_absmax(cudaStream_t st, int64_t n, const double* v, double* part, unsigned* tickets, Scalars* sc,
                           int slot);
 
+// Lower triangle of M64 = A D A' in double-float on the FP32 pipes (A exact
+// in FP32: float or BF16 storage); D2 (n float2) receives D as hi + lo.
+template <typename T>
+cudaError_t launch_syrk_df(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, float2* D2,
+                           double* M64, int64_t ldm, const Scalars* sc);
+
 // Akept (m x k, row-major) = the columns idx[0..k) of A; Dkept = D[idx].
 template <typename T>
 cudaError_t launch_gather_columns(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, int64_t k,

@@ -482,3 +482,55 @@ def test_gemv_widening_special_values(pdas, storage):
             # bit for bit what the oracle's A v gives (a sum started at +0 turns -0 into +0)
             want = oracle.gemv(ref, e)
             assert np.array_equal(col.view(np.int64), want.view(np.int64)), (j, col, want)
+
+
+# ---------------------------------------------------------------------------
+# the FP64 tier of a mixed form: double-float normal matrix, dropped columns
+
+@pytest.mark.parametrize("storage", ["bf16", "f32"])
+@pytest.mark.parametrize("m,n", [(5, 37), (130, 520), (257, 1024)])
+def test_double_float_normal_matrix(pdas, storage, m, n):
+    """Once a mixed form runs an FP64 factor, M is formed in double-float on
+    the FP32 pipes (A exact in FP32): D.*A to ~2^-48 and TwoSum accumulation,
+    so |M_df - M| <= 2 n 2^-46 (|A| D |A|') elementwise."""
+    lp = lpgen.generate(m, n, seed=m + 3, storage=storage, scaled=True)
+    rng = np.random.default_rng(13)
+    x, s = rng.uniform(0.01, 10, n), rng.uniform(0.01, 10, n)
+    form = "bf16_ir" if storage == "bf16" else "fp32_ir"
+    with pdas.Solver(m, n, form, TORCH_DT[storage], dspread_refactor=1e-300) as S:
+        A = dev_A(lp)
+        _, _, _, info = S.direction(A, dv(x), dv(s))  # the rule switches to the FP64 tier at once
+        assert info["used_fp64"] == 1 and info["fp64_reason"] == 1 and info["normal_form"] == 2
+        S.form_normal(A, dv(x), dv(s))
+        M = host(S.copy_matrix())
+    D = oracle.scaling(x, s)
+    ref = oracle.normal_matrix(lp.A64, D)
+    low = np.tril_indices(m)
+    bound = 2 * n * 2.0 ** -46 * ((np.abs(lp.A64) * D) @ np.abs(lp.A64).T)
+    assert np.all(np.abs(M[low] - ref[low]) <= bound[low])
+    assert scaled_error(M, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f32"])
+def test_fp64_tier_whole_solve(pdas, storage):
+    """A mixed form forced into its FP64 tier from the first iteration
+    (double-float M of the significant columns, FP64 factor, PCG on the whole
+    M) reaches the oracle's objective in the oracle's number of iterations."""
+    lp = lpgen.generate(256, 1024, seed=21, storage=storage, scaled=True)
+    ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+    form = "bf16_ir" if storage == "bf16" else "fp32_ir"
+    cols = []
+    with pdas.Solver(lp.m, lp.n, form, TORCH_DT[storage], dspread_refactor=1e-300) as S:
+        for k in range(ref["iters"]):
+            st, info = S.step(A, b, c, x, y, s, alpha=0.95)
+            assert info["used_fp64"] == 1
+            cols.append(info["factor_columns"])
+    assert info["rel_gap"] < 1e-8
+    obj_ref = float(lp.c @ ref["x"])
+    assert abs(float(lp.c @ host(x)) - obj_ref) <= 1e-8 * abs(obj_ref)
+    assert min(cols) < lp.n  # columns were dropped late in the solve
+    xh, yh, sh = host(x), host(y), host(s)
+    assert np.linalg.norm(lp.A64 @ xh - lp.b) <= 1e-9 * np.linalg.norm(lp.b)
+    assert np.linalg.norm(lp.A64.T @ yh + sh - lp.c) <= 1e-12 * np.linalg.norm(lp.c)
