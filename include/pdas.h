@@ -154,9 +154,21 @@ pdas_status pdas_step(pdas_handle h, const void* A, const double* b, const doubl
 pdas_status pdas_solve(pdas_handle h, const void* A, const double* b, const double* c, double* x, double* y,
                        double* s, double alpha, double tol, int* iters_out, double* rel_gap_out);
 
-/* Sensitivities of a loss L(x*) at the final iterate of the last solve.
- * Not available in this build: returns PDAS_ERR_UNSUPPORTED. */
-pdas_status pdas_backward(pdas_handle h, const double* dL_dx, double* dL_dA, double* dL_db, double* dL_dc);
+/* Sensitivities of a loss L(x*) at a final iterate (x, y, s) of the
+ * algorithm: implicit differentiation of F = [A x - b; A'y + s - c; X s - sigma]
+ * = 0 with sigma = x.*s held fixed.  The adjoint of the Newton matrix of
+ * Eq. (3) reduces, like the direction (Eq. 4), to the normal equations:
+ *     (A D A') la = A D g,   lb = D (A' la - g),   D = X S^{-1},  g = dL/dx,
+ * solved by FP64 conjugate gradients on A D A' (matrix-free) preconditioned
+ * by the handle's last factor (so a pdas_step or pdas_solve must come first),
+ * then refined on the full adjoint system with FP64 residuals (lb would
+ * otherwise lose accuracy where D is large).
+ * Outputs: dL_db (m) = la, dL_dc (n) = lb, dL_dA (m x n row-major, may be
+ * NULL) = -(la x' + y lb').  A: m x n (a_dtype); x, y, s, dL_dx: device
+ * doubles.  PDAS_ERR_ARG without a factor; PDAS_ERR_NOT_SPD if the
+ * preconditioned solve breaks down. */
+pdas_status pdas_backward(pdas_handle h, const void* A, const double* x, const double* y, const double* s,
+                          const double* dL_dx, double* dL_dA, double* dL_db, double* dL_dc);
 
 /* Releases the workspace and the handle.  NULL is ignored. */
 void pdas_destroy(pdas_handle h);

@@ -15,7 +15,7 @@ import torch
 
 from . import _native as N
 
-__all__ = ["Solver", "PdasError", "FORMS", "A_DTYPES"]
+__all__ = ["Solver", "PdasError", "FORMS", "A_DTYPES", "solve_lp"]
 
 FORMS = {"fp64": N.FP64, "tf32_ir": N.TF32_IR, "bf16_ir": N.BF16_IR, "fp32_ir": N.FP32_IR}
 A_DTYPES = {torch.float64: N.A_F64, torch.float32: N.A_F32, torch.bfloat16: N.A_BF16}
@@ -163,13 +163,17 @@ class Solver:
         self._check(st, "pdas_direction")
         return dx, dy, ds, info.as_dict()
 
-    def backward(self, dL_dx):
-        dA = torch.empty(self.m * self.n, dtype=torch.float64, device=dL_dx.device)
-        db = torch.empty(self.m, dtype=torch.float64, device=dL_dx.device)
-        dc = torch.empty(self.n, dtype=torch.float64, device=dL_dx.device)
-        st = N.lib().pdas_backward(self._h, self._vn(dL_dx, "dL_dx"), _ptr(dA), _ptr(db), _ptr(dc))
+    def backward(self, A, x, y, s, dL_dx, want_dA=True):
+        """Sensitivities of L(x*) at the final iterate (x, y, s): returns
+        (dL/dA or None, dL/db, dL/dc), FP64 (pdas_backward)."""
+        dev = dL_dx.device
+        dA = torch.empty(self.m * self.n, dtype=torch.float64, device=dev) if want_dA else None
+        db = torch.empty(self.m, dtype=torch.float64, device=dev)
+        dc = torch.empty(self.n, dtype=torch.float64, device=dev)
+        st = N.lib().pdas_backward(self._h, self._A(A), self._vn(x, "x"), self._vm(y, "y"), self._vn(s, "s"),
+                                   self._vn(dL_dx, "dL_dx"), _ptr(dA) if want_dA else None, _ptr(db), _ptr(dc))
         self._check(st, "pdas_backward")
-        return dA.view(self.m, self.n), db, dc
+        return (dA.view(self.m, self.n) if want_dA else None), db, dc
 
     # -- components ----------------------------------------------------------
     def form_normal(self, A, x, s):
@@ -209,3 +213,34 @@ class Solver:
         out = torch.empty(self.n, dtype=torch.float64, device=u.device)
         self._check(N.lib().pdas_gemv_t(self._h, self._A(A), self._vm(u, "u"), _ptr(out)), "pdas_gemv_t")
         return out
+
+
+class _LPSolve(torch.autograd.Function):
+    """x* = PDAS solution of min c'x s.t. Ax = b, x >= 0 from (x0, y0, s0);
+    its backward is pdas_backward (implicit differentiation at the final
+    iterate with x.*s held fixed)."""
+
+    @staticmethod
+    def forward(ctx, A, b, c, x0, y0, s0, solver, alpha, tol):
+        x, y, s = x0.detach().clone(), y0.detach().clone(), s0.detach().clone()
+        out = solver.solve(A.detach(), b.detach(), c.detach(), x, y, s, alpha=alpha, tol=tol)
+        if out["status"] < 0:
+            raise PdasError(out["status"], "pdas_solve")
+        ctx.solver = solver
+        ctx.save_for_backward(A, x, y, s)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        A, x, y, s = ctx.saved_tensors
+        dA, db, dc = ctx.solver.backward(A.detach(), x, y, s, gx.detach().contiguous().double(),
+                                         want_dA=ctx.needs_input_grad[0])
+        if dA is not None:
+            dA = dA.to(A.dtype)
+        return dA, db, dc, None, None, None, None, None, None
+
+
+def solve_lp(A, b, c, x0, y0, s0, solver, alpha=0.95, tol=1e-8):
+    """Differentiable LP solve through libpdas: returns x*; gradients with
+    respect to A, b, c come from the adjoint at the final iterate."""
+    return _LPSolve.apply(A, b, c, x0, y0, s0, solver, alpha, tol)

@@ -82,7 +82,7 @@ SIGNATURES = {
     "pdas_create": ([_I64, _I64, ctypes.POINTER(Options), ctypes.POINTER(_H)], _I),
     "pdas_step": ([_H, _P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(IterInfo)], _I),
     "pdas_solve": ([_H, _P, _P, _P, _P, _P, _P, _D, _D, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
-    "pdas_backward": ([_H, _P, _P, _P, _P], _I),
+    "pdas_backward": ([_H, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "pdas_destroy": ([_H], None),
     "pdas_status_str": ([_I], ctypes.c_char_p),
     "pdas_last_error_index": ([_H], _I64),

@@ -59,6 +59,8 @@ struct pdas_ctx {
   bool no_df_once = false;      // the double-float factor failed: form in FP64 this time
   float2* d2 = nullptr;         // D as FP32 pairs (double-float formation)
   int last_normal_form = 3;     // pdas_iter_info.normal_form of the last formation
+  bool have_factor = false;     // a factor from a previous step is in the workspace
+  double* adj = nullptr;        // adjoint vectors (5 n + m), lazily allocated
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
   char errmsg[256] = {0};
@@ -448,6 +450,7 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
     STAGE(h, PDAS_STAGE_FACTOR);
     if ((st = factor(h)) != PDAS_OK) return st;
     STAGE_END(h);
+    h->have_factor = true;  // (a failed factor is reported below and retried)
     STAGE(h, PDAS_STAGE_SOLVE);
     if ((st = factor_solve(h, h->r, h->dy)) != PDAS_OK) return st;
     h->last_fp64 = h->cur_f64;
@@ -660,6 +663,7 @@ void pdas_destroy(pdas_handle h) {
   if (h->dkept) cudaFree(h->dkept);
   if (h->kidx) cudaFree(h->kidx);
   if (h->d2) cudaFree(h->d2);
+  if (h->adj) cudaFree(h->adj);
   if (h->dinv64) cudaFree(h->dinv64);
   if (h->dinv32) cudaFree(h->dinv32);
   if (h->tickets) cudaFree(h->tickets);
@@ -784,9 +788,68 @@ pdas_status pdas_solve(pdas_handle h, const void* A, const double* b, const doub
   return result;
 }
 
-pdas_status pdas_backward(pdas_handle h, const double* dL_dx, double* dL_dA, double* dL_db, double* dL_dc) {
-  (void)h; (void)dL_dx; (void)dL_dA; (void)dL_db; (void)dL_dc;
-  return PDAS_ERR_UNSUPPORTED;
+pdas_status pdas_backward(pdas_handle h, const void* A, const double* x, const double* y, const double* s,
+                          const double* dL_dx, double* dL_dA, double* dL_db, double* dL_dc) {
+  if (!h || check_vec_args(A, x, s) != PDAS_OK || !y || !dL_dx || !dL_db || !dL_dc) return PDAS_ERR_ARG;
+  if (!h->have_factor) return PDAS_ERR_ARG;  // the preconditioner comes from a previous step
+  h->err_index = -1;
+  const int64_t m = h->m, n = h->n;
+  pdas_status st = reset_status(h);
+  if (st != PDAS_OK) return st;
+  if (!h->adj) CK(cudaMalloc(&h->adj, sizeof(double) * (5 * n + m)));
+  double* lb = h->adj;      // dL/dc
+  double* lc = lb + n;      // multiplier of X s = sigma
+  double* wt = lc + n;      // A' la
+  double* r1 = wt + n;      // residual of A' la + S lc = g
+  double* r3 = r1 + n;      // residual of lb + X lc = 0
+  double* la = r3 + n;      // dL/db (m)
+  // The preconditioner is the factor of the previous iterate's D: allow the
+  // conjugate gradients four times the usual number of steps.
+  const int cap = h->opt.refine_max;
+  auto solve_normal = [&](int* ok) -> pdas_status {  // (A D A') dy = h->r, w = A' dy
+    pdas_status t = factor_solve(h, h->r, h->dy);
+    if (t != PDAS_OK) return t;
+    h->opt.refine_max = 4 * cap;
+    t = refine(h, A, ok);
+    h->opt.refine_max = cap;
+    return t;
+  };
+  KL(launch_scaling(h->st, n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+  // max_p M_pp at this D for the backward-error test of the refinement (the
+  // matrix itself is not formed: the preconditioner is the last factor);
+  // ldm = 0 makes the diagonal reduction read the m-vector M_pp.
+  st = with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    KL(launch_normal_diag<T>(h->st, m, n, (const T*)A, h->D, h->kq, h->sc), 1);
+    return PDAS_OK;
+  });
+  if (st != PDAS_OK) return st;
+  KL(launch_diag_max<double>(h->st, m, 0, h->kq, h->part, h->tickets, h->sc), 1);
+  // reduced solve: (A D A') la = A (D g); lb = D (A' la - g); lc = -lb / x
+  KL(launch_scale_vec(h->st, n, h->D, dL_dx, h->u, h->sc), 1);
+  if ((st = gemv(h, A, h->u, nullptr, h->r, 0)) != PDAS_OK) return st;
+  int ok = 0;
+  if ((st = solve_normal(&ok)) != PDAS_OK) return st;
+  if (!ok) return PDAS_ERR_NOT_SPD;
+  CK(cudaMemcpyAsync(la, h->dy, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  KL(launch_adjoint_init(h->st, n, h->D, h->w, dL_dx, x, lb, lc, wt, h->sc), 1);
+  // lb = D (A' la - g) cancels where D is large; two steps of refinement on
+  // the full adjoint system [A' 0 S; 0 A 0; 0 I X] (la, lb, lc) = (g, 0, 0)
+  // with FP64 residuals recover it.  Each correction solves the same
+  // normal equations: (A D A') da = A (D r1 - r3 - lb).
+  for (int it = 0; it < 2; ++it) {
+    KL(launch_adjoint_resid(h->st, n, h->D, dL_dx, x, s, wt, lb, lc, r1, r3, h->u, h->sc), 1);
+    if ((st = gemv(h, A, h->u, nullptr, h->r, 0)) != PDAS_OK) return st;
+    if ((st = solve_normal(&ok)) != PDAS_OK) return st;
+    if (!ok) break;  // the correction is at the rounding level: keep what we have
+    KL(launch_axpy(h->st, m, 1.0, h->dy, la, h->sc), 1);
+    KL(launch_adjoint_update(h->st, n, h->D, h->w, x, r1, r3, lb, lc, wt, h->sc), 1);
+  }
+  CK(cudaMemcpyAsync(dL_db, la, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(dL_dc, lb, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  if (dL_dA) KL(launch_adjoint_dA(h->st, m, n, la, x, y, lb, dL_dA, h->sc), 1);
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  return device_status(h);
 }
 
 // ---- components ------------------------------------------------------------
@@ -830,7 +893,9 @@ pdas_status pdas_factor(pdas_handle h) {
   if (st != PDAS_OK) return st;
   if ((st = factor(h)) != PDAS_OK) return st;
   if ((st = read_scalars(h)) != PDAS_OK) return st;
-  return device_status(h);
+  st = device_status(h);
+  h->have_factor = st == PDAS_OK;
+  return st;
 }
 
 pdas_status pdas_factor_solve(pdas_handle h, const double* rhs, double* out) {

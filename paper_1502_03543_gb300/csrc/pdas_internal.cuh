@@ -116,6 +116,30 @@ template <typename T>
 cudaError_t launch_gather_columns(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, int64_t k,
                                   const int* idx, T* Akept, double* Dkept);
 
+// Adjoint helpers: u = D .* g;  lb = D .* (w - g);  dA = -(la x' + y lb').
+// out_p = (A D A')_pp without forming the matrix (m outputs).
+template <typename T>
+cudaError_t launch_normal_diag(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, double* out,
+                               const Scalars* sc);
+cudaError_t launch_scale_vec(cudaStream_t st, int64_t n, const double* D, const double* g, double* u,
+                             const Scalars* sc);
+cudaError_t launch_adjoint_lb(cudaStream_t st, int64_t n, const double* D, const double* w, const double* g,
+                              double* lb, const Scalars* sc);
+// Refinement of the full adjoint system (see pdas_backward):
+//   init:   lb = D (w - g), lc = -lb / x, wt = w
+//   resid:  r1 = g - wt - s.*lc, r3 = -lb - x.*lc, t = D r1 - r3 - lb
+//   update: db = D (w - r1) + r3, dc = (r3 - db) / x; lb += db, lc += dc, wt += w
+cudaError_t launch_adjoint_init(cudaStream_t st, int64_t n, const double* D, const double* w, const double* g,
+                                const double* x, double* lb, double* lc, double* wt, const Scalars* sc);
+cudaError_t launch_adjoint_resid(cudaStream_t st, int64_t n, const double* D, const double* g, const double* x,
+                                 const double* s, const double* wt, const double* lb, const double* lc, double* r1,
+                                 double* r3, double* t, const Scalars* sc);
+cudaError_t launch_adjoint_update(cudaStream_t st, int64_t n, const double* D, const double* w, const double* x,
+                                  const double* r1, const double* r3, double* lb, double* lc, double* wt,
+                                  const Scalars* sc);
+cudaError_t launch_adjoint_dA(cudaStream_t st, int64_t m, int64_t n, const double* la, const double* x,
+                              const double* y, const double* lb, double* dA, const Scalars* sc);
+
 cudaError_t launch_convert_matrix(cudaStream_t st, int64_t m, int64_t ld_src, const void* src, int src_f64,
                                   int64_t ld_dst, void* dst, int dst_f64);
 

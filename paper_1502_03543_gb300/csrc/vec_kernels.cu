@@ -453,6 +453,89 @@ __global__ void k_gather_columns(int64_t m, int64_t n, const T* __restrict__ A, 
   }
 }
 
+// out_p = sum_j A_pj^2 D_j = (A D A')_pp, one block per row (fixed order).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_normal_diag(int64_t m, int64_t n, const T* __restrict__ A,
+                                                          const double* __restrict__ D, double* out,
+                                                          const Scalars* sc) {
+  __shared__ double sm[32];
+  if (failed(sc)) return;
+  for (int64_t p = blockIdx.x; p < m; p += gridDim.x) {
+    const T* row = A + p * n;
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double a = widen(row[j]);
+      acc = fma(a * a, D[j], acc);
+    }
+    acc = block_reduce<0>(acc, sm);
+    if (threadIdx.x == 0) out[p] = acc;
+  }
+}
+
+__global__ void k_scale_vec(int64_t n, const double* __restrict__ D, const double* __restrict__ g, double* u,
+                            const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    u[j] = D[j] * g[j];
+}
+
+__global__ void k_adjoint_lb(int64_t n, const double* __restrict__ D, const double* __restrict__ w,
+                             const double* __restrict__ g, double* lb, const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    lb[j] = D[j] * (w[j] - g[j]);
+}
+
+__global__ void k_adjoint_init(int64_t n, const double* __restrict__ D, const double* __restrict__ w,
+                               const double* __restrict__ g, const double* __restrict__ x, double* lb, double* lc,
+                               double* wt, const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double b = D[j] * (w[j] - g[j]);
+    lb[j] = b;
+    lc[j] = -b / x[j];
+    wt[j] = w[j];
+  }
+}
+
+__global__ void k_adjoint_resid(int64_t n, const double* __restrict__ D, const double* __restrict__ g,
+                                const double* __restrict__ x, const double* __restrict__ s,
+                                const double* __restrict__ wt, const double* __restrict__ lb,
+                                const double* __restrict__ lc, double* r1, double* r3, double* t, const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double a = g[j] - wt[j] - s[j] * lc[j];
+    const double c = -lb[j] - x[j] * lc[j];
+    r1[j] = a;
+    r3[j] = c;
+    t[j] = D[j] * a - c - lb[j];
+  }
+}
+
+__global__ void k_adjoint_update(int64_t n, const double* __restrict__ D, const double* __restrict__ w,
+                                 const double* __restrict__ x, const double* __restrict__ r1,
+                                 const double* __restrict__ r3, double* lb, double* lc, double* wt,
+                                 const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double db = D[j] * (w[j] - r1[j]) + r3[j];
+    lb[j] += db;
+    lc[j] += (r3[j] - db) / x[j];
+    wt[j] += w[j];
+  }
+}
+
+__global__ void k_adjoint_dA(int64_t m, int64_t n, const double* __restrict__ la, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ lb, double* dA,
+                             const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t p = blockIdx.y; p < m; p += gridDim.y) {
+    const double lp = la[p], yp = y[p];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+      dA[p * n + j] = -(lp * x[j] + yp * lb[j]);
+  }
+}
+
 __global__ void k_krylov_update(int64_t n, const double* base, const double* __restrict__ p, double* out, int sign,
                                 const Scalars* sc) {
   if (failed(sc)) return;
@@ -586,6 +669,59 @@ template cudaError_t launch_gather_columns<__nv_bfloat16>(cudaStream_t, int64_t,
 cudaError_t launch_absmax(cudaStream_t st, int64_t n, const double* v, double* part, unsigned* tickets, Scalars* sc,
                           int slot) {
   k_absmax<<<grid_for(n, 4), kThreads, 0, st>>>(n, v, part, tickets, sc, slot);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_normal_diag(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* D, double* out,
+                               const Scalars* sc) {
+  k_normal_diag<T><<<(unsigned)(m < 4 * 1184 ? m : 4 * 1184), kThreads, 0, st>>>(m, n, A, D, out, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_normal_diag<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, double*,
+                                                const Scalars*);
+template cudaError_t launch_normal_diag<float>(cudaStream_t, int64_t, int64_t, const float*, const double*, double*,
+                                               const Scalars*);
+template cudaError_t launch_normal_diag<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const __nv_bfloat16*,
+                                                       const double*, double*, const Scalars*);
+
+cudaError_t launch_scale_vec(cudaStream_t st, int64_t n, const double* D, const double* g, double* u,
+                             const Scalars* sc) {
+  k_scale_vec<<<grid_for(n), kThreads, 0, st>>>(n, D, g, u, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_lb(cudaStream_t st, int64_t n, const double* D, const double* w, const double* g,
+                              double* lb, const Scalars* sc) {
+  k_adjoint_lb<<<grid_for(n), kThreads, 0, st>>>(n, D, w, g, lb, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(cudaStream_t st, int64_t n, const double* D, const double* w, const double* g,
+                                const double* x, double* lb, double* lc, double* wt, const Scalars* sc) {
+  k_adjoint_init<<<grid_for(n), kThreads, 0, st>>>(n, D, w, g, x, lb, lc, wt, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_resid(cudaStream_t st, int64_t n, const double* D, const double* g, const double* x,
+                                 const double* s, const double* wt, const double* lb, const double* lc, double* r1,
+                                 double* r3, double* t, const Scalars* sc) {
+  k_adjoint_resid<<<grid_for(n), kThreads, 0, st>>>(n, D, g, x, s, wt, lb, lc, r1, r3, t, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_update(cudaStream_t st, int64_t n, const double* D, const double* w, const double* x,
+                                  const double* r1, const double* r3, double* lb, double* lc, double* wt,
+                                  const Scalars* sc) {
+  k_adjoint_update<<<grid_for(n), kThreads, 0, st>>>(n, D, w, x, r1, r3, lb, lc, wt, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_dA(cudaStream_t st, int64_t m, int64_t n, const double* la, const double* x,
+                              const double* y, const double* lb, double* dA, const Scalars* sc) {
+  dim3 grid((unsigned)((n + kThreads - 1) / kThreads < 64 ? (n + kThreads - 1) / kThreads : 64),
+            (unsigned)(m < 4096 ? m : 4096));
+  k_adjoint_dA<<<grid, kThreads, 0, st>>>(m, n, la, x, y, lb, dA, sc);
   return cudaGetLastError();
 }
 
