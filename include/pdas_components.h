@@ -55,6 +55,18 @@ pdas_status pdas_gemv(pdas_handle h, const void* A, const double* v, double* out
 /* out (n) = A' u (m), FP64 accumulation: the product behind ds = -A' dy. */
 pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* out);
 
+/* Host-only, no GPU needed: the task order of the single-launch tile
+ * Cholesky behind pdas_factor for FP32 factors (128 x 128 tiles, nb =
+ * ceil(m / 128) tile rows), scheduled for nproc resident CTAs.  Writes
+ * min(cap, count) tasks to out as int32 quadruples {kind, i, l, k}:
+ * kind 0 = last update of diagonal tile (l, l) by tile column k = l - 1 (none
+ * for l = 0), then its factorisation (i = l); 1 = last update of tile (i, l),
+ * i > l, then its triangular solve against L_ll; 2 = update of tile (i, l) by
+ * tile columns i and l of step k <= l - 2.  Returns the count (0 for m <= 0);
+ * out may be NULL to query it.  Every task comes after the tasks it waits
+ * for, which is what makes the launch deadlock-free. */
+int64_t pdas_chol_tile_tasks(int64_t m, int32_t nproc, int32_t* out, int64_t cap);
+
 /* Size of the fixed device scratch behind pdas_gemv_t_noalloc: 8 MiB. */
 #define PDAS_NOALLOC_SCRATCH_BYTES (8u << 20)
 

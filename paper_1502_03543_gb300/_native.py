@@ -96,6 +96,7 @@ SIGNATURES = {
     "pdas_gemv": ([_H, _P, _P, _P], _I),
     "pdas_gemv_t": ([_H, _P, _P, _P], _I),
     "pdas_gemv_t_noalloc": ([_I64, _I64, _I, _P, _P, _P, _P], _I),
+    "pdas_chol_tile_tasks": ([_I64, _I, _P, _I64], _I64),
     "pdas_profile_enable": ([_H, _I], _I),
     "pdas_profile_read": ([_H, ctypes.POINTER(Profile)], _I),
 }

@@ -61,6 +61,10 @@ struct pdas_ctx {
   int last_normal_form = 3;     // pdas_iter_info.normal_form of the last formation
   bool have_factor = false;     // a factor from a previous step is in the workspace
   double* adj = nullptr;        // adjoint vectors (5 n + m), lazily allocated
+  int4* chol_tasks = nullptr;   // task list of the tile Cholesky (FP32 factor)
+  int chol_ntasks = 0;
+  int* chol_state = nullptr;    // per-tile counters of the tile Cholesky
+  float* uinv32 = nullptr;      // L_ll^{-T} of every diagonal tile of the FP32 tile factor
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
   char errmsg[256] = {0};
@@ -315,7 +319,11 @@ pdas_status form_normal(pdas_ctx* h, const void* A) {
 
 pdas_status factor(pdas_ctx* h) {
   if (h->cur_f64) KL(cholesky<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->sc), chol_launches(h->m));
-  else KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->sc), chol_launches(h->m));
+  else if (h->chol_ntasks == 0) KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->sc), chol_launches(h->m));
+  else
+    KL(cholesky_tiles<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->uinv32, h->chol_tasks, h->chol_ntasks,
+                             h->chol_state, h->tickets + T_CHOL, h->sc),
+       1);
   return PDAS_OK;
 }
 
@@ -324,6 +332,9 @@ pdas_status factor_solve(pdas_ctx* h, const double* rhs, double* out) {
   if (h->cur_f64) {
     KL(trsv_lower<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, rhs, h->z, h->flags, h->tickets, h->sc), 1);
     KL(trsv_upper_t<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->z, out, h->flags, h->tickets, h->sc), 1);
+  } else if (h->chol_ntasks > 0) {  // the tile factor, with the inverses of its diagonal tiles
+    KL(trsv_lower_blk(h->st, h->m, h->ldm, h->M32, h->uinv32, rhs, h->z, h->flags, h->tickets + T_TRSV, h->sc), 1);
+    KL(trsv_upper_blk(h->st, h->m, h->ldm, h->M32, h->uinv32, h->z, out, h->flags, h->tickets + T_TRSV, h->sc), 1);
   } else {
     KL(trsv_lower<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, rhs, h->z, h->flags, h->tickets, h->sc), 1);
     KL(trsv_upper_t<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->z, out, h->flags, h->tickets, h->sc), 1);
@@ -630,6 +641,20 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
       al((void**)&h->dinv32, sizeof(float) * m);
     }
   }
+  if (e == cudaSuccess && opt.form != PDAS_FP64 && chol_tile_count(m) <= kTileCholMaxTiles) {
+    // the single-launch tile Cholesky of the FP32 factor
+    std::vector<int4> tasks;
+    const int workers = chol_tiles_resident();
+    if (workers < 1) e = cudaErrorUnknown;
+    chol_tile_tasks(m, workers, &tasks);
+    const int64_t nb = chol_tile_count(m);
+    h->chol_ntasks = (int)tasks.size();
+    al((void**)&h->chol_tasks, sizeof(int4) * tasks.size());
+    al((void**)&h->chol_state, sizeof(int) * nb * nb);
+    al((void**)&h->uinv32, sizeof(float) * nb * kCholTile * kCholTile);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->chol_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && (opt.form == PDAS_BF16_IR || opt.form == PDAS_TF32_IR)) {
     e = tc_workspace_create(&h->tc, opt.form, opt.a_dtype, opt.splits, m, n);
     if (e == cudaErrorNotSupported) {
@@ -664,6 +689,9 @@ void pdas_destroy(pdas_handle h) {
   if (h->kidx) cudaFree(h->kidx);
   if (h->d2) cudaFree(h->d2);
   if (h->adj) cudaFree(h->adj);
+  if (h->chol_tasks) cudaFree(h->chol_tasks);
+  if (h->chol_state) cudaFree(h->chol_state);
+  if (h->uinv32) cudaFree(h->uinv32);
   if (h->dinv64) cudaFree(h->dinv64);
   if (h->dinv32) cudaFree(h->dinv32);
   if (h->tickets) cudaFree(h->tickets);

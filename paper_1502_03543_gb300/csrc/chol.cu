@@ -16,13 +16,12 @@
 // the blocks it depends on, so a block only waits on blocks that were handed
 // out earlier and are running or done -- no deadlock.  On a timeout it sets
 // PDAS_ERR_TIMEOUT and returns.
+#include "sync_util.cuh"
 #include "tile_core.cuh"
 
 namespace pdas {
 
 namespace {
-
-__device__ __forceinline__ bool dev_failed(const Scalars* sc) { return *(volatile const int*)&sc->status != 0; }
 
 template <typename T>
 __device__ __forceinline__ bool pivot_bad(T d) {
@@ -179,44 +178,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k_chol_updat
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
-
-// Lane 0 of the calling warp waits (bounded) for flags[j] != 0; the warp
-// learns the outcome.  The acquire by lane 0 and the warp barrier order the
-// warp's later loads of the solution block after the producer's release.
-__device__ bool warp_wait(const int* flags, int64_t j, Scalars* sc) {
-  int res = 1;
-  if ((threadIdx.x & 31) == 0) {
-    const uint64_t t0 = global_ns();
-    while (ld_acquire(flags + j) == 0) {
-      if (dev_failed(sc)) { res = 0; break; }
-      if (global_ns() - t0 > kWaitLimitNs) {
-        atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
-        res = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
-  }
-  res = __shfl_sync(0xffffffffu, res, 0);
-  __syncwarp();
-  return res != 0;
-}
-
 // L z = v.  Block row b (64 rows): z_b = L_bb^{-1} (v_b - sum_{j<b} L_bj z_j).
 // Arithmetic in T (the factor's precision; the FP32 factor of the mixed forms
 // is a preconditioner, refined in FP64 afterwards); v, z in FP64.  Warp w

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pdas.h"
 #include "pdas_components.h"
 
@@ -40,7 +42,7 @@ struct Scalars {
 
 // Counters for the "last block finishes the reduction" pattern and the
 // triangular-solve tickets.
-enum Ticket { T_SCALING = 0, T_PSI, T_STEP, T_NORM, T_NORM2, T_DOT, T_TRSV, T_COUNT = 8 };
+enum Ticket { T_SCALING = 0, T_PSI, T_STEP, T_NORM, T_NORM2, T_DOT, T_TRSV, T_CHOL, T_COUNT = 8 };
 
 // ---- exact widening of the stored A ---------------------------------------
 __device__ __forceinline__ double widen(double v) { return v; }
@@ -90,6 +92,29 @@ cudaError_t launch_syrk_simt(cudaStream_t st, int64_t m, int64_t n, const T* A, 
 // Blocked Cholesky in place; dinv (m) receives the reciprocals of the pivots.
 template <typename T>
 cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Scalars* sc);
+
+// The single-launch tile Cholesky (chol_tiles.cu): 128 x 128 tiles; the task
+// list comes from chol_tile_tasks (built once per m); state holds
+// chol_tile_count(m)^2 ints; ticket is one counter.  Both are cleared here.
+// Beyond 256 tile rows (m > 32768) the task list (~nb^3/6 tasks, built on
+// the host at handle creation) grows past ~3M entries; such handles keep the
+// multi-launch blocked factor.
+constexpr int kTileCholMaxTiles = 256;
+constexpr int kCholTile = 128;  // tile edge of the tile Cholesky and its triangular solves
+int64_t chol_tile_count(int64_t m);
+int chol_tiles_resident();  // resident CTAs on the current device, 0 on error
+void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out);
+// Uinv receives U_l = L_ll^{-T} for every diagonal tile (nb x 128 x 128,
+// row-major per tile), for trsv_lower_blk / trsv_upper_blk.
+template <typename T>
+cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, T* Uinv, const int4* tasks,
+                           int ntasks, int* state, unsigned* ticket, Scalars* sc);
+// The triangular solves with the FP32 tile factor (trsv_blk.cu); flags needs
+// ceil(m / 128) ints.
+cudaError_t trsv_lower_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
+                           const double* v, double* z, int* flags, unsigned* ticket, Scalars* sc);
+cudaError_t trsv_upper_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
+                           const double* z, double* y, int* flags, unsigned* ticket, Scalars* sc);
 template <typename T>
 cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* v,
                        double* z, int* flags, unsigned* tickets, Scalars* sc);

@@ -74,6 +74,7 @@ __device__ void tile_rank_k(const TIn* __restrict__ P, int64_t ldp, int64_t p0, 
 // ty + 16 i and columns tx + 16 j (i, j < 8).  The next K chunk is fetched
 // into registers while the current one is multiplied.
 constexpr int kBig = 128;
+static_assert(kBig == kCholTile, "the tile Cholesky works on 128 x 128 tiles");
 
 template <typename TAcc>
 struct TileSmem128 {

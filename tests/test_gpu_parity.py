@@ -128,7 +128,7 @@ def test_cholesky_and_solves_fp64(pdas, m):
     assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("m", [7, 65, 200])
+@pytest.mark.parametrize("m", [7, 65, 200, 384, 700])  # the FP32 factor runs on 128 x 128 tiles
 def test_cholesky_fp32(pdas, m):
     M = spd_matrix(m, seed=100 + m)
     Lo, _ = oracle.cholesky(M)
@@ -147,14 +147,14 @@ def test_cholesky_fp32(pdas, m):
 
 
 @pytest.mark.parametrize("form,dt", [("fp64", torch.float64), ("fp32_ir", torch.float32)])
-def test_not_spd_reports_pivot(pdas, form, dt):
-    m = 150
+@pytest.mark.parametrize("m,bad", [(150, 97), (400, 300)])
+def test_not_spd_reports_pivot(pdas, form, dt, m, bad):
     M = np.eye(m)
-    M[97, 97] = -1.0
+    M[bad, bad] = -1.0
     with pdas.Solver(m, m + 1, form, dt) as S:
         S.load_matrix(dv(M).to(dt))
         st = S.factor(raise_on_error=False)
-        assert st == -3 and S.last_error_index() == 97
+        assert st == -3 and S.last_error_index() == bad
 
 
 def lapack_direction(A, x, s):
