@@ -87,6 +87,13 @@ typedef struct {
                               D_j >= drop_tol max(D) only (refinement still applies the whole
                               A D A'); 0 keeps every column                               (1e-10) */
   double drop_keep;        /* ... but never fewer than drop_keep * m columns (the largest D_j)  (1.25) */
+  int exact_passes;        /* mixed forms with A stored as FP32 / BF16: 0 = the operator products
+                              M p of the refinement's conjugate gradients while the factor is
+                              FP32 (and pdas_gemv / pdas_gemv_t) run in double-float on the
+                              FP32 pipes (FP32 pairs, FP64 accumulation every 16-32 terms),
+                              several times faster on GB300; 1 = FP64.  The right-hand side,
+                              the true residuals that decide acceptance and A' dy are FP64
+                              either way                                                  (0) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */

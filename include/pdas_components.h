@@ -49,10 +49,13 @@ pdas_status pdas_direction(pdas_handle h, const void* A, const double* x, const 
                            double* ds, pdas_iter_info* info);
 
 /* out (m) = A v (n), FP64 accumulation of exactly widened A: the right-hand
- * side A x of the normal equations. */
+ * side A x of the normal equations.  On a mixed-form handle with A stored as
+ * FP32 / BF16 (and exact_passes off) this is the double-float pass of the
+ * refinement's operator (error within 2^-41 of sum |a v|). */
 pdas_status pdas_gemv(pdas_handle h, const void* A, const double* v, double* out);
 
-/* out (n) = A' u (m), FP64 accumulation: the product behind ds = -A' dy. */
+/* out (n) = A' u (m), FP64 accumulation: the product behind ds = -A' dy
+ * (double-float on mixed-form handles, as pdas_gemv). */
 pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* out);
 
 /* Host-only, no GPU needed: the task order of the single-launch tile

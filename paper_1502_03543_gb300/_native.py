@@ -35,6 +35,7 @@ class Options(ctypes.Structure):
         ("refine_be", ctypes.c_double),
         ("drop_tol", ctypes.c_double),
         ("drop_keep", ctypes.c_double),
+        ("exact_passes", ctypes.c_int),
     ]
 
 

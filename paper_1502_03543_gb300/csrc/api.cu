@@ -65,6 +65,7 @@ struct pdas_ctx {
   int chol_ntasks = 0;
   int* chol_state = nullptr;    // per-tile counters of the tile Cholesky
   float* uinv32 = nullptr;      // L_ll^{-T} of every diagonal tile of the FP32 tile factor
+  float2* pairs = nullptr;      // the vector of a double-float pass as FP32 pairs (max(m, n))
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
   char errmsg[256] = {0};
@@ -197,7 +198,30 @@ pdas_status reset_status(pdas_ctx* h) {
 }
 
 // A v -> out (base == null) or base - A v -> out; norm_slot as in launch_gemv.
-pdas_status gemv(pdas_ctx* h, const void* A, const double* v, const double* base, double* out, int norm_slot) {
+// Double-float passes over A (gemv_df.cu) are available to the mixed forms
+// when A is exact in FP32 (stored as FP32 or BF16) and exact_passes is off.
+// The solve uses them only for the conjugate-gradient operator M p of the
+// refinement while it factors in FP32: every quantity the acceptance test or
+// the direction depends on
+// (r = A x, the true residual r - A(D(A' dy)), w = A' dy) stays FP64, since
+// the double-float rounding of a residual is close to the 1e-14 acceptance
+// level, while in M p it scales with the search direction and only slows
+// the iteration by rounding.  The component entry points pdas_gemv /
+// pdas_gemv_t of a mixed handle expose the double-float pass itself.
+bool df_passes(const pdas_ctx* h) { return is_mixed(h) && h->opt.a_dtype != PDAS_A_F64 && !h->opt.exact_passes; }
+
+pdas_status gemv(pdas_ctx* h, const void* A, const double* v, const double* base, double* out, int norm_slot,
+                 bool df = false) {
+  if (df) {
+    KL(launch_split_pairs(h->st, h->n, v, h->pairs), 1);
+    if (h->opt.a_dtype == PDAS_A_F32)
+      KL(launch_gemv_df<float>(h->st, h->m, h->n, (const float*)A, h->pairs, base, out, h->part, h->tickets, h->sc,
+                               norm_slot), 1);
+    else
+      KL(launch_gemv_df<__nv_bfloat16>(h->st, h->m, h->n, (const __nv_bfloat16*)A, h->pairs, base, out, h->part,
+                                       h->tickets, h->sc, norm_slot), 1);
+    return PDAS_OK;
+  }
   return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
     using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
     KL(launch_gemv<T>(h->st, h->m, h->n, (const T*)A, v, base, out, h->part, h->tickets, h->sc, norm_slot), 1);
@@ -207,7 +231,18 @@ pdas_status gemv(pdas_ctx* h, const void* A, const double* v, const double* base
 
 // w = A' u, then the finish mode (see launch_gemv_t_finish).
 pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const double* x, double* o0, double* o1,
-                   double* o2) {
+                   double* o2, bool df = false) {
+  if (df) {
+    KL(launch_split_pairs(h->st, h->m, u, h->pairs), 1);
+    if (h->opt.a_dtype == PDAS_A_F32)
+      KL(launch_gemv_t_df<float>(h->st, h->m, h->n, (const float*)A, h->pairs, h->gt_part, h->gt_chunks, h->gt_rows),
+         1);
+    else
+      KL(launch_gemv_t_df<__nv_bfloat16>(h->st, h->m, h->n, (const __nv_bfloat16*)A, h->pairs, h->gt_part,
+                                         h->gt_chunks, h->gt_rows), 1);
+    KL(launch_gemv_t_finish(h->st, h->n, h->gt_chunks, h->gt_part, mode, x, h->D, o0, o1, o2, h->sc), 1);
+    return PDAS_OK;
+  }
   pdas_status s = with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
     using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
     KL(launch_gemv_t<T>(h->st, h->m, h->n, (const T*)A, u, h->gt_part, h->gt_chunks, h->gt_rows), 1);
@@ -351,9 +386,13 @@ pdas_status residual(pdas_ctx* h, const void* A, const double* v) {
 
 // M v (matrix-free, FP64) -> out.
 pdas_status apply_normal(pdas_ctx* h, const void* A, const double* v, double* out) {
-  pdas_status s = gemv_t(h, A, v, 2, nullptr, h->u, nullptr, nullptr);
+  // (not once the solve has switched to an FP64 factor: there the FP64 factor
+  // dominates the iteration, and near the end the operator's rounding decides
+  // whether the refinement still reaches its tolerance)
+  const bool df = df_passes(h) && !h->refactored;
+  pdas_status s = gemv_t(h, A, v, 2, nullptr, h->u, nullptr, nullptr, df);
   if (s != PDAS_OK) return s;
-  return gemv(h, A, h->u, nullptr, out, -1);
+  return gemv(h, A, h->u, nullptr, out, -1, df);
 }
 
 // FP64 refinement of dy for the mixed forms (a6): conjugate gradients on
@@ -551,6 +590,7 @@ void pdas_default_options(pdas_options* opt) {
   opt->refine_be = 1e-14;
   opt->drop_tol = 1e-10;
   opt->drop_keep = 1.25;
+  opt->exact_passes = 0;
   opt->dspread_refactor = 0.0;
   opt->stream = nullptr;
   opt->splits = 0;
@@ -587,7 +627,7 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (opt.form < PDAS_FP64 || opt.form > PDAS_FP32_IR) return PDAS_ERR_ARG;
   if (opt.a_dtype < PDAS_A_F64 || opt.a_dtype > PDAS_A_BF16) return PDAS_ERR_ARG;
   if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) ||
-      !(opt.drop_tol >= 0) || !(opt.drop_keep >= 1.0) || opt.splits < 0 ||
+      !(opt.drop_tol >= 0) || !(opt.drop_keep >= 1.0) || opt.splits < 0 || (opt.exact_passes & ~1) ||
       opt.splits > 3 ||
       opt.stall_count < 1 || !(opt.stall_theta >= 0))
     return PDAS_ERR_ARG;
@@ -630,6 +670,7 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   al((void**)&h->gt_part, sizeof(double) * n * h->gt_chunks);
   al((void**)&h->tickets, sizeof(unsigned) * T_COUNT);
   al((void**)&h->flags, sizeof(int) * (nblk + 1));
+  if (opt.form != PDAS_FP64 && opt.a_dtype != PDAS_A_F64) al((void**)&h->pairs, sizeof(float2) * n);  // n > m
   al((void**)&h->sc, sizeof(Scalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->sc_host, sizeof(Scalars));
   if (e == cudaSuccess) {
@@ -692,6 +733,7 @@ void pdas_destroy(pdas_handle h) {
   if (h->chol_tasks) cudaFree(h->chol_tasks);
   if (h->chol_state) cudaFree(h->chol_state);
   if (h->uinv32) cudaFree(h->uinv32);
+  if (h->pairs) cudaFree(h->pairs);
   if (h->dinv64) cudaFree(h->dinv64);
   if (h->dinv32) cudaFree(h->dinv32);
   if (h->tickets) cudaFree(h->tickets);
@@ -940,7 +982,7 @@ pdas_status pdas_gemv(pdas_handle h, const void* A, const double* v, double* out
   if (!h || !A || !v || !out) return PDAS_ERR_ARG;
   pdas_status st = reset_status(h);
   if (st != PDAS_OK) return st;
-  if ((st = gemv(h, A, v, nullptr, out, -1)) != PDAS_OK) return st;
+  if ((st = gemv(h, A, v, nullptr, out, -1, df_passes(h))) != PDAS_OK) return st;
   if ((st = read_scalars(h)) != PDAS_OK) return st;
   return device_status(h);
 }
@@ -949,7 +991,7 @@ pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* o
   if (!h || !A || !u || !out) return PDAS_ERR_ARG;
   pdas_status st = reset_status(h);
   if (st != PDAS_OK) return st;
-  if ((st = gemv_t(h, A, u, 0, nullptr, out, nullptr, nullptr)) != PDAS_OK) return st;
+  if ((st = gemv_t(h, A, u, 0, nullptr, out, nullptr, nullptr, df_passes(h))) != PDAS_OK) return st;
   if ((st = read_scalars(h)) != PDAS_OK) return st;
   return device_status(h);
 }

@@ -48,6 +48,24 @@ enum Ticket { T_SCALING = 0, T_PSI, T_STEP, T_NORM, T_NORM2, T_DOT, T_TRSV, T_CH
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float v) { return (double)v; }
 __device__ __forceinline__ double widen(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+// FP32 -> FP64 widening by bit manipulation on the integer pipes: on GB300
+// the FP64 pipe is the bound of every pass over A, and a conversion
+// instruction would occupy it as long as the multiply-add does.  Exact for
+// every FP32 value: normal numbers move their exponent from bias 127 to
+// 1023, zeros keep their sign, Inf/NaN map to exponent 2047; subnormals take
+// the conversion instruction (they do not occur in practice).
+__device__ __forceinline__ double widen_bits(uint32_t u) {
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t mant = u & 0x7fffffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u) {
+    if (mant == 0u) return __longlong_as_double((long long)sign);
+    return (double)__uint_as_float(u);
+  }
+  const unsigned long long e64 = (e == 0xffu) ? 2047ull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)mant << 29)));
+}
+
 __device__ __forceinline__ float widen32(double v) { return (float)v; }
 __device__ __forceinline__ float widen32(float v) { return v; }
 __device__ __forceinline__ float widen32(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -60,6 +78,17 @@ cudaError_t launch_gemv(cudaStream_t st, int64_t m, int64_t n, const T* A, const
 template <typename T>
 cudaError_t launch_gemv_t(cudaStream_t st, int64_t m, int64_t n, const T* A, const double* u, double* part,
                           int chunks, int64_t rows_per_chunk);
+
+// The passes over A in double-float on the FP32 pipes (gemv_df.cu), for A
+// stored as FP32 or BF16: v (or u) is first split into FP32 pairs by
+// launch_split_pairs; results and partials are FP64 as above.
+cudaError_t launch_split_pairs(cudaStream_t st, int64_t n, const double* v, float2* out);
+template <typename T>
+cudaError_t launch_gemv_df(cudaStream_t st, int64_t m, int64_t n, const T* A, const float2* v2, const double* base,
+                           double* out, double* part, unsigned* tickets, Scalars* sc, int norm_slot);
+template <typename T>
+cudaError_t launch_gemv_t_df(cudaStream_t st, int64_t m, int64_t n, const T* A, const float2* u2, double* part,
+                             int chunks, int64_t rows_per_chunk);
 // w = sum of the gemv_t partials; then per mode:
 //   0: out0 = w
 //   1: direction: out0 = dx = D w - x, out1 = ds = -w, out2 = w (may be null)

@@ -9,91 +9,13 @@
 // (ticket counter, no float atomics) combines the per-block partials in block
 // order.  The grid of each reduction depends on the sizes only, so results
 // are bit-identical from run to run.
-#include "pdas_internal.cuh"
+#include "reduce_util.cuh"
 
 namespace pdas {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double warp_min(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// op: 0 sum, 1 max, 2 min.  Result valid in thread 0.
-template <int OP>
-__device__ double block_reduce(double v, double* sm) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = OP == 0 ? warp_sum(v) : OP == 1 ? warp_max(v) : warp_min(v);
-  __syncthreads();
-  if (lane == 0) sm[w] = v;
-  __syncthreads();
-  double t = OP == 0 ? 0.0 : OP == 1 ? -INFINITY : INFINITY;
-  if (w == 0) {
-    if (lane < nw) t = sm[lane];
-    t = OP == 0 ? warp_sum(t) : OP == 1 ? warp_max(t) : warp_min(t);
-  }
-  return t;
-}
-
-// True in every thread of the block that finishes last.  Partials written
-// before the call are visible to that block.
-__device__ bool last_block(unsigned* ticket) {
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
-  __syncthreads();
-  return last;
-}
-
-// Combine nparts partials in index order by one block (fixed order).
-template <int OP>
-__device__ double combine(const double* part, int nparts, double* sm) {
-  double v = OP == 0 ? 0.0 : OP == 1 ? -INFINITY : INFINITY;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    double p = __ldcg(part + i);
-    v = OP == 0 ? v + p : OP == 1 ? fmax(v, p) : fmin(v, p);
-  }
-  return block_reduce<OP>(v, sm);
-}
-
-__device__ __forceinline__ bool failed(const Scalars* sc) { return *(volatile const int*)&sc->status != 0; }
-
-int grid_for(int64_t n, int per_thread = 1) {
-  int64_t g = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
-  if (g < 1) g = 1;
-  if (g > 1184) g = 1184;  // 8 blocks per SM on 148+ SMs; strided loops cover the rest
-  return (int)g;
-}
-
 // ---- vector loads of VEC consecutive elements of A, widened to double ----
-// FP32 -> FP64 widening by bit manipulation on the integer pipes: on GB300
-// the FP64 pipe is the bound of every pass over A, and a conversion
-// instruction would occupy it as long as the multiply-add does.  Exact for
-// every FP32 value: normal numbers move their exponent from bias 127 to
-// 1023, zeros keep their sign, Inf/NaN map to exponent 2047; subnormals take
-// the conversion instruction (they do not occur in practice).
-__device__ __forceinline__ double widen_bits(uint32_t u) {
-  const uint32_t e = (u >> 23) & 0xffu;
-  const uint32_t mant = u & 0x7fffffu;
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  if (e == 0u) {
-    if (mant == 0u) return __longlong_as_double((long long)sign);
-    return (double)__uint_as_float(u);
-  }
-  const unsigned long long e64 = (e == 0xffu) ? 2047ull : (unsigned long long)(e + 896u);
-  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)mant << 29)));
-}
-
 template <typename T>
 struct Vec;
 template <>
@@ -563,10 +485,6 @@ __global__ void k_convert_matrix(int64_t m, int64_t ld_src, const void* src, int
     }
 }
 
-template <typename T>
-bool vec_aligned(const T* A, int64_t n) {
-  return ((uintptr_t)A % 16 == 0) && ((n * (int64_t)sizeof(T)) % 16 == 0);
-}
 
 }  // namespace
 

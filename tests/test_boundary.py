@@ -54,6 +54,7 @@ def test_host_side_validation_without_gpu(lib):
     L.pdas_default_options(ctypes.byref(o))
     assert o.max_iter == 500 and o.refine_tol == 1e-14 and o.dspread_refactor == 0.0 and o.form == N.FP64
     assert o.refine_be == 1e-14 and o.drop_tol == 1e-10 and o.drop_keep == 1.25 and o.refine_max == 40
+    assert o.exact_passes == 0
     h = ctypes.c_void_p()
     # m < n and m >= 1 (Section I)
     assert L.pdas_create(10, 10, ctypes.byref(o), ctypes.byref(h)) == N.ERR_ARG
@@ -62,6 +63,9 @@ def test_host_side_validation_without_gpu(lib):
     assert not h.value
     bad = N.Options.from_buffer_copy(o)
     bad.form = 9
+    assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_ARG
+    bad = N.Options.from_buffer_copy(o)
+    bad.exact_passes = 2
     assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_ARG
     bad = N.Options.from_buffer_copy(o)
     bad.refine_tol = -1.0

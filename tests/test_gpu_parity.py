@@ -73,6 +73,31 @@ def test_gemv_and_gemv_t(pdas, storage, m, n):
     assert np.all(np.abs(w - ref_w) <= bound_w + 1e-300)
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n", SHAPES + [(33, 4104), (130, 2048)])
+def test_gemv_double_float_mixed_forms(pdas, storage, m, n):
+    """The mixed forms run the passes over A in double-float on the FP32 pipes:
+    each term a v carries <= 2^-47 relative error, the FP32 low part of a
+    16- or 32-term partial sum adds <= 32 x 2^-48 of its terms, and the FP64
+    accumulation of the partials gamma_n(u64): together well within 2^-41 of
+    sum |a v|, some 10^5 times below FP32 accuracy.  exact_passes=1 restores
+    the FP64 passes (FP64 bound)."""
+    lp = lpgen.generate(m, n, seed=m + n + 7, storage=storage, scaled=storage == "bf16")
+    A = dev_A(lp)
+    rng = np.random.default_rng(2)
+    v, u = rng.standard_normal(n), rng.standard_normal(m)
+    ref_r, ref_w = oracle.gemv(lp.A64, v), oracle.gemv_t(lp.A64, u)
+    mag_r, mag_w = np.abs(lp.A64) @ np.abs(v), np.abs(lp.A64).T @ np.abs(u)
+    with pdas.Solver(m, n, "fp32_ir", TORCH_DT[storage]) as S:
+        r, w = host(S.gemv(A, dv(v))), host(S.gemv_t(A, dv(u)))
+    assert np.all(np.abs(r - ref_r) <= (2.0 ** -41 + 2 * gamma(n, U64)) * mag_r + 1e-300)
+    assert np.all(np.abs(w - ref_w) <= (2.0 ** -41 + 2 * gamma(m, U64)) * mag_w + 1e-300)
+    with pdas.Solver(m, n, "fp32_ir", TORCH_DT[storage], exact_passes=1) as S:
+        r, w = host(S.gemv(A, dv(v))), host(S.gemv_t(A, dv(u)))
+    assert np.all(np.abs(r - ref_r) <= 2 * gamma(n, U64) * mag_r + 1e-300)
+    assert np.all(np.abs(w - ref_w) <= 2 * gamma(m, U64) * mag_w + 1e-300)
+
+
 @pytest.mark.parametrize("storage", ["f64", "bf16"])
 @pytest.mark.parametrize("m,n", SHAPES)
 def test_normal_matrix_fp64(pdas, storage, m, n):
@@ -437,8 +462,11 @@ def test_full_size_bf16_tensor_core_sampled(pdas):
         got = {pq: float(M[pq[0], pq[1]]) for pq in pairs}
         del M
         dx, dy, ds, info = S.direction(A, x, s)
-        adx = host(S.gemv(A, dx))
-        w = host(S.gemv_t(A, dy))
+    # the identities through the FP64 passes (the ones the direction uses; the
+    # component entry points of a default mixed handle run the double-float pass)
+    with pdas.Solver(m, n, "bf16_ir", torch.bfloat16, exact_passes=1) as E:
+        adx = host(E.gemv(A, dx))
+        w = host(E.gemv_t(A, dy))
     D = lp.x0 / lp.s0
     diag = {p: oracle.normal_entry(lp.A64, D, p, p) for pq in got for p in pq}
     for (p, q), g in got.items():
