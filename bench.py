@@ -46,24 +46,55 @@ def load_peaks():
     return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, source="fallback")
 
 
-def syrk_roofline(form, m, n, splits, ms_per_launch, peaks):
-    """Roofline record of the normal-matrix kernel (lower triangle m(m+1)/2
-    entries, n multiply-adds each, per split term)."""
+# DRAM bytes (read + write) per launch of the normal-matrix kernel from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of
+# `bench.py --kernel normal` on this workload; profiles/syrk_tc_bf16x3_8192x32768.md.
+# Valid only for the kernel as captured: drop the entry when it changes.
+SYRK_TRAFFIC = {("dense_8192x32768_bf16_colscaled", 3): 10.32e9 + 0.131e9}
+
+
+def syrk_roofline(form, m, n, splits, ms_per_launch, peaks, workload=None):
+    """Roofline record of the normal-matrix kernel.  Algorithmic work is one
+    lower-triangle product, m(m+1)/2 entries of n multiply-adds (m^2 n flops,
+    FMA = 2); the tensor-core forms execute that product once per split term
+    of D.*A, reported separately as executed work."""
     terms = splits if form in ("bf16_ir", "tf32_ir") else 1
-    flops = float(m) * (m + 1) * n * terms  # FMA = 2 flops
+    flops = float(m) * (m + 1) * n
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     if form == "bf16_ir":
         bound, peak, note = "tensor", peaks["bf16_sus"], "bf16 dense, sustained, of %s" % peaks["source"]
     elif form == "tf32_ir":
         bound, peak, note = "tensor", peaks["bf16_sus"] * 1.1 / 2.25, "tf32 = bf16 sustained x 1.1/2.25 nominal ratio"
     elif form == "fp32_ir":
-        # 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
-        bound, peak, note = "alu", 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "FP32 SIMT from unit counts"
+        bound, peak, note = "alu", fp32_simt_peak(peaks), "FP32 SIMT from unit counts"
     else:
         bound, peak, note = "alu", 1.25, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+    traffic = SYRK_TRAFFIC.get((workload, terms)) if form == "bf16_ir" else None
     return dict(bound=bound, achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
-                frac=round(achieved / peak, 4), traffic=None, kernel="normal-matrix (a3)", peak_note=note,
-                algorithmic_flops_per_launch=flops)
+                frac=round(achieved / peak, 4), traffic=traffic, kernel="normal-matrix k_syrk_tc (a3)",
+                peak_note=note, algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4),
+                split_terms=terms, executed_flops_per_launch=flops * terms,
+                executed_frac=round(achieved * terms / peak, 4))
+
+
+def fp32_simt_peak(peaks):
+    """152 SMs x 128 FP32 lanes x 2 flops x the maximum SM clock (TFLOP/s)."""
+    return 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+
+
+def chol_roofline(form, m, ms_per_launch, peaks):
+    """Roofline record of the Cholesky factor: m^3/3 flops; the FP32 tile
+    factor of the mixed forms runs on the FP32 SIMT pipes, the FP64 form's
+    factor on the FP64 pipes."""
+    flops = float(m) ** 3 / 3.0
+    achieved = flops / (ms_per_launch * 1e-3) / 1e12
+    if form == "fp64":
+        peak, note, kern = 1.25, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)", "blocked FP64 Cholesky (a4)"
+    else:
+        peak, note, kern = fp32_simt_peak(peaks), "FP32 SIMT from unit counts", "k_chol_tiles<float> (a4)"
+    return dict(bound="alu", achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
+                frac=round(achieved / peak, 4), traffic=None, kernel=kern, peak_note=note,
+                algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4))
 
 
 class ClockSampler:
@@ -252,12 +283,13 @@ def run_normal_only(args):
     S.close()
     ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
     splits = args.splits or 3
-    roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, load_peaks())
+    peaks = load_peaks()
+    roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, peaks, args.workload)
     out = dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits, ms_per_launch=ms,
                launches=prof["launches"], wall_s=wall, roofline=roof)
     if factor:
         out["factor_ms"] = fms / args.steps
-        out["factor_tflops"] = lp.m ** 3 / 3 / (fms / args.steps * 1e-3) / 1e12
+        out["factor_roofline"] = chol_roofline(args.form, lp.m, fms / args.steps, peaks)
     print(json.dumps(out))
 
 
@@ -372,7 +404,12 @@ def run_ours(args):
         return
     peaks = load_peaks()
     normal_ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
-    roof = syrk_roofline(args.form, m, n, splits, normal_ms, peaks)
+    factor_ms = prof["ms"]["factor"] / max(1, prof["calls"]["factor"])
+    # the dominant kernel of the step is reported as "roofline"; both records
+    # are listed under "rooflines"
+    roofs = [syrk_roofline(args.form, m, n, splits, normal_ms, peaks, args.workload),
+             chol_roofline(args.form, m, factor_ms, peaks)]
+    roof = max(roofs, key=lambda r: r["ms_per_launch"])
     stages = {k: round(v / max(1, args.steps), 4) for k, v in prof["ms"].items()}
     clocks = clk.summary()
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -383,7 +420,7 @@ def run_ours(args):
                             steps_from="seeded interior start (restart after convergence)",
                             l2="inputs larger than L2 (A is %d MB)" % (A.numel() * A.element_size() // 2 ** 20),
                             parallelism="replicas" if world > 1 else "single"),
-                roofline=roof, stages_ms_per_step=stages,
+                roofline=roof, rooflines=roofs, stages_ms_per_step=stages,
                 refine_sweeps=[i["refine_sweeps"] for i in infos], used_fp64=[i["used_fp64"] for i in infos],
                 gpu_launches=prof["launches"],
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=vec_bytes, d2h_bytes_per_step=vec_bytes),

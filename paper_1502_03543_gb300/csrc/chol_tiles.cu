@@ -174,27 +174,44 @@ __device__ __forceinline__ void rank_update(T (&acc)[8][8], int64_t m, int64_t l
   }
 }
 
+// 1 / sqrt(d): the hardware estimate refined by one Newton step (within
+// about 2 ulp in FP32; the FP32 factor is a preconditioner); IEEE for FP64.
+__device__ __forceinline__ float inv_sqrt(float d) {
+  const float r = rsqrtf(d);
+  return r * fmaf(-0.5f * d * r, r, 1.5f);
+}
+__device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
+
 // Step C of the right-looking factorisation of a 32 x 32 block held by one
-// warp (lane = row): pivot by shuffle from lane C, scale column C, then the
-// rank-1 update of the later columns, each entry L_qC coming from lane q.
+// warp (lane = row): the pivot comes by shuffle from lane C; every lane
+// scales its entry of column C and publishes it in a 32-entry column buffer
+// (double-buffered, so one warp barrier per step); each lane then reads the
+// column entries it needs with 16-byte broadcast loads and updates its row.
 // Recursion on C keeps every register index a compile-time constant.
 template <typename T, int C>
-__device__ __forceinline__ void warp_potrf_step(T (&row)[32], int lane, int& bad, T* rcp) {
+__device__ __forceinline__ void warp_potrf_step(T (&row)[32], int lane, int& bad, T& myrs, T* cbuf) {
   const T d = __shfl_sync(0xffffffffu, row[C], C);
   if (bad < 0 && pivot_bad(d)) bad = C;  // (the sweep runs on; the block is discarded)
-  const T lcc = sqrt(d), rs = T(1) / lcc;
-  if (lane == C) {
-    row[C] = lcc;
-    rcp[C] = rs;
-  } else if (lane > C) {
-    row[C] *= rs;
-  }
+  const T rs = inv_sqrt(d);
+  const T v = lane > C ? row[C] * rs : (lane == C ? d * rs : T(0));
+  if (lane >= C) row[C] = v;
+  if (lane == C) myrs = rs;
+  T* col = cbuf + (C & 1) * 32;
+  col[lane] = v;
+  __syncwarp();
+  constexpr int Q0 = (C + 1) & ~3;  // first 4-aligned group holding an entry q > C
 #pragma unroll
-  for (int q = C + 1; q < 32; ++q) {
-    const T ljc = __shfl_sync(0xffffffffu, row[C], q);
-    if (lane >= q) row[q] = fma(-row[C], ljc, row[q]);
+  for (int q4 = Q0; q4 < 32; q4 += 4) {
+    T c4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c4[e] = col[q4 + e];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int q = q4 + e;
+      if (q > C && lane >= q) row[q] = fma(-v, c4[e], row[q]);
+    }
   }
-  if constexpr (C + 1 < 32) warp_potrf_step<T, C + 1>(row, lane, bad, rcp);
+  if constexpr (C + 1 < 32) warp_potrf_step<T, C + 1>(row, lane, bad, myrs, cbuf);
 }
 
 // Factorisation of the diagonal tile (held in acc) through shared memory in
@@ -231,7 +248,9 @@ __device__ __forceinline__ bool tile_potrf(const T (&acc)[8][8], int64_t m, int6
 #pragma unroll
       for (int q = 0; q < 32; ++q) row[q] = S[c0 + lane][c0 + q];
       int bad = -1;
-      warp_potrf_step<T, 0>(row, lane, bad, sm.rcp + c0);
+      T myrs = T(1);
+      warp_potrf_step<T, 0>(row, lane, bad, myrs, &sm.cb[0][0]);
+      sm.rcp[c0 + lane] = myrs;
       if (bad >= 0) {
         if (lane == 0) s_fail = c0 + bad;
       } else {

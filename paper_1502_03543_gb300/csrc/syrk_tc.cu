@@ -427,11 +427,26 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   e = cudaMalloc(&w->opb, sizeof(__nv_bfloat16) * (size_t)w->splits * m * w->kpad);
   if (e == cudaSuccess && n % 8 != 0) e = cudaMalloc(&w->opa, sizeof(__nv_bfloat16) * (size_t)m * w->kpad);
   if (e == cudaSuccess) e = cudaMalloc(&hs->D32, sizeof(float) * (size_t)((n + 7) / 8 * 8));
-  // lower-triangle tile list: (I, J) with some row p >= some column q
+  // Lower-triangle tile list ((I, J) with some row p >= some column q),
+  // ordered by G x G super-tiles with G ~ sqrt(#SMs): the CTAs resident at
+  // one time then cover about G row blocks of A and G row blocks of the
+  // split planes, whose K panels they stream at roughly the same pace, so L2
+  // serves most operand reads (in plain row order a wave spans a few rows of
+  // tiles but up to all tile columns, and the split planes were re-read from
+  // DRAM about a dozen times per launch).  Super-tiles go in row-major lower
+  // order, so consecutive ones share their row blocks of A.
   std::vector<int2> tl;
   const int64_t nI = (m + BM - 1) / BM, nJ = (m + BN - 1) / BN;
-  for (int64_t I = 0; I < nI; ++I)
-    for (int64_t J = 0; J < nJ && J * BN <= I * BM + BM - 1; ++J) tl.push_back(make_int2((int)I, (int)J));
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t G = 1;
+  while ((G + 1) * (G + 1) <= (int64_t)sms) ++G;
+  for (int64_t PI = 0; PI < nI; PI += G)
+    for (int64_t PJ = 0; PJ <= PI; PJ += G)
+      for (int64_t I = PI; I < nI && I < PI + G; ++I)
+        for (int64_t J = PJ; J < nJ && J < PJ + G && J * BN <= I * BM + BM - 1; ++J)
+          tl.push_back(make_int2((int)I, (int)J));
   hs->ntiles = (int)tl.size();
   if (e == cudaSuccess) e = cudaMalloc(&hs->tiles, sizeof(int2) * tl.size());
   if (e == cudaSuccess) e = cudaMemcpy(hs->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
