@@ -119,3 +119,36 @@ WORKLOADS = {
 def workload(name: str, seed: int = 0) -> LP:
     w = WORKLOADS[name]
     return generate(w["m"], w["n"], seed=seed, storage=w["storage"], scaled=w["scaled"])
+
+
+# ---- batches of small LPs ---------------------------------------------------
+def batch_sizes(count: int = 512, seed: int = 0, m_lo: int = 16, m_hi: int = 256, k_lo: int = 2, k_hi: int = 4):
+    """Sizes of a batch of uneven LPs: numpy default_rng(seed) draws
+    m ~ U{m_lo..m_hi} for every instance, then k ~ U{k_lo..k_hi}; n = m k."""
+    rng = np.random.default_rng(seed)
+    m = rng.integers(m_lo, m_hi + 1, count)
+    k = rng.integers(k_lo, k_hi + 1, count)
+    return m.astype(np.int64), (m * k).astype(np.int64)
+
+
+def batch(count: int = 512, seed: int = 0, storage: str = "f32", base_seed: int = 1000, sizes=None):
+    """The LPs of a batch: instance i is generate(m_i, n_i, seed=base_seed + i)
+    with the sizes of batch_sizes(count, seed) (or the given (m, n) arrays)."""
+    m, n = sizes if sizes is not None else batch_sizes(count, seed)
+    return [generate(int(m[i]), int(n[i]), seed=base_seed + i, storage=storage) for i in range(len(m))]
+
+
+def pack(lps):
+    """Concatenate a batch in LP order: A (each A_i row-major, in its storage
+    dtype), b, c, x0, y0, s0 (float64), and the m, n arrays; the offsets of
+    LP i are the prefix sums of m_k n_k, m_k and n_k over k < i."""
+    A = np.concatenate([lp.A_store.ravel() for lp in lps])
+    cat = lambda f: np.concatenate([getattr(lp, f) for lp in lps]).astype(np.float64)
+    return dict(A=A, b=cat("b"), c=cat("c"), x0=cat("x0"), y0=cat("y0"), s0=cat("s0"),
+                m=np.array([lp.m for lp in lps], dtype=np.int32), n=np.array([lp.n for lp in lps], dtype=np.int32))
+
+
+BATCHES = {
+    # 512 LPs, m ~ U{16..256}, n = m U{2..4}, FP32 storage, instance seeds 1000 + i
+    "batch_512_f32": dict(count=512, seed=0, storage="f32", tol=1e-7),
+}

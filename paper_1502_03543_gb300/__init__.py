@@ -11,6 +11,8 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
+
 import torch
 
 from . import _native as N
@@ -238,6 +240,81 @@ class _LPSolve(torch.autograd.Function):
         if dA is not None:
             dA = dA.to(A.dtype)
         return dA, db, dc, None, None, None, None, None, None
+
+
+class BatchSolver:
+    """A libpdas batch handle (pdas_batch.h): count small LPs solved together,
+    one CTA per LP, replayed as one CUDA graph.
+
+    A: packed float32 CUDA tensor (A_i row-major, in LP order); b, c, x, y, s:
+    packed float64 CUDA tensors (lpgen.pack gives the layout).  The tensors
+    are bound to the handle: it keeps references to them until close();
+    (x, y, s) is updated in place by solve()."""
+
+    def __init__(self, m, n, A, b, c, x, y, s, alpha=0.95, tol=1e-7, max_iter=500, refine_tol=1e-14,
+                 refine_max=40, autotune=True, stream=None):
+        lib = N.lib()
+        self.m = np.ascontiguousarray(m, dtype=np.int32)
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.count = int(self.m.size)
+        mt, nt, at = int(self.m.sum()), int(self.n.sum()), int((self.m.astype(np.int64) * self.n).sum())
+        self._bufs = (A, b, c, x, y, s)
+        ptrs = [_ptr(A, torch.float32, at, "A"), _ptr(b, torch.float64, mt, "b"), _ptr(c, torch.float64, nt, "c"),
+                _ptr(x, torch.float64, nt, "x"), _ptr(y, torch.float64, mt, "y"), _ptr(s, torch.float64, nt, "s")]
+        o = N.BatchOptions()
+        lib.pdas_batch_default_options(ctypes.byref(o))
+        o.alpha, o.tol, o.max_iter, o.refine_tol, o.refine_max = alpha, tol, max_iter, refine_tol, refine_max
+        o.autotune = 1 if autotune else 0
+        self.stream = stream
+        o.stream = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        h = ctypes.c_void_p()
+        st = lib.pdas_batch_create(self.count, self.m.ctypes.data_as(ctypes.c_void_p),
+                                   self.n.ctypes.data_as(ctypes.c_void_p), *ptrs, ctypes.byref(o), ctypes.byref(h))
+        if st != N.OK:
+            raise PdasError(st, "pdas_batch_create")
+        self._h = h
+
+    def solve(self):
+        """Runs every LP to its stop: dict of per-LP status, iters, gap, FP64-tier
+        and unrefined iteration counts (numpy) and the device time in ms."""
+        status = np.zeros(self.count, dtype=np.int32)
+        iters = np.zeros(self.count, dtype=np.int32)
+        gap = np.zeros(self.count, dtype=np.float64)
+        cp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        st = N.lib().pdas_batch_solve(self._h, cp(status), cp(iters), cp(gap))
+        if st != N.OK:
+            raise PdasError(st, "pdas_batch_solve", N.lib().pdas_batch_last_error_message(self._h).decode())
+        fp64 = np.zeros(self.count, dtype=np.int32)
+        unrefined = np.zeros(self.count, dtype=np.int32)
+        N.lib().pdas_batch_diagnostics(self._h, cp(fp64), cp(unrefined))
+        return dict(status=status, iters=iters, gap=gap, fp64_iters=fp64, unrefined=unrefined,
+                    ms=N.lib().pdas_batch_last_ms(self._h))
+
+    def config(self):
+        """The buckets: list of (m bound, CTA threads, LP count)."""
+        k = 8
+        mb, th, ct = (np.zeros(k, dtype=np.int32) for _ in range(3))
+        cp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        nb = N.lib().pdas_batch_config(self._h, cp(mb), cp(th), cp(ct), k)
+        return [(int(mb[i]), int(th[i]), int(ct[i])) for i in range(min(nb, k))]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().pdas_batch_destroy(self._h)
+            self._h = None
+            self._bufs = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_lp(A, b, c, x0, y0, s0, solver, alpha=0.95, tol=1e-8):

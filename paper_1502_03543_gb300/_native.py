@@ -64,6 +64,18 @@ class IterInfo(ctypes.Structure):
 STAGES = ("rhs", "normal", "factor", "solve", "direction", "step", "fold")
 
 
+class BatchOptions(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("refine_tol", ctypes.c_double),
+        ("refine_max", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 7), ("calls", ctypes.c_int64 * 7), ("launches", ctypes.c_int64)]
 
@@ -98,6 +110,15 @@ SIGNATURES = {
     "pdas_gemv_t": ([_H, _P, _P, _P], _I),
     "pdas_gemv_t_noalloc": ([_I64, _I64, _I, _P, _P, _P, _P], _I),
     "pdas_chol_tile_tasks": ([_I64, _I, _P, _I64], _I64),
+    "pdas_batch_default_options": ([ctypes.POINTER(BatchOptions)], None),
+    "pdas_batch_create": ([_I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(BatchOptions), ctypes.POINTER(_H)],
+                          _I),
+    "pdas_batch_solve": ([_H, _P, _P, _P], _I),
+    "pdas_batch_config": ([_H, _P, _P, _P, _I], _I),
+    "pdas_batch_last_ms": ([_H], _D),
+    "pdas_batch_diagnostics": ([_H, _P, _P], _I),
+    "pdas_batch_last_error_message": ([_H], ctypes.c_char_p),
+    "pdas_batch_destroy": ([_H], None),
     "pdas_profile_enable": ([_H, _I], _I),
     "pdas_profile_read": ([_H, ctypes.POINTER(Profile)], _I),
 }

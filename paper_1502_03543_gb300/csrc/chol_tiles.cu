@@ -448,16 +448,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
 
 }  // namespace
 
+template <typename T>
+size_t chol_tiles_smem_bytes() {
+  return sizeof(TileCholSmem<T>);
+}
+
 int64_t chol_tile_count(int64_t m) { return (m + kBig - 1) / kBig; }
 
 // Resident CTAs of the FP32 tile Cholesky on the current device (the worker
 // count the task order is scheduled for).
 int chol_tiles_resident() {
   cudaError_t e = cudaFuncSetAttribute(k_chol_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(TileCholSmem<float>));
+                                       (int)chol_tiles_smem_bytes<float>());
   int occ = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chol_tiles<float>, kThreads, sizeof(TileCholSmem<float>));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chol_tiles<float>, kThreads,
+                                                      chol_tiles_smem_bytes<float>());
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess || occ < 1 || sms < 1) {
@@ -583,11 +589,6 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
         try_ready(w);
       }
   }
-}
-
-template <typename T>
-size_t chol_tiles_smem_bytes() {
-  return sizeof(TileCholSmem<T>);
 }
 
 template <typename T>

@@ -15,6 +15,7 @@
 // multiply-add; the error stays within a few units of 2^-44 of sum |a v|,
 // the level of FP64 accumulation over the same row length.  Block
 // reductions, chunk sums and the norm slots are FP64, as in the FP64 passes.
+#include "df_util.cuh"
 #include "reduce_util.cuh"
 
 namespace pdas {
@@ -47,28 +48,9 @@ struct Vec32<__nv_bfloat16> {
   __device__ static float one(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 };
 
-// (hi, lo) += a (vh + vl)
-__device__ __forceinline__ void df_madd(float& hi, float& lo, float a, float vh, float vl) {
-  const float ph = a * vh;
-  const float pl = fmaf(a, vl, fmaf(a, vh, -ph));
-  const float t = hi + ph;
-  const float bb = t - hi;
-  lo += ((hi - (t - bb)) + (ph - bb)) + pl;
-  hi = t;
-}
-
-__device__ __forceinline__ void df_flush(double& acc, float& hi, float& lo) {
-  acc += widen_bits(__float_as_uint(hi)) + widen_bits(__float_as_uint(lo));
-  hi = 0.f;
-  lo = 0.f;
-}
-
 __global__ void k_split_pairs(int64_t n, const double* __restrict__ v, float2* __restrict__ out) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const double d = v[j];
-    const float h = (float)d;
-    out[j] = make_float2(h, (float)(d - (double)h));
-  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = df_split(v[j]);
 }
 
 // out_p = A_p. v (base == null) or base_p - A_p. v; ROWS rows per block; as
