@@ -78,8 +78,9 @@ pdas_status pdas_batch_solve(pdas_batch_handle h, int* status_out, int* iters_ou
  * (an LP moves to it for good once its FP32 factor meets a pivot that is not
  * positive); unrefined_out = iterations whose refinement stopped at
  * refine_max without meeting refine_tol (their direction is used as it
- * stands). */
-pdas_status pdas_batch_diagnostics(pdas_batch_handle h, int* fp64_out, int* unrefined_out);
+ * stands); time_us_out = device time of each LP's solve in microseconds
+ * (its CTA's global timer, start to end). */
+pdas_status pdas_batch_diagnostics(pdas_batch_handle h, int* fp64_out, int* unrefined_out, float* time_us_out);
 
 /* The bucket layout: up to cap buckets, each with its upper bound on m, its
  * CTA size (threads) and its number of LPs.  Returns the bucket count. */

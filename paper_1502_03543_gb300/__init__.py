@@ -286,8 +286,9 @@ class BatchSolver:
             raise PdasError(st, "pdas_batch_solve", N.lib().pdas_batch_last_error_message(self._h).decode())
         fp64 = np.zeros(self.count, dtype=np.int32)
         unrefined = np.zeros(self.count, dtype=np.int32)
-        N.lib().pdas_batch_diagnostics(self._h, cp(fp64), cp(unrefined))
-        return dict(status=status, iters=iters, gap=gap, fp64_iters=fp64, unrefined=unrefined,
+        time_us = np.zeros(self.count, dtype=np.float32)
+        N.lib().pdas_batch_diagnostics(self._h, cp(fp64), cp(unrefined), cp(time_us))
+        return dict(status=status, iters=iters, gap=gap, fp64_iters=fp64, unrefined=unrefined, time_us=time_us,
                     ms=N.lib().pdas_batch_last_ms(self._h))
 
     def config(self):

@@ -116,7 +116,7 @@ SIGNATURES = {
     "pdas_batch_solve": ([_H, _P, _P, _P], _I),
     "pdas_batch_config": ([_H, _P, _P, _P, _I], _I),
     "pdas_batch_last_ms": ([_H], _D),
-    "pdas_batch_diagnostics": ([_H, _P, _P], _I),
+    "pdas_batch_diagnostics": ([_H, _P, _P, _P], _I),
     "pdas_batch_last_error_message": ([_H], ctypes.c_char_p),
     "pdas_batch_destroy": ([_H], None),
     "pdas_profile_enable": ([_H, _I], _I),

@@ -58,6 +58,7 @@ struct BatchArgs {
   double* gap;
   int* shifted;    // iterations run with the FP64 factor (after the FP32 factor failed)
   int* unrefined;  // iterations whose refinement stopped without meeting refine_tol
+  float* time_us;  // device time of each LP's solve
   unsigned* ticket;
   double* scratch;  // FP64 tier: per CTA slot, packed lower M / L then 1 / L_pp
   int64_t slot;     // doubles per slot: m_cap (m_cap + 1) / 2 + m_cap
@@ -65,7 +66,7 @@ struct BatchArgs {
 
 // Shared-memory layout for capacities (mc, nc): 16-byte aligned sections.
 struct BatchSmem {
-  size_t L, dinv, zf, vm, D, w, un2, stage, dc, scal, total;
+  size_t L, dinv, zf, vm, pm2, D, w, un2, kidx, stage, dc, scal, total;
 };
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
 __host__ __device__ inline BatchSmem batch_smem(int mc, int nc) {
@@ -75,10 +76,12 @@ __host__ __device__ inline BatchSmem batch_smem(int mc, int nc) {
   o.dinv = p;  p = al16(p + sizeof(float) * mc);
   o.zf = p;    p = al16(p + sizeof(float) * mc);
   o.vm = p;    p = al16(p + sizeof(double) * 6 * mc);
+  o.pm2 = p;   p = al16(p + sizeof(float2) * mc);
   o.D = p;     p = al16(p + sizeof(double) * nc);
   o.w = p;     p = al16(p + sizeof(double) * nc);
   o.un2 = p;   p = al16(p + sizeof(float2) * nc);
-  o.stage = p; p = al16(p + sizeof(float) * mc * 33);
+  o.kidx = p;  p = al16(p + sizeof(int) * nc);
+  o.stage = p; p = al16(p + sizeof(float) * mc * 34);  // (also an FP64 panel of 16 columns, pitch 17)
   o.dc = p;    p = al16(p + sizeof(float) * 64);
   o.scal = p;  p = al16(p + sizeof(double) * 32);
   o.total = p;
@@ -107,6 +110,8 @@ struct Ctx {
   double* D;     // x / s
   double* w;     // A' (an m-vector)
   float2* un2;   // an n-vector as FP32 pairs
+  float2* pm2;   // an m-vector as FP32 pairs
+  int* kidx;     // FP64 tier: the columns kept for the normal matrix
   float* stage;  // [m_cap][33]: 32 columns of A D^1/2
   float* dc;     // 32 entries of D^1/2, or of D as FP32 pairs (64 floats)
   double* scal;  // reduction scratch
@@ -144,16 +149,19 @@ __device__ void blk_gemv(const Ctx& c, const float2* v2, const double* base, dou
     const float* row = c.A + (int64_t)p * c.n;
     double acc = 0.0;
     float hi = 0.f, lo = 0.f;
-    int cnt = 0;
-    for (int j = lane; j < c.n; j += 32) {
-      const float2 v = v2[j];
-      df_madd(hi, lo, __ldg(row + j), v.x, v.y);
-      if (++cnt == 16) {
-        df_flush(acc, hi, lo);
-        cnt = 0;
+    for (int j0 = lane; j0 < c.n; j0 += 32 * 8) {  // 8 loads in flight per lane
+      float av[8];
+      float2 vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + 32 * u;
+        av[u] = j < c.n ? __ldg(row + j) : 0.f;
+        vv[u] = j < c.n ? v2[j] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) df_madd(hi, lo, av[u], vv[u].x, vv[u].y);
+      df_flush(acc, hi, lo);
     }
-    df_flush(acc, hi, lo);
     acc = warp_sum(acc);
     if (lane == 0) out[p] = base ? base[p] - acc : acc;
   }
@@ -166,10 +174,16 @@ __device__ void blk_gemv(const Ctx& c, const float2* v2, const double* base, dou
 template <int T>
 __device__ void blk_gemv_t(const Ctx& c, const double* u, double* out) {
   for (int j = threadIdx.x; j < c.n; j += T) {
+    const float* col = c.A + j;
     double acc = 0.0;
-#pragma unroll 4
-    for (int p = 0; p < c.m; ++p)
-      acc = fma(widen_bits(__float_as_uint(__ldg(c.A + (int64_t)p * c.n + j))), u[p], acc);
+    for (int p0 = 0; p0 < c.m; p0 += 8) {  // 8 loads in flight per thread
+      float av[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) av[k] = p0 + k < c.m ? __ldg(col + (int64_t)(p0 + k) * c.n) : 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (p0 + k < c.m) acc = fma(widen_bits(__float_as_uint(av[k])), u[p0 + k], acc);
+    }
     out[j] = acc;
   }
 }
@@ -230,7 +244,8 @@ __device__ void blk_syrk(const Ctx& c, int m_cap) {
 }
 
 // In-place Cholesky of the packed lower triangle (FP32), right-looking by
-// columns, two block barriers per column.  Returns false on a pivot that is
+// columns, two block barriers per column; the scaled column is read from a
+// contiguous copy (zf) in the trailing update.  Returns false on a pivot that is
 // not positive and finite (the same in every thread).
 template <int T>
 __device__ bool blk_chol(const Ctx& c) {
@@ -241,15 +256,20 @@ __device__ bool blk_chol(const Ctx& c) {
     const float d = c.L[pk(k, k)];
     if (!(d > 0.f) || !isfinite(d)) return false;
     const float rs = inv_sqrt32(d);
-    for (int r = k + 1 + threadIdx.x; r < m; r += T) c.L[pk(r, k)] *= rs;
+    for (int r = k + 1 + threadIdx.x; r < m; r += T) {  // the scaled column, also kept in zf
+      const float v = c.L[pk(r, k)] * rs;
+      c.L[pk(r, k)] = v;
+      c.zf[r] = v;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       c.L[pk(k, k)] = d * rs;
       c.dinv[k] = rs;
     }
     for (int r = k + 1 + wp; r < m; r += NW) {
-      const float lrk = c.L[pk(r, k)];
-      for (int q = k + 1 + lane; q <= r; q += 32) c.L[pk(r, q)] = fmaf(-lrk, c.L[pk(q, k)], c.L[pk(r, q)]);
+      const float lrk = c.zf[r];
+      float* row = c.L + pk(r, 0);
+      for (int q = k + 1 + lane; q <= r; q += 32) row[q] = fmaf(-lrk, c.zf[q], row[q]);
     }
   }
   __syncthreads();
@@ -264,11 +284,12 @@ __device__ void blk_precond(const Ctx& c, const double* v, double* out) {
   for (int i = threadIdx.x; i < m; i += T) c.zf[i] = (float)v[i];
   __syncthreads();
   if (threadIdx.x < 32) {
-    for (int k = 0; k < m; ++k) {  // L z = v
-      const float zk = c.zf[k] * c.dinv[k];
-      for (int r = k + 1 + lane; r < m; r += 32) c.zf[r] = fmaf(-c.L[pk(r, k)], zk, c.zf[r]);
-      __syncwarp();
-      if (lane == 0) c.zf[k] = zk;
+    for (int r = 0; r < m; ++r) {  // L z = v, row by row (contiguous packed rows)
+      const float* row = c.L + pk(r, 0);
+      float t = 0.f;
+      for (int k = lane; k < r; k += 32) t = fmaf(row[k], c.zf[k], t);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) c.zf[r] = (c.zf[r] - t) * c.dinv[r];
       __syncwarp();
     }
     for (int k = m - 1; k >= 0; --k) {  // L' y = z
@@ -286,26 +307,27 @@ __device__ void blk_precond(const Ctx& c, const double* v, double* out) {
 
 // ---- the FP64 tier: M and L (FP64) in the CTA's global scratch slot ----
 
-// M = A D A' (FP64, packed lower) in double-float on the FP32 pipes: the
-// same 32-column chunks of A as blk_syrk (unscaled), D_k as an FP32 pair,
+// M_K = A_K D_K A_K' (FP64, packed lower) over the nk columns listed in
+// kidx, in double-float on the FP32 pipes: 32-column chunks of A_K staged as
+// in blk_syrk (unscaled), D_k as an FP32 pair,
 // (A_qk D_k) split exactly by FMA, the products accumulated as FP32 pairs
 // over the chunk and flushed into FP64 once per chunk.
 template <int T>
-__device__ void blk_syrk_df(const Ctx& c, int m_cap, double* M) {
+__device__ void blk_syrk_df(const Ctx& c, int m_cap, double* M, int nk) {
   constexpr int NW = T / 32;
-  const int m = c.m, n = c.n;
+  const int m = c.m, n = nk;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, lr = lane >> 2, lc = lane & 3;
   const int mt = (m + 31) >> 5, ntile = mt * (mt + 1) / 2;
   for (int e = threadIdx.x; e < m * (m + 1) / 2; e += T) M[e] = 0.0;
   for (int k0 = 0; k0 < n; k0 += 32) {
     if (threadIdx.x < 32) {
-      const float2 d = k0 + threadIdx.x < n ? df_split(c.D[k0 + threadIdx.x]) : make_float2(0.f, 0.f);
+      const float2 d = k0 + threadIdx.x < n ? df_split(c.D[c.kidx[k0 + threadIdx.x]]) : make_float2(0.f, 0.f);
       c.dc[threadIdx.x] = d.x;
       c.dc[32 + threadIdx.x] = d.y;
     }
     for (int e = threadIdx.x; e < m_cap * 32; e += T) {
       const int r = e >> 5, kk = e & 31;
-      c.stage[r * 33 + kk] = (r < m && k0 + kk < n) ? __ldg(c.A + (int64_t)r * n + k0 + kk) : 0.f;
+      c.stage[r * 33 + kk] = (r < m && k0 + kk < n) ? __ldg(c.A + (int64_t)r * c.n + c.kidx[k0 + kk]) : 0.f;
     }
     __syncthreads();
     for (int t = wp; t < ntile; t += NW) {
@@ -350,32 +372,57 @@ __device__ void blk_syrk_df(const Ctx& c, int m_cap, double* M) {
   }
 }
 
-// In-place FP64 Cholesky of the packed lower triangle in global memory,
-// right-looking by columns; the scaled column is kept in shared memory (col,
-// m doubles) for the trailing update.  dinv receives 1 / L_kk.  Returns false
-// on a pivot that is not positive and finite.
+// In-place FP64 Cholesky of the packed lower triangle in global memory, in
+// panels of 16 columns: the panel (rows k0.. m-1) is factored in shared
+// memory (the stage area, pitch 17 doubles), written back, and the trailing
+// lower triangle is updated once per panel (16 multiply-adds per entry, one
+// read-modify-write of global memory).  dinv receives 1 / L_kk.  Returns
+// false on a pivot that is not positive and finite.
 template <int T>
-__device__ bool blk_chol64(const Ctx& c, double* L, double* dinv, double* col) {
-  constexpr int NW = T / 32;
+__device__ bool blk_chol64(const Ctx& c, double* L, double* dinv) {
+  constexpr int NW = T / 32, PW = 16, PP = 17;
   const int m = c.m, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int k = 0; k < m; ++k) {
+  double* P = reinterpret_cast<double*>(c.stage);
+  for (int k0 = 0; k0 < m; k0 += PW) {
+    const int kb = m - k0 < PW ? m - k0 : PW, R = m - k0;
     __syncthreads();
-    const double d = L[pk(k, k)];
-    if (!(d > 0.0) || !isfinite(d)) return false;
-    const double lkk = sqrt(d), rs = 1.0 / lkk;
-    for (int r = k + 1 + threadIdx.x; r < m; r += T) {
-      const double v = L[pk(r, k)] * rs;
-      L[pk(r, k)] = v;
-      col[r] = v;
-    }
-    if (threadIdx.x == 0) {
-      L[pk(k, k)] = lkk;
-      dinv[k] = rs;
+    for (int e = threadIdx.x; e < R * PW; e += T) {
+      const int r = e / PW, cc = e % PW;
+      P[r * PP + cc] = (cc < kb && cc <= r) ? L[pk(k0 + r, k0 + cc)] : 0.0;
     }
     __syncthreads();
-    for (int r = k + 1 + wp; r < m; r += NW) {
-      const double lrk = col[r];
-      for (int q = k + 1 + lane; q <= r; q += 32) L[pk(r, q)] = fma(-lrk, col[q], L[pk(r, q)]);
+    for (int cc = 0; cc < kb; ++cc) {
+      const double d = P[cc * PP + cc];
+      if (!(d > 0.0) || !isfinite(d)) return false;
+      const double lkk = sqrt(d), rs = 1.0 / lkk;
+      for (int r = cc + 1 + threadIdx.x; r < R; r += T) P[r * PP + cc] *= rs;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        P[cc * PP + cc] = lkk;
+        dinv[k0 + cc] = rs;
+      }
+      const int nc = kb - cc - 1;  // later panel columns
+      for (int e = threadIdx.x; e < (R - cc - 1) * nc; e += T) {
+        const int r = cc + 1 + e / nc, q = cc + 1 + e % nc;
+        if (q <= r) P[r * PP + q] = fma(-P[r * PP + cc], P[q * PP + cc], P[r * PP + q]);
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < R * kb; e += T) {
+      const int r = e / kb, cc = e % kb;
+      if (cc <= r) L[pk(k0 + r, k0 + cc)] = P[r * PP + cc];
+    }
+    for (int r = kb + wp; r < R; r += NW) {  // trailing: L_rq -= sum_c P_rc P_qc
+      double pr[PW];
+#pragma unroll
+      for (int cc = 0; cc < PW; ++cc) pr[cc] = P[r * PP + cc];
+      double* row = L + pk(k0 + r, k0);
+      for (int q = kb + lane; q <= r; q += 32) {
+        double v = row[q];
+#pragma unroll
+        for (int cc = 0; cc < PW; ++cc) v = fma(-pr[cc], P[q * PP + cc], v);
+        row[q] = v;
+      }
     }
   }
   __syncthreads();
@@ -409,11 +456,43 @@ __device__ void blk_precond64(const Ctx& c, const double* L, const double* dinv,
   __syncthreads();
 }
 
-// out = M v = A (D (A' v)), double-float passes, FP64 result.  Leaves
-// w = A' v.  (base != null: out = base - M v.)
+// out_j = sum_p A_pj u_p in double-float for the FP32-pair vector u2 (m);
+// one thread per column.  Used for the conjugate-gradient operator while the
+// factor is FP32, where D spans fewer orders of magnitude.
 template <int T>
-__device__ void blk_apply_m(const Ctx& c, const double* v, const double* base, double* out) {
-  blk_gemv_t<T>(c, v, c.w);
+__device__ void blk_gemv_t_df(const Ctx& c, const float2* u2, double* out) {
+  for (int j = threadIdx.x; j < c.n; j += T) {
+    const float* col = c.A + j;
+    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
+    for (int p0 = 0; p0 < c.m; p0 += 8) {  // 8 loads in flight per thread
+      float av[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) av[u] = p0 + u < c.m ? __ldg(col + (int64_t)(p0 + u) * c.n) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float2 q = p0 + u < c.m ? u2[p0 + u] : make_float2(0.f, 0.f);
+        df_madd(hi, lo, av[u], q.x, q.y);
+      }
+      if ((p0 & 15) == 8) df_flush(acc, hi, lo);
+    }
+    df_flush(acc, hi, lo);
+    out[j] = acc;
+  }
+}
+
+// out = M v = A (D (A' v)), FP64 result; the outer pass in double-float, the
+// inner one in FP64 (or double-float when df_inner).  Leaves w = A' v.
+// (base != null: out = base - M v.)
+template <int T>
+__device__ void blk_apply_m(const Ctx& c, const double* v, const double* base, double* out, bool df_inner = false) {
+  if (df_inner) {
+    for (int i = threadIdx.x; i < c.m; i += T) c.pm2[i] = df_split(v[i]);
+    __syncthreads();
+    blk_gemv_t_df<T>(c, c.pm2, c.w);
+  } else {
+    blk_gemv_t<T>(c, v, c.w);
+  }
   __syncthreads();
   for (int j = threadIdx.x; j < c.n; j += T) c.un2[j] = df_split(c.D[j] * c.w[j]);
   __syncthreads();
@@ -470,13 +549,36 @@ __device__ void solve_lp(const BatchArgs& a, const BatchLP lp, Ctx& c, int& stat
       tier2 = !blk_chol<T>(c);
     }
     if (tier2) {
-      blk_syrk_df<T>(c, a.m_cap, M64);
+      // the significant columns: D_j >= 1e-10 max D, at least min(n, 1.25 m)
+      // of them (the threshold drops by 16x until enough pass); the factor
+      // of A_K D_K A_K' preconditions the exact M in the refinement
+      double dmx = 0.0;
+      for (int j = threadIdx.x; j < n; j += T) dmx = fmax(dmx, c.D[j]);
+      dmx = bmax<T>(dmx, c.scal);
+      const int want = min(n, (5 * m + 3) / 4);
+      double thr = dmx * 1e-10;
+      for (int guard = 0; guard < 64; ++guard) {
+        int cnt = 0;
+        for (int j = threadIdx.x; j < n; j += T) cnt += c.D[j] >= thr;
+        if ((int)bsum<T>((double)cnt, c.scal) >= want) break;
+        thr *= 0x1p-4;
+      }
+      if (threadIdx.x == 0) {  // ordered compaction
+        int k = 0;
+        for (int j = 0; j < n; ++j)
+          if (c.D[j] >= thr) c.kidx[k++] = j;
+        c.scal[31] = (double)k;
+      }
+      __syncthreads();
+      const int nk = (int)c.scal[31];
+      __syncthreads();
+      blk_syrk_df<T>(c, a.m_cap, M64, nk);
       double dm = 0.0;
       for (int i = threadIdx.x; i < m; i += T) dm = fmax(dm, M64[pk(i, i)]);
       mnorm = bmax<T>(dm, c.scal);
       // (a non-positive FP64 pivot means M is singular to working precision at
       // this iterate: a nearly degenerate LP close to its optimum)
-      if (!blk_chol64<T>(c, M64, dinv64, c.w)) {
+      if (!blk_chol64<T>(c, M64, dinv64)) {
         status = PDAS_ERR_NOT_SPD;
         break;
       }
@@ -517,7 +619,7 @@ __device__ void solve_lp(const BatchArgs& a, const BatchLP lp, Ctx& c, int& stat
       };
       restart();
       for (int k = 0; k < a.refine_max && rz > 0.0 && isfinite(rz); ++k) {
-        blk_apply_m<T>(c, c.p, nullptr, c.q);
+        blk_apply_m<T>(c, c.p, nullptr, c.q, !tier2);
         double t = 0.0;
         for (int i = threadIdx.x; i < m; i += T) t += c.p[i] * c.q[i];
         const double pq = bsum<T>(t, c.scal);
@@ -618,6 +720,8 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs a) {
   c.D = reinterpret_cast<double*>(batch_smem_raw + L.D);
   c.w = reinterpret_cast<double*>(batch_smem_raw + L.w);
   c.un2 = reinterpret_cast<float2*>(batch_smem_raw + L.un2);
+  c.pm2 = reinterpret_cast<float2*>(batch_smem_raw + L.pm2);
+  c.kidx = reinterpret_cast<int*>(batch_smem_raw + L.kidx);
   c.stage = reinterpret_cast<float*>(batch_smem_raw + L.stage);
   c.dc = reinterpret_cast<float*>(batch_smem_raw + L.dc);
   c.scal = reinterpret_cast<double*>(batch_smem_raw + L.scal);
@@ -636,8 +740,13 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs a) {
     c.n = lp.n;
     int status, iters, n_shift, n_unref;
     double gap;
+    uint64_t t0 = 0;
+    if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     solve_lp<T>(a, lp, c, status, iters, gap, n_shift, n_unref);
     if (threadIdx.x == 0) {
+      uint64_t t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      a.time_us[id] = (float)((t1 - t0) * 1e-3);
       a.status[id] = status;
       a.iters[id] = iters;
       a.gap[id] = gap;
@@ -689,6 +798,7 @@ struct pdas_batch_ctx {
   double* gap = nullptr;
   int* shifted = nullptr;
   int* unrefined = nullptr;
+  float* time_us = nullptr;
   unsigned* tickets = nullptr;  // one per bucket
   double* scratch = nullptr;    // FP64 tier slots, one per LP of each bucket
   int* h_status = nullptr;      // pinned mirrors
@@ -696,6 +806,7 @@ struct pdas_batch_ctx {
   double* h_gap = nullptr;
   int* h_shifted = nullptr;
   int* h_unrefined = nullptr;
+  float* h_time_us = nullptr;
   struct Bucket {
     int m_bound = 0, m_cap = 0, n_cap = 0, count = 0, offset = 0, threads = 256, grid = 0;
     int64_t slot = 0, scratch_off = 0;  // doubles per FP64-tier slot; first slot of the bucket
@@ -747,6 +858,7 @@ BatchArgs bucket_args(const pdas_batch_ctx* h, int bi, double* x, double* y, dou
   a.gap = h->gap;
   a.shifted = h->shifted;
   a.unrefined = h->unrefined;
+  a.time_us = h->time_us;
   a.ticket = h->tickets + bi;
   a.scratch = h->scratch + B.scratch_off;
   a.slot = B.slot;
@@ -832,6 +944,8 @@ pdas_status capture(pdas_batch_ctx* h) {
     e = cudaMemcpyAsync(h->h_shifted, h->shifted, sizeof(int) * h->count, cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->h_unrefined, h->unrefined, sizeof(int) * h->count, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_time_us, h->time_us, sizeof(float) * h->count, cudaMemcpyDeviceToHost, h->st);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
   if (e != cudaSuccess) {
@@ -881,6 +995,8 @@ void pdas_batch_destroy(pdas_batch_handle h) {
   if (h->unrefined) cudaFree(h->unrefined);
   if (h->h_shifted) cudaFreeHost(h->h_shifted);
   if (h->h_unrefined) cudaFreeHost(h->h_unrefined);
+  if (h->time_us) cudaFree(h->time_us);
+  if (h->h_time_us) cudaFreeHost(h->h_time_us);
   if (h->tickets) cudaFree(h->tickets);
   if (h->scratch) cudaFree(h->scratch);
   if (h->h_status) cudaFreeHost(h->h_status);
@@ -974,6 +1090,8 @@ pdas_status pdas_batch_create(int count, const int* m, const int* n, const float
   if (e == cudaSuccess) e = cudaMalloc(&h->unrefined, sizeof(int) * count);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_shifted, sizeof(int) * count);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_unrefined, sizeof(int) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&h->time_us, sizeof(float) * count);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_time_us, sizeof(float) * count);
   if (e == cudaSuccess) e = cudaMalloc(&h->tickets, sizeof(unsigned) * kBuckets);
   if (e == cudaSuccess) e = cudaMalloc(&h->scratch, sizeof(double) * std::max<int64_t>(scratch_total, 1));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(int) * count);
@@ -1040,10 +1158,11 @@ int pdas_batch_config(pdas_batch_handle h, int* m_bound, int* threads, int* lp_c
 
 double pdas_batch_last_ms(pdas_batch_handle h) { return h ? h->last_ms : -1.0; }
 
-pdas_status pdas_batch_diagnostics(pdas_batch_handle h, int* shifted_out, int* unrefined_out) {
+pdas_status pdas_batch_diagnostics(pdas_batch_handle h, int* fp64_out, int* unrefined_out, float* time_us_out) {
   if (!h) return PDAS_ERR_ARG;
-  if (shifted_out) memcpy(shifted_out, h->h_shifted, sizeof(int) * h->count);
+  if (fp64_out) memcpy(fp64_out, h->h_shifted, sizeof(int) * h->count);
   if (unrefined_out) memcpy(unrefined_out, h->h_unrefined, sizeof(int) * h->count);
+  if (time_us_out) memcpy(time_us_out, h->h_time_us, sizeof(float) * h->count);
   return PDAS_OK;
 }
 
