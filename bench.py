@@ -436,6 +436,49 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """The batch configuration (512 LPs, m ~ U{16..256}, n = m U{2..4}, FP32,
+    gap 1e-7) through pdas_batch: K timed graph replays after W warm-up
+    replays, each from the seeded starts; prints one JSON line (not the
+    headline metric: total Newton iterations of all LPs per second)."""
+    import torch
+
+    import paper_1502_03543_gb300 as P
+    from paper_1502_03543_gb300 import build as B
+
+    B.build()
+    spec = lpgen.BATCHES["batch_512_f32"]
+    lps = lpgen.batch(spec["count"], seed=spec["seed"], storage=spec["storage"])
+    pk = lpgen.pack(lps)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    A = torch.from_numpy(np.ascontiguousarray(pk["A"], dtype=np.float32)).cuda()
+    b, c = dv(pk["b"]), dv(pk["c"])
+    x0, y0, s0 = dv(pk["x0"]), dv(pk["y0"]), dv(pk["s0"])
+    x, y, s = x0.clone(), y0.clone(), s0.clone()
+    S = P.BatchSolver(pk["m"], pk["n"], A, b, c, x, y, s, tol=spec["tol"])
+    times, iters, out = [], 0, None
+    for k in range(args.warmup + args.steps):
+        x.copy_(x0)
+        y.copy_(y0)
+        s.copy_(s0)
+        out = S.solve()
+        if k >= args.warmup:
+            times.append(out["ms"])
+            iters += int(out["iters"].sum())
+    cfg = S.config()
+    S.close()
+    ms = float(np.sum(times))
+    st, cnt = np.unique(out["status"], return_counts=True)
+    print(json.dumps(dict(metric="Newton iters/s (batch of 512 small LPs)", value=iters / (ms * 1e-3),
+                          unit="Newton iters/s", ms_per_batch=ms / len(times), steps=args.steps, warmup=args.warmup,
+                          iterations_per_batch=iters // len(times), higher_is_better=True,
+                          config=dict(workload="batch_512_f32", count=len(lps), tol=spec["tol"], alpha=0.95,
+                                      buckets=[dict(m_bound=m_, threads=t_, lps=n_) for m_, t_, n_ in cfg]),
+                          statuses={str(int(a)): int(b_) for a, b_ in zip(st, cnt)},
+                          fp64_tier_iterations=int(out["fp64_iters"].sum()),
+                          slowest_lp_ms=float(out["time_us"].max() * 1e-3))))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,10 +493,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["step", "normal", "factor"], default="step",
                     help="normal: time only the normal-matrix stage; factor: also the Cholesky (for profiles)")
+    ap.add_argument("--batch", action="store_true", help="time the 512-LP batch configuration instead")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step":
+    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step" and not args.batch:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.batch:
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.kernel in ("normal", "factor"):
         run_normal_only(args)
