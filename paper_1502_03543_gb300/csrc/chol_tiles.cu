@@ -8,6 +8,10 @@
 //   FINAL(i, l)    apply M_il -= L_i,l-1 L_l,l-1', wait for FINAL(l, l),
 //                  then L_il = M_il L_ll^{-T}
 //   UPDATE(i,l,k)  M_il -= L_ik L_lk'   for k <= l - 2 (rank 128)
+// In the FP32 factor every product L_ik L_lk' runs on the tcgen05 tensor
+// cores (BF16 operand planes, FP32 accumulation in tensor memory; see the
+// section "FP32 products on the tensor cores"); the FP64 instantiation keeps
+// SIMT products.
 // A tile's last update and its factorisation or triangular solve run in one
 // task on the tile held in registers, so the dependency chain of the
 // factorisation (FINAL(l,l) -> FINAL(l+1,l) -> FINAL(l+1,l+1) ...) has no
@@ -15,10 +19,14 @@
 // triangle has a counter in global memory: the number of updates applied to
 // it, then l + 1 once it holds its final L values.
 //
-// CTAs take tasks from a ticket counter in a fixed list order.  In that order
-// every task comes after all tasks it waits for, so a CTA only waits on tasks
-// that running CTAs hold, and those finish by induction on the order; every
-// wait is also bounded (2 s, PDAS_ERR_TIMEOUT).  The order itself comes from
+// Block 0 runs the diagonal tasks FINAL(l, l) in order of l, so the task at
+// the head of the dependency chain never queues behind trailing updates.  The
+// other CTAs take the remaining tasks from a ticket counter in a fixed list
+// order.  In that order every task comes after all tasks it waits for (block
+// 0's tasks included), so the first unfinished task is always held by a
+// running CTA and has all it waits for done, and every task finishes by
+// induction on the order; every wait is also bounded (2 s, PDAS_ERR_TIMEOUT).
+// The order itself comes from
 // a list schedule simulated on the host for the number of resident CTAs:
 // the ready task with the longest remaining path to the end of the
 // factorisation (its "bottom level", from per-task cost estimates) goes
@@ -29,7 +37,10 @@
 #include <queue>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "sync_util.cuh"
+#include "tc_util.cuh"
 #include "tile_core.cuh"
 
 namespace pdas {
@@ -51,14 +62,26 @@ constexpr int upd_vec() {  // elements per 16-byte load
   return 16 / (int)sizeof(T);
 }
 
+// Tensor-core products (FP32 factor): the two K chunks of 64 columns of both
+// operand tiles pass through shared memory as three BF16 planes each
+// (x = x0 + x1 + x2, 8 significant bits apiece, so every product of planes is
+// exact in FP32), 128 rows x 128 bytes, 128-byte swizzle.
+constexpr int kTcPlaneBytes = kBig * 128;
+constexpr int kTcOpsBytes = 6 * kTcPlaneBytes;  // A0 A1 A2 | B0 B1 B2
+constexpr uint32_t kTcCols = 256;               // TMEM: leading term | the five correction terms
+constexpr uint32_t kTcIdesc = tc::idesc_bf16(kBig, kBig);
+
 template <typename T>
 struct TileCholSmem {
   union {
-    T stage[2][2][kBig][upd_pitch<T>()];  // UPDATE: [buffer][row tile i | row tile l][row][k]
-    T ls[kBig][kBig + 1];                 // TRSM: the factor of the diagonal tile
+    T stage[2][2][kBig][upd_pitch<T>()];  // UPDATE (FP64): [buffer][row tile i | row tile l][row][k]
+    T ls[kBig][kBig + 1];                 // TRSM: the factor of the diagonal tile; FP32 products: D
+    unsigned char tc_ops[kTcOpsBytes + 1024];  // FP32 products: the BF16 planes (1024-aligned inside)
   };
   T cb[2][kBig];  // column buffers of the POTRF / TRSM sweeps (double-buffered)
   T rcp[kBig];    // TRSM: 1 / L_cc; POTRF: the diagonal on entry
+  unsigned long long mma_bar;  // FP32 products: completion of the issued MMAs
+  uint32_t tmem_slot;
   int4 task;
   int go;
 };
@@ -174,44 +197,50 @@ __device__ __forceinline__ void rank_update(T (&acc)[8][8], int64_t m, int64_t l
   }
 }
 
-// 1 / sqrt(d): the hardware estimate refined by one Newton step (within
-// about 2 ulp in FP32; the FP32 factor is a preconditioner); IEEE for FP64.
-__device__ __forceinline__ float inv_sqrt(float d) {
-  const float r = rsqrtf(d);
-  return r * fmaf(-0.5f * d * r, r, 1.5f);
-}
+// 1 / sqrt(d) of a pivot: the hardware estimate (within 2 ulp in FP32; the
+// FP32 factor is a preconditioner, and every entry of a column is scaled by
+// the same value); IEEE for FP64.
+__device__ __forceinline__ float inv_sqrt(float d) { return rsqrtf(d); }
 __device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
 
-// Step C of the right-looking factorisation of a 32 x 32 block held by one
-// warp (lane = row): the pivot comes by shuffle from lane C; every lane
-// scales its entry of column C and publishes it in a 32-entry column buffer
-// (double-buffered, so one warp barrier per step); each lane then reads the
-// column entries it needs with 16-byte broadcast loads and updates its row.
-// Recursion on C keeps every register index a compile-time constant.
-template <typename T, int C>
-__device__ __forceinline__ void warp_potrf_step(T (&row)[32], int lane, int& bad, T& myrs, T* cbuf) {
-  const T d = __shfl_sync(0xffffffffu, row[C], C);
-  if (bad < 0 && pivot_bad(d)) bad = C;  // (the sweep runs on; the block is discarded)
-  const T rs = inv_sqrt(d);
-  const T v = lane > C ? row[C] * rs : (lane == C ? d * rs : T(0));
-  if (lane >= C) row[C] = v;
-  if (lane == C) myrs = rs;
-  T* col = cbuf + (C & 1) * 32;
-  col[lane] = v;
-  __syncwarp();
-  constexpr int Q0 = (C + 1) & ~3;  // first 4-aligned group holding an entry q > C
+// Right-looking factorisation of a 32 x 32 block held by one warp (lane =
+// row), as a loop over the pivot column C: row[] is shifted left every step,
+// so row[0] always holds column C and the loop body has fixed register
+// indices.  Per step the lane of row C + 1 forms the next pivot from its own
+// new entry and broadcasts it (one shuffle on the dependency chain); the new
+// column goes to a 32-entry window of a shared buffer (indexed relative to
+// C, double-buffered) that every lane reads with 16-byte loads to update its
+// later entries.  Finished entries of column C go to out[C] (out = this
+// lane's row of the block; rows above the diagonal are not written).
+template <typename T>
+__device__ __forceinline__ void warp_potrf(T (&row)[32], int lane, int& bad, T& myrs, T* cbuf, T* out) {
+  constexpr int VN = 16 / (int)sizeof(T);
+  struct alignas(16) V {
+    T v[VN];
+  };
+  T d = __shfl_sync(0xffffffffu, row[0], 0);
+#pragma unroll 1
+  for (int C = 0; C < 32; ++C) {
+    if (bad < 0 && pivot_bad(d)) bad = C;  // (the sweep runs on; the block is discarded)
+    const T rs = inv_sqrt(d);
+    const T v = lane > C ? row[0] * rs : (lane == C ? d * rs : T(0));
+    if (lane >= C) out[C] = v;
+    if (lane == C) myrs = rs;
+    const T dn = __shfl_sync(0xffffffffu, fma(-v, v, row[1]), (C + 1) & 31);
+    T* col = cbuf + (C & 1) * 64;
+    col[lane - C + 32] = v;  // entry q (relative to C) at 32 + q; lanes below C write below the window
+    __syncwarp();
 #pragma unroll
-  for (int q4 = Q0; q4 < 32; q4 += 4) {
-    T c4[4];
+    for (int q4 = 0; q4 < 32; q4 += VN) {
+      const V c4 = *reinterpret_cast<const V*>(col + 32 + q4);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) c4[e] = col[q4 + e];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int q = q4 + e;
-      if (q > C && lane >= q) row[q] = fma(-v, c4[e], row[q]);
+      for (int e = 0; e < VN; ++e)
+        if (q4 + e >= 1) row[q4 + e] = fma(-v, c4.v[e], row[q4 + e]);
     }
+#pragma unroll
+    for (int q = 0; q < 31; ++q) row[q] = row[q + 1];
+    d = dn;
   }
-  if constexpr (C + 1 < 32) warp_potrf_step<T, C + 1>(row, lane, bad, myrs, cbuf);
 }
 
 // Factorisation of the diagonal tile (held in acc) through shared memory in
@@ -249,15 +278,9 @@ __device__ __forceinline__ bool tile_potrf(const T (&acc)[8][8], int64_t m, int6
       for (int q = 0; q < 32; ++q) row[q] = S[c0 + lane][c0 + q];
       int bad = -1;
       T myrs = T(1);
-      warp_potrf_step<T, 0>(row, lane, bad, myrs, &sm.cb[0][0]);
+      warp_potrf<T>(row, lane, bad, myrs, &sm.cb[0][0], &S[c0 + lane][c0]);
       sm.rcp[c0 + lane] = myrs;
-      if (bad >= 0) {
-        if (lane == 0) s_fail = c0 + bad;
-      } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (q <= lane) S[c0 + lane][c0 + q] = row[q];
-      }
+      if (bad >= 0 && lane == 0) s_fail = c0 + bad;
     }
     __syncthreads();
     if (s_fail >= 0) break;
@@ -378,6 +401,229 @@ __device__ __forceinline__ void tile_inverse(T (&acc)[8][8], int64_t m, int64_t 
     for (int j = 0; j < 8; ++j) U[(ty + 16 * i) * kBig + tx + 16 * j] = acc[i][j];
 }
 
+// ---- FP32 products on the tensor cores ---------------------------------------
+// D = L_ik L_lk' for one tile column k (K = 128) of the FP32 factor, with
+// every operand split into three BF16 planes: the leading term A0 B0' goes
+// to TMEM columns [0, 128), the five terms A0 B1' + A1 B0' + A0 B2' + A1 B1' +
+// A2 B0' (each at most 2^-8 of it) to columns [128, 256).  The dropped terms
+// are below 2^-24 relative, so the sum carries FP32 accuracy; the tensor
+// core's FP32 accumulation rounds toward zero, and keeping the leading term
+// in an accumulator of its own holds that to 8 accumulation steps.
+
+// Item t of this thread (t = 0..3): row e / 8 and BF16 chunk e % 8 (8
+// columns) of the 64-column K chunk, e = tid + 256 t.  Rows past m read 0.
+template <bool DIAG>
+__device__ __forceinline__ void tc_fetch(const float* M, int64_t ldm, int64_t m, int64_t pa, int64_t pb, int64_t kcol,
+                                         float4 (&v)[2][4][2]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int e = threadIdx.x + kThreads * t, r = e >> 3, c8 = e & 7;
+#pragma unroll
+    for (int op = 0; op < (DIAG ? 1 : 2); ++op) {
+      const int64_t row = (op ? pb : pa) + r;
+      if (row < m) {
+        const float4* src = reinterpret_cast<const float4*>(M + row * ldm + kcol + 8 * c8);
+        v[op][t][0] = __ldcg(src);
+        v[op][t][1] = __ldcg(src + 1);
+      } else {
+        v[op][t][0] = v[op][t][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+}
+
+// x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)
+// (each difference exact in FP32), for the pair (a, b): word s holds the
+// BF16 term s of a (low half) and of b (high half).
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void bf16x2_split3(float a, float b, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  w0 = bf16x2_bits(a, b);
+  const float ra = a - __uint_as_float(w0 << 16), rb = b - __uint_as_float(w0 & 0xffff0000u);
+  w1 = bf16x2_bits(ra, rb);
+  const float sa = ra - __uint_as_float(w1 << 16), sb = rb - __uint_as_float(w1 & 0xffff0000u);
+  w2 = bf16x2_bits(sa, sb);
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void tc_split_store(const float4 (&v)[2][4][2], unsigned char* ops) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int e = threadIdx.x + kThreads * t, r = e >> 3, c8 = e & 7;
+    const int off = r * 128 + ((c8 ^ (r & 7)) << 4);
+#pragma unroll
+    for (int op = 0; op < (DIAG ? 1 : 2); ++op) {
+      const float x[8] = {v[op][t][0].x, v[op][t][0].y, v[op][t][0].z, v[op][t][0].w,
+                          v[op][t][1].x, v[op][t][1].y, v[op][t][1].z, v[op][t][1].w};
+      uint32_t w[3][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bf16x2_split3(x[2 * q], x[2 * q + 1], w[0][q], w[1][q], w[2][q]);
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp)
+        *reinterpret_cast<uint4*>(ops + (3 * op + sp) * kTcPlaneBytes + off) = make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
+    }
+  }
+}
+
+// One thread: the 24 MMAs of a K chunk, then a commit to the barrier.
+__device__ __forceinline__ void tc_issue(uint32_t ops, bool diag, uint32_t tmem, bool first, uint32_t bar) {
+  tc::fence_after();
+  const uint32_t a0 = ops, a1 = ops + kTcPlaneBytes, a2 = ops + 2 * kTcPlaneBytes;
+  const uint32_t b0 = diag ? ops : ops + 3 * kTcPlaneBytes, b1 = b0 + kTcPlaneBytes, b2 = b0 + 2 * kTcPlaneBytes;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {  // K = 16 per MMA: 32 bytes along the swizzled row
+    const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+    const uint64_t da0 = tc::sdesc_sw128(a0) + 2 * ks, da1 = tc::sdesc_sw128(a1) + 2 * ks,
+                   da2 = tc::sdesc_sw128(a2) + 2 * ks;
+    const uint64_t db0 = tc::sdesc_sw128(b0) + 2 * ks, db1 = tc::sdesc_sw128(b1) + 2 * ks,
+                   db2 = tc::sdesc_sw128(b2) + 2 * ks;
+    tc::umma_f16(tmem, da0, db0, kTcIdesc, acc);
+    tc::umma_f16(tmem + kBig, da0, db1, kTcIdesc, acc);
+    tc::umma_f16(tmem + kBig, da1, db0, kTcIdesc, 1u);
+    tc::umma_f16(tmem + kBig, da0, db2, kTcIdesc, 1u);
+    tc::umma_f16(tmem + kBig, da1, db1, kTcIdesc, 1u);
+    tc::umma_f16(tmem + kBig, da2, db0, kTcIdesc, 1u);
+  }
+  tc::umma_commit(bar);
+}
+
+// Every thread: bounded wait for the next completion of the MMA barrier.  On
+// a timeout the status is set and the MMAs get a second bounded wait to
+// drain (the caller then leaves, and TMEM is freed).
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t& parity, Scalars* sc) {
+  const bool ok = tc::mbar_wait(bar, parity, nullptr);
+  if (!ok) {
+    atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+    tc::mbar_wait(bar, parity, nullptr);
+  }
+  parity ^= 1u;
+  tc::fence_after();
+  return ok;
+}
+
+// All threads: stage both K chunks and issue their MMAs; returns with the
+// second chunk's MMAs in flight (finish with tc_product_end).  The second
+// chunk's loads are in flight while the first chunk's MMAs run.
+template <bool DIAG>
+__device__ __forceinline__ bool tc_product_begin(int64_t m, int64_t ldm, const float* M, int64_t pa, int64_t pb,
+                                                 int64_t k0, TileCholSmem<float>& sm, uint32_t tmem,
+                                                 uint32_t& parity, Scalars* sc) {
+  unsigned char* ops = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm.tc_ops) + 1023) & ~uintptr_t(1023));
+  const uint32_t ops_s = tc::smem_u32(ops), bar = tc::smem_u32(&sm.mma_bar);
+  float4 v[2][4][2];
+  tc_fetch<DIAG>(M, ldm, m, pa, pb, k0, v);
+  tc_split_store<DIAG>(v, ops);
+  tc_fetch<DIAG>(M, ldm, m, pa, pb, k0 + 64, v);
+  tc::fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) tc_issue(ops_s, DIAG, tmem, true, bar);
+  const bool ok = tc_wait(bar, parity, sc);  // the planes are reused
+  tc_split_store<DIAG>(v, ops);
+  tc::fence_proxy_async();
+  if (!__syncthreads_and(ok)) return false;
+  if (threadIdx.x == 0) tc_issue(ops_s, DIAG, tmem, false, bar);
+  return true;
+}
+
+__device__ __forceinline__ bool tc_product_end(TileCholSmem<float>& sm, uint32_t& parity, Scalars* sc) {
+  const bool ok = tc_wait(tc::smem_u32(&sm.mma_bar), parity, sc);
+  return __syncthreads_and(ok);
+}
+
+// UPDATE epilogue: C -= D on the tile (p0, q0) in global memory, by whole
+// rows with 16-byte accesses: warp w owns rows w + 8 j (j = 0..15), lane the
+// columns 4 lane .. + 3.  tc_load_rows prefetches the warp's rows of C (while
+// the last MMAs run); tc_sub_global drains TMEM (warp w: lanes 32 (w % 4) ..
+// + 31, one row per thread, columns 64 (w / 4) .. + 63) into a staging area
+// (the operand planes are free once the MMAs completed) and applies it.  On a
+// diagonal tile only q <= p is written.
+constexpr int kStagePitch = kBig + 4;  // 16-byte rows; 8 consecutive rows in distinct bank groups
+static_assert(kBig * kStagePitch * (int)sizeof(float) <= kTcOpsBytes, "the staging area lies inside the planes");
+constexpr int kRowsPerWarp = kBig / (kThreads / 32);
+
+__device__ __forceinline__ void tc_load_rows(float4 (&x)[kRowsPerWarp], int64_t m, int64_t ldm, const float* M,
+                                             int64_t p0, int64_t q0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = q0 + 4 * lane;
+#pragma unroll
+  for (int j = 0; j < kRowsPerWarp; ++j) {
+    const int64_t p = p0 + warp + (kThreads / 32) * j;
+    x[j] = (p < m && q + 3 < m) ? __ldcg(reinterpret_cast<const float4*>(M + p * ldm + q)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void tc_sub_global(float4 (&x)[kRowsPerWarp], int64_t m, int64_t ldm, float* M, int64_t p0,
+                                              int64_t q0, uint32_t tmem, TileCholSmem<float>& sm) {
+  float(*S)[kStagePitch] = reinterpret_cast<float(*)[kStagePitch]>(sm.tc_ops);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3, half = warp >> 2;
+  const int r = quarter * 32 + lane;
+  const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    const int c = half * 64 + g * 16;
+    uint32_t lead[16], corr[16];
+    tc::tmem_ld16(taddr + c, lead);
+    tc::tmem_ld16(taddr + kBig + c, corr);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      *reinterpret_cast<float4*>(&S[r][c + 4 * v]) =
+          make_float4(__uint_as_float(lead[4 * v]) + __uint_as_float(corr[4 * v]),
+                      __uint_as_float(lead[4 * v + 1]) + __uint_as_float(corr[4 * v + 1]),
+                      __uint_as_float(lead[4 * v + 2]) + __uint_as_float(corr[4 * v + 2]),
+                      __uint_as_float(lead[4 * v + 3]) + __uint_as_float(corr[4 * v + 3]));
+  }
+  tc::fence_before();
+  __syncthreads();
+  const int64_t q = q0 + 4 * lane;
+#pragma unroll
+  for (int j = 0; j < kRowsPerWarp; ++j) {
+    const int rr = warp + (kThreads / 32) * j;
+    const int64_t p = p0 + rr;
+    if (p < m) {
+      const float4 dd = *reinterpret_cast<const float4*>(&S[rr][4 * lane]);
+      float* dst = M + p * ldm + q;
+      if (q + 3 < m && (!DIAG || q + 3 <= p)) {
+        *reinterpret_cast<float4*>(dst) = make_float4(x[j].x - dd.x, x[j].y - dd.y, x[j].z - dd.z, x[j].w - dd.w);
+      } else {
+        const float de[4] = {dd.x, dd.y, dd.z, dd.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (q + e < m && (!DIAG || q + e <= p)) dst[e] = __ldcg(dst + e) - de[e];
+      }
+    }
+  }
+  __syncthreads();  // the staging area holds the next task's operand planes
+}
+
+// FINAL epilogue: acc (tile layout) -= D, through the staging area.
+__device__ __forceinline__ void tc_sub_acc(float (&acc)[8][8], uint32_t tmem, TileCholSmem<float>& sm) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int r = quarter * 32 + lane;
+  const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+  for (int g = 0; g < 2; ++g) {
+    const int c = half * 64 + g * 32;
+    uint32_t dv[32];
+    tc::tmem_ld32(taddr + c, dv);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sm.ls[r][c + j] = __uint_as_float(dv[j]);
+    tc::tmem_ld32(taddr + kBig + c, dv);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sm.ls[r][c + j] += __uint_as_float(dv[j]);
+  }
+  tc::fence_before();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] -= sm.ls[ty + 16 * i][tx + 16 * j];
+  __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     k_chol_tiles(int64_t m, int64_t ldm, T* M, T* dinv, T* Uinv, const int4* __restrict__ tasks, int ntasks, int nb,
@@ -385,12 +631,41 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
   extern __shared__ __align__(16) unsigned char chol_tiles_smem[];
   TileCholSmem<T>& sm = *reinterpret_cast<TileCholSmem<T>*>(chol_tiles_smem);
   const int tid = threadIdx.x;
+  constexpr bool kTc = sizeof(T) == 4;  // FP32 factor: products on the tensor cores
+  uint32_t tmem = 0, mma_parity = 0;
+  if constexpr (kTc) {
+    if (tid == 0) {
+      tc::mbar_init(tc::smem_u32(&sm.mma_bar), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((tid >> 5) == 0) tc::tmem_alloc(tc::smem_u32(&sm.tmem_slot), kTcCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    tmem = sm.tmem_slot;
+  }
+  int chain_l = 0;  // block 0: the next diagonal task
   for (;;) {
     if (tid == 0) {  // take a task and wait for the tiles it starts from
       int go = 0;
-      const unsigned t = atomicAdd(ticket, 1u);
-      if (t < (unsigned)ntasks && !dev_failed(sc)) {
-        const int4 d = tasks[t];
+      bool have = false;
+      int4 d = make_int4(0, 0, 0, 0);
+      if (blockIdx.x == 0) {  // FINAL(l, l) in order of l
+        have = chain_l < nb;
+        d = make_int4(TK_FINAL_DIAG, chain_l, chain_l, chain_l - 1);
+        ++chain_l;
+      } else {  // the other tasks in list order
+        for (;;) {
+          const unsigned t = atomicAdd(ticket, 1u);
+          if (t >= (unsigned)ntasks) break;
+          d = tasks[t];
+          if (d.x != TK_FINAL_DIAG) {
+            have = true;
+            break;
+          }
+        }
+      }
+      if (have && !dev_failed(sc)) {
         sm.task = d;
         const int64_t i = d.y, l = d.z, k = d.w;
         if (d.x == TK_UPDATE)
@@ -407,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
       sm.go = go;
     }
     __syncthreads();
-    if (!sm.go) return;
+    if (!sm.go) break;
     const int4 d = sm.task;
     const int i = d.y, l = d.z;
     const int64_t p0 = (int64_t)i * kBig, q0 = (int64_t)l * kBig;
@@ -419,22 +694,56 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
       continue;
     }
     if (d.x == TK_UPDATE) {
-      load_tile(acc, M, ldm, m, p0, q0, i == l);
-      if (i == l) rank_update<T, true>(acc, m, ldm, M, i, l, d.w, sm);
-      else rank_update<T, false>(acc, m, ldm, M, i, l, d.w, sm);
-      store_tile(acc, M, ldm, m, p0, q0, i == l);
+      const int64_t k0 = (int64_t)d.w * kBig;
+      if constexpr (kTc) {
+        const bool ok = i == l ? tc_product_begin<true>(m, ldm, M, p0, q0, k0, sm, tmem, mma_parity, sc)
+                               : tc_product_begin<false>(m, ldm, M, p0, q0, k0, sm, tmem, mma_parity, sc);
+        if (!ok) break;
+        float4 cx[kRowsPerWarp];
+        tc_load_rows(cx, m, ldm, M, p0, q0);
+        if (!tc_product_end(sm, mma_parity, sc)) break;
+        if (i == l) tc_sub_global<true>(cx, m, ldm, M, p0, q0, tmem, sm);
+        else tc_sub_global<false>(cx, m, ldm, M, p0, q0, tmem, sm);
+      } else {
+        load_tile(acc, M, ldm, m, p0, q0, i == l);
+        if (i == l) rank_update<T, true>(acc, m, ldm, M, i, l, d.w, sm);
+        else rank_update<T, false>(acc, m, ldm, M, i, l, d.w, sm);
+        store_tile(acc, M, ldm, m, p0, q0, i == l);
+      }
       val = d.w + 1;
     } else if (d.x == TK_FINAL_DIAG) {
-      load_tile(acc, M, ldm, m, p0, p0, true);
-      if (l > 0) rank_update<T, true>(acc, m, ldm, M, l, l, l - 1, sm);
-      if (!tile_potrf<T>(acc, m, ldm, M, dinv, l, sm, sc)) return;
+      if constexpr (kTc) {
+        if (l > 0) {
+          if (!tc_product_begin<true>(m, ldm, M, p0, p0, (int64_t)(l - 1) * kBig, sm, tmem, mma_parity, sc)) break;
+          load_tile(acc, M, ldm, m, p0, p0, true);
+          if (!tc_product_end(sm, mma_parity, sc)) break;
+          tc_sub_acc(acc, tmem, sm);
+        } else {
+          load_tile(acc, M, ldm, m, p0, p0, true);
+        }
+      } else {
+        load_tile(acc, M, ldm, m, p0, p0, true);
+        if (l > 0) rank_update<T, true>(acc, m, ldm, M, l, l, l - 1, sm);
+      }
+      if (!tile_potrf<T>(acc, m, ldm, M, dinv, l, sm, sc)) break;
       val = l + 1;
     } else {
-      load_tile(acc, M, ldm, m, p0, q0, false);
-      if (l > 0) rank_update<T, false>(acc, m, ldm, M, i, l, l - 1, sm);
+      if constexpr (kTc) {
+        if (l > 0) {
+          if (!tc_product_begin<false>(m, ldm, M, p0, q0, (int64_t)(l - 1) * kBig, sm, tmem, mma_parity, sc)) break;
+          load_tile(acc, M, ldm, m, p0, q0, false);
+          if (!tc_product_end(sm, mma_parity, sc)) break;
+          tc_sub_acc(acc, tmem, sm);
+        } else {
+          load_tile(acc, M, ldm, m, p0, q0, false);
+        }
+      } else {
+        load_tile(acc, M, ldm, m, p0, q0, false);
+        if (l > 0) rank_update<T, false>(acc, m, ldm, M, i, l, l - 1, sm);
+      }
       if (tid == 0) sm.go = wait_at_least(state + (int64_t)l * nb + l, l + 1, sc);  // L_ll
       __syncthreads();
-      if (!sm.go) return;
+      if (!sm.go) break;
       load_diag_factor<T>(m, ldm, M, dinv, l, sm);
       trsm_sweep<T>(acc, sm);
       store_tile(acc, M, ldm, m, p0, q0, false);
@@ -443,6 +752,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     __threadfence();
     __syncthreads();
     if (tid == 0) st_release(state + (int64_t)i * nb + l, val);
+  }
+  if constexpr (kTc) {  // every exit: all MMAs have completed (or drained after a timeout)
+    tc::fence_before();
+    __syncthreads();
+    if ((tid >> 5) == 0) {
+      tc::fence_after();
+      tc::tmem_dealloc(tmem, kTcCols);
+    }
   }
 }
 
@@ -474,15 +791,16 @@ int chol_tiles_resident() {
 }
 
 // The task order (see the file comment): a list schedule of the task graph
-// on nproc identical workers.  Costs are relative estimates per task kind
-// (a diagonal update skips about 44% of the products; the triangular solve
-// and the factorisation sweep 128 columns with a block barrier each).
+// on nproc identical workers.  Costs are per task kind, in microseconds as
+// measured on GB300 for the FP32 factor (two CTAs per SM): a product on the
+// tensor cores, diagonal or not, 10; the diagonal factorisation 50; the
+// triangular solve with its load of L_ll 26; the inverse 24.
 void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
   const int nb = (int)chol_tile_count(m);
   out->clear();
   if (nb <= 0 || nb > kTileCholMaxTiles) return;
   if (nproc < 1) nproc = 1;
-  constexpr double kUpd = 31.0, kUpdDiag = 18.0, kPotrf = 63.0, kTrsm = 46.0, kInv = 46.0;
+  constexpr double kUpd = 10.0, kUpdDiag = 10.0, kPotrf = 50.0, kTrsm = 26.0, kInv = 24.0;
   struct Node {
     int4 d;
     double pre, post;  // cost before / after the mid-task wait (FINAL(i, l): for L_ll)
@@ -612,8 +930,9 @@ cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* din
   e = cudaMemsetAsync(state, 0, sizeof(int) * (size_t)nb * nb, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  int grid = sms * per_sm;
+  int grid = sms * per_sm;  // (at least 2: block 0 runs only the diagonal tasks)
   if (grid > ntasks) grid = ntasks;
+  if (grid < 2) return cudaErrorInvalidConfiguration;
   k_chol_tiles<T><<<grid, kThreads, chol_tiles_smem_bytes<T>(), st>>>(m, ldm, M, dinv, Uinv, tasks, ntasks, nb,
                                                                      state, ticket, sc);
   return cudaGetLastError();
