@@ -65,6 +65,7 @@ struct pdas_ctx {
   int chol_ntasks = 0;
   int* chol_state = nullptr;    // per-tile counters of the tile Cholesky
   float* uinv32 = nullptr;      // L_ll^{-T} of every diagonal tile of the FP32 tile factor
+  unsigned char* chol_planes = nullptr;  // BF16 operand planes of the tile factor's off-diagonal tiles
   float2* pairs = nullptr;      // the vector of a double-float pass as FP32 pairs (max(m, n))
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
   int64_t err_index = -1;
@@ -357,7 +358,7 @@ pdas_status factor(pdas_ctx* h) {
   else if (h->chol_ntasks == 0) KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->sc), chol_launches(h->m));
   else
     KL(cholesky_tiles<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->uinv32, h->chol_tasks, h->chol_ntasks,
-                             h->chol_state, h->tickets + T_CHOL, h->sc),
+                             h->chol_state, h->tickets + T_CHOL, h->sc, h->chol_planes),
        1);
   return PDAS_OK;
 }
@@ -693,6 +694,7 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
     al((void**)&h->chol_tasks, sizeof(int4) * tasks.size());
     al((void**)&h->chol_state, sizeof(int) * nb * nb);
     al((void**)&h->uinv32, sizeof(float) * nb * kCholTile * kCholTile);
+    if (nb > 1) al((void**)&h->chol_planes, (size_t)chol_plane_bytes(m));
     if (e == cudaSuccess)
       e = cudaMemcpy(h->chol_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice);
   }
@@ -733,6 +735,7 @@ void pdas_destroy(pdas_handle h) {
   if (h->chol_tasks) cudaFree(h->chol_tasks);
   if (h->chol_state) cudaFree(h->chol_state);
   if (h->uinv32) cudaFree(h->uinv32);
+  if (h->chol_planes) cudaFree(h->chol_planes);
   if (h->pairs) cudaFree(h->pairs);
   if (h->dinv64) cudaFree(h->dinv64);
   if (h->dinv32) cudaFree(h->dinv32);

@@ -62,14 +62,23 @@ constexpr int upd_vec() {  // elements per 16-byte load
   return 16 / (int)sizeof(T);
 }
 
-// Tensor-core products (FP32 factor): the two K chunks of 64 columns of both
-// operand tiles pass through shared memory as three BF16 planes each
-// (x = x0 + x1 + x2, 8 significant bits apiece, so every product of planes is
-// exact in FP32), 128 rows x 128 bytes, 128-byte swizzle.
-constexpr int kTcPlaneBytes = kBig * 128;
-constexpr int kTcOpsBytes = 6 * kTcPlaneBytes;  // A0 A1 A2 | B0 B1 B2
-constexpr uint32_t kTcCols = 256;               // TMEM: leading term | the five correction terms
+// Tensor-core products (FP32 factor).  Every finished off-diagonal tile of L
+// is stored once more as three BF16 planes (x = x0 + x1 + x2, 8 significant
+// bits apiece, so every product of planes is exact in FP32), per K chunk of
+// 64 columns: 128 rows x 128 bytes with the 128-byte swizzle, the layout the
+// MMA reads from shared memory.  A product copies the chunks of both operand
+// tiles into shared memory with bulk copies (the tensor memory accelerator)
+// and multiplies them there.
+constexpr int kTcPlaneBytes = kBig * 128;          // one plane of one K chunk
+constexpr int kTcChunkBytes = 3 * kTcPlaneBytes;   // the three planes of one operand's K chunk
+constexpr int kTcTileBytes = 2 * kTcChunkBytes;    // one tile: both K chunks (its slot in the plane buffer)
+constexpr int kTcBufBytes = 2 * kTcChunkBytes;     // one K chunk in shared memory: A planes | B planes
+constexpr int kTcOpsBytes = 2 * kTcBufBytes;       // both K chunks
+constexpr uint32_t kTcCols = 256;                  // TMEM: leading term | the five correction terms
 constexpr uint32_t kTcIdesc = tc::idesc_bf16(kBig, kBig);
+
+// Slot of the off-diagonal tile (i, k), i > k, in the plane buffer.
+__host__ __device__ constexpr int64_t plane_slot(int64_t i, int64_t k) { return i * (i - 1) / 2 + k; }
 
 template <typename T>
 struct TileCholSmem {
@@ -80,8 +89,10 @@ struct TileCholSmem {
   };
   T cb[2][kBig];  // column buffers of the POTRF / TRSM sweeps (double-buffered)
   T rcp[kBig];    // TRSM: 1 / L_cc; POTRF: the diagonal on entry
-  unsigned long long mma_bar;  // FP32 products: completion of the issued MMAs
+  unsigned long long mma_bar;      // FP32 products: completion of the issued MMAs
+  unsigned long long full_bar[2];  // FP32 products: arrival of the K chunks' planes
   uint32_t tmem_slot;
+  int tc_ok;
   int4 task;
   int go;
 };
@@ -332,17 +343,63 @@ __device__ __forceinline__ bool tile_potrf(const T (&acc)[8][8], int64_t m, int6
   return true;
 }
 
+// 16-byte vectors of T in registers (component access by constant index).
+template <typename T>
+struct Vec16Reg;
+template <>
+struct Vec16Reg<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static V load(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+  __device__ static float get(const V& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+  __device__ static V make(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+};
+template <>
+struct Vec16Reg<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static V load(const double* p) { return __ldcg(reinterpret_cast<const double2*>(p)); }
+  __device__ static double get(const V& v, int k) { return k == 0 ? v.x : v.y; }
+  __device__ static V make(const double (&a)[2]) { return make_double2(a[0], a[1]); }
+};
+
 // Loads L_ll (strictly lower part; rows and columns past m read as the
-// identity) and its pivot reciprocals into shared memory.
+// identity) and its pivot reciprocals into shared memory: 16-byte loads,
+// issued in batches of eight before their stores.
 template <typename T>
 __device__ __forceinline__ void load_diag_factor(int64_t m, int64_t ldm, const T* M, const T* dinv, int l,
                                                  TileCholSmem<T>& sm) {
+  using R = Vec16Reg<T>;
+  constexpr int VN = R::N;
+  constexpr int VPR = kBig / VN;              // vectors per row
+  constexpr int PER = kBig * VPR / kThreads;  // vectors per thread
+  constexpr int BATCH = 8;                    // in flight per thread (the caller holds its tile in registers)
+  static_assert(PER % BATCH == 0, "whole batches");
   const int tid = threadIdx.x;
   const int64_t q0 = (int64_t)l * kBig;
   const int kb = (int)(m - q0 < kBig ? m - q0 : kBig);
-  for (int e = tid; e < kBig * kBig; e += kThreads) {
-    const int r = e >> 7, c = e & 127;
-    sm.ls[r][c] = (c < r && r < kb) ? __ldcg(M + (q0 + r) * ldm + q0 + c) : T(0);
+#pragma unroll 1
+  for (int u0 = 0; u0 < PER; u0 += BATCH) {
+    typename R::V buf[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int e = tid + kThreads * (u0 + u), r = e / VPR, c = (e % VPR) * VN;
+      const T* src = M + (q0 + r) * ldm + q0 + c;
+      if (r < kb && c + VN <= r + 1) {  // every column of the vector is <= r < kb: inside the matrix
+        buf[u] = R::load(src);
+      } else {
+        T a[VN];
+#pragma unroll
+        for (int k = 0; k < VN; ++k) a[k] = (c + k < r && r < kb) ? __ldcg(src + k) : T(0);
+        buf[u] = R::make(a);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int e = tid + kThreads * (u0 + u), r = e / VPR, c = (e % VPR) * VN;
+#pragma unroll
+      for (int k = 0; k < VN; ++k) sm.ls[r][c + k] = c + k < r ? R::get(buf[u], k) : T(0);
+    }
   }
   if (tid < kBig) sm.rcp[tid] = tid < kb ? __ldcg(dinv + q0 + tid) : T(1);
   __syncthreads();
@@ -350,25 +407,45 @@ __device__ __forceinline__ void load_diag_factor(int64_t m, int64_t ldm, const T
 
 // X L_ll' = C for the 128 rows held in acc, column by column with the pivot
 // reciprocals (L_ll and 1 / L_cc in shared memory).  Row ty + 16 i of the
-// tile lives in one half-warp (its 16 threads hold columns tx + 16 j), so the
-// finished entry x = c_c / L_cc reaches the rest of its row by a width-16
-// shuffle and the sweep needs no block barrier; every thread then subtracts
-// x L_col,c from its later columns.
+// tile lives in one half-warp (its 16 threads hold columns tx + 16 j): the
+// thread of column c scales its 8 entries to x = c_c / L_cc and posts them in
+// a per-half-warp slot of shared memory (two 16-byte stores; slots alternate
+// with the column parity), and after a warp barrier the other threads of the
+// half-warp read them (two 16-byte broadcast loads) and subtract x L_col,c
+// from their later columns.  No block barrier in the sweep.
 template <typename T>
 __device__ __forceinline__ void trsm_sweep(T (&acc)[8][8], TileCholSmem<T>& sm) {
-  const int tid = threadIdx.x, tx = tid & 15, half = tid & 16;
+  constexpr int VN = 16 / (int)sizeof(T);
+  struct alignas(16) V {
+    T v[VN];
+  };
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T* slots = &sm.cb[0][0];  // [column parity][half-warp ty][8 rows]
 #pragma unroll
   for (int jo = 0; jo < 8; ++jo) {
 #pragma unroll 1
     for (int cl = 0; cl < 16; ++cl) {
       const int c = 16 * jo + cl;
-      const T rc = sm.rcp[c];
+      T* slot = slots + ((c & 1) * 16 + ty) * 8;
+      if (tx == cl) {
+        const T rc = sm.rcp[c];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) acc[ii][jo] *= rc;
+#pragma unroll
+        for (int v = 0; v < 8; v += VN) {
+          V w;
+#pragma unroll
+          for (int e = 0; e < VN; ++e) w.v[e] = acc[v + e][jo];
+          *reinterpret_cast<V*>(slot + v) = w;
+        }
+      }
+      __syncwarp();
       T x[8];
 #pragma unroll
-      for (int ii = 0; ii < 8; ++ii) x[ii] = __shfl_sync(0xffffffffu, acc[ii][jo] * rc, half | cl);
-      if (tx == cl) {
+      for (int v = 0; v < 8; v += VN) {
+        const V w = *reinterpret_cast<const V*>(slot + v);
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii) acc[ii][jo] = x[ii];
+        for (int e = 0; e < VN; ++e) x[v + e] = w.v[e];
       }
 #pragma unroll
       for (int j = jo; j < 8; ++j) {
@@ -379,6 +456,7 @@ __device__ __forceinline__ void trsm_sweep(T (&acc)[8][8], TileCholSmem<T>& sm) 
       }
     }
   }
+  __syncwarp();
 }
 
 // U_l = L_ll^{-T} (upper triangular; the identity past m): the sweep above
@@ -410,28 +488,6 @@ __device__ __forceinline__ void tile_inverse(T (&acc)[8][8], int64_t m, int64_t 
 // core's FP32 accumulation rounds toward zero, and keeping the leading term
 // in an accumulator of its own holds that to 8 accumulation steps.
 
-// Item t of this thread (t = 0..3): row e / 8 and BF16 chunk e % 8 (8
-// columns) of the 64-column K chunk, e = tid + 256 t.  Rows past m read 0.
-template <bool DIAG>
-__device__ __forceinline__ void tc_fetch(const float* M, int64_t ldm, int64_t m, int64_t pa, int64_t pb, int64_t kcol,
-                                         float4 (&v)[2][4][2]) {
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int e = threadIdx.x + kThreads * t, r = e >> 3, c8 = e & 7;
-#pragma unroll
-    for (int op = 0; op < (DIAG ? 1 : 2); ++op) {
-      const int64_t row = (op ? pb : pa) + r;
-      if (row < m) {
-        const float4* src = reinterpret_cast<const float4*>(M + row * ldm + kcol + 8 * c8);
-        v[op][t][0] = __ldcg(src);
-        v[op][t][1] = __ldcg(src + 1);
-      } else {
-        v[op][t][0] = v[op][t][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-  }
-}
-
 // x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)
 // (each difference exact in FP32), for the pair (a, b): word s holds the
 // BF16 term s of a (low half) and of b (high half).
@@ -447,31 +503,51 @@ __device__ __forceinline__ void bf16x2_split3(float a, float b, uint32_t& w0, ui
   w2 = bf16x2_bits(sa, sb);
 }
 
-template <bool DIAG>
-__device__ __forceinline__ void tc_split_store(const float4 (&v)[2][4][2], unsigned char* ops) {
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int e = threadIdx.x + kThreads * t, r = e >> 3, c8 = e & 7;
-    const int off = r * 128 + ((c8 ^ (r & 7)) << 4);
-#pragma unroll
-    for (int op = 0; op < (DIAG ? 1 : 2); ++op) {
-      const float x[8] = {v[op][t][0].x, v[op][t][0].y, v[op][t][0].z, v[op][t][0].w,
-                          v[op][t][1].x, v[op][t][1].y, v[op][t][1].z, v[op][t][1].w};
-      uint32_t w[3][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) bf16x2_split3(x[2 * q], x[2 * q + 1], w[0][q], w[1][q], w[2][q]);
-#pragma unroll
-      for (int sp = 0; sp < 3; ++sp)
-        *reinterpret_cast<uint4*>(ops + (3 * op + sp) * kTcPlaneBytes + off) = make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
-    }
-  }
+constexpr int kStagePitch = kBig + 4;  // FP32 staging rows: 16-byte aligned; 8 consecutive rows in distinct bank groups
+static_assert(kBig * kStagePitch * (int)sizeof(float) <= kTcOpsBytes, "the staging area lies inside the planes");
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
-// One thread: the 24 MMAs of a K chunk, then a commit to the barrier.
-__device__ __forceinline__ void tc_issue(uint32_t ops, bool diag, uint32_t tmem, bool first, uint32_t bar) {
-  tc::fence_after();
+// The BF16 planes of the finished tile held in acc (tile layout) to its slot
+// of the plane buffer.  The tile passes through a staging area as FP32 rows;
+// thread item e (8 per thread) is K chunk e / 1024, row (e / 8) % 128 and
+// 16-byte chunk e % 8 of that row.  Rows past m hold zeros in acc.
+__device__ __forceinline__ void tc_write_planes(const float (&acc)[8][8], unsigned char* slot, TileCholSmem<float>& sm) {
+  float(*S)[kStagePitch] = reinterpret_cast<float(*)[kStagePitch]>(sm.tc_ops);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  __syncthreads();  // (the staging area overlaps L_ll)
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) S[ty + 16 * i][tx + 16 * j] = acc[i][j];
+  __syncthreads();
+#pragma unroll 2
+  for (int u = 0; u < 2 * kBig * 8 / kThreads; ++u) {
+    const int e = tid + kThreads * u, kc = e >> 10, r = (e >> 3) & (kBig - 1), c8 = e & 7;
+    const float4 lo = *reinterpret_cast<const float4*>(&S[r][64 * kc + 8 * c8]);
+    const float4 hi = *reinterpret_cast<const float4*>(&S[r][64 * kc + 8 * c8 + 4]);
+    uint32_t w[3][4];
+    bf16x2_split3(lo.x, lo.y, w[0][0], w[1][0], w[2][0]);
+    bf16x2_split3(lo.z, lo.w, w[0][1], w[1][1], w[2][1]);
+    bf16x2_split3(hi.x, hi.y, w[0][2], w[1][2], w[2][2]);
+    bf16x2_split3(hi.z, hi.w, w[0][3], w[1][3], w[2][3]);
+    unsigned char* dst = slot + kc * kTcChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
+#pragma unroll
+    for (int sp = 0; sp < 3; ++sp)
+      *reinterpret_cast<uint4*>(dst + sp * kTcPlaneBytes) = make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
+  }
+  asm volatile("fence.proxy.async.global;" ::: "memory");  // read next by bulk copies (async proxy)
+}
+
+// One thread: the 24 MMAs of a K chunk (A planes at ops, B planes after them
+// or, on a diagonal tile, the A planes again).
+__device__ __forceinline__ void tc_issue(uint32_t ops, bool diag, uint32_t tmem, bool first) {
   const uint32_t a0 = ops, a1 = ops + kTcPlaneBytes, a2 = ops + 2 * kTcPlaneBytes;
-  const uint32_t b0 = diag ? ops : ops + 3 * kTcPlaneBytes, b1 = b0 + kTcPlaneBytes, b2 = b0 + 2 * kTcPlaneBytes;
+  const uint32_t b0 = diag ? ops : ops + kTcChunkBytes, b1 = b0 + kTcPlaneBytes, b2 = b0 + 2 * kTcPlaneBytes;
 #pragma unroll
   for (int ks = 0; ks < 4; ++ks) {  // K = 16 per MMA: 32 bytes along the swizzled row
     const uint32_t acc = (first && ks == 0) ? 0u : 1u;
@@ -486,50 +562,60 @@ __device__ __forceinline__ void tc_issue(uint32_t ops, bool diag, uint32_t tmem,
     tc::umma_f16(tmem + kBig, da1, db1, kTcIdesc, 1u);
     tc::umma_f16(tmem + kBig, da2, db0, kTcIdesc, 1u);
   }
-  tc::umma_commit(bar);
 }
 
-// Every thread: bounded wait for the next completion of the MMA barrier.  On
-// a timeout the status is set and the MMAs get a second bounded wait to
-// drain (the caller then leaves, and TMEM is freed).
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t& parity, Scalars* sc) {
-  const bool ok = tc::mbar_wait(bar, parity, nullptr);
+// D = L_ia L_ib' for the tiles in plane slots ta, tb (ta == tb on a diagonal
+// tile).  Thread 0 copies both K chunks of both operands into shared memory
+// and issues each chunk's MMAs once its planes have landed; the other threads
+// go on (the caller overlaps its loads of C) and meet at tc_product_end.  Every
+// barrier completes once per product, so one parity bit serves all three.
+template <bool DIAG>
+__device__ __forceinline__ void tc_product_begin(const unsigned char* planes, int64_t ta, int64_t tb,
+                                                 TileCholSmem<float>& sm, uint32_t tmem, uint32_t parity,
+                                                 Scalars* sc) {
+  if (threadIdx.x != 0) return;
+  unsigned char* ops = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm.tc_ops) + 1023) & ~uintptr_t(1023));
+  const uint32_t ops_s = tc::smem_u32(ops);
+  asm volatile("fence.proxy.async.global;" ::: "memory");  // the planes were published by generic stores
+  const unsigned char* A = planes + ta * kTcTileBytes;
+  const unsigned char* B = planes + tb * kTcTileBytes;
+#pragma unroll
+  for (int kc = 0; kc < 2; ++kc) {
+    const uint32_t bar = tc::smem_u32(&sm.full_bar[kc]);
+    tc::mbar_expect_tx(bar, DIAG ? kTcChunkBytes : 2 * kTcChunkBytes);
+    bulk_copy(ops_s + kc * kTcBufBytes, A + kc * kTcChunkBytes, kTcChunkBytes, bar);
+    if (!DIAG) bulk_copy(ops_s + kc * kTcBufBytes + kTcChunkBytes, B + kc * kTcChunkBytes, kTcChunkBytes, bar);
+  }
+  int ok = 1;
+#pragma unroll
+  for (int kc = 0; kc < 2; ++kc) {
+    if (ok && !tc::mbar_wait(tc::smem_u32(&sm.full_bar[kc]), parity, nullptr)) ok = 0;
+    if (ok) {
+      tc::fence_after();
+      tc_issue(ops_s + kc * kTcBufBytes, DIAG, tmem, kc == 0);
+    }
+  }
+  tc::umma_commit(tc::smem_u32(&sm.mma_bar));
+  if (!ok) {  // a copy did not land in time: record it and let the copies drain (bounded)
+    atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+    for (int kc = 0; kc < 2; ++kc) tc::mbar_wait(tc::smem_u32(&sm.full_bar[kc]), parity, nullptr);
+  }
+  sm.tc_ok = ok;
+}
+
+// Every thread: bounded wait for the product's MMAs; false (for all threads)
+// on a timeout here or in tc_product_begin.
+__device__ __forceinline__ bool tc_product_end(TileCholSmem<float>& sm, uint32_t& parity, Scalars* sc) {
+  const uint32_t bar = tc::smem_u32(&sm.mma_bar);
+  bool ok = tc::mbar_wait(bar, parity, nullptr);
   if (!ok) {
     atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
-    tc::mbar_wait(bar, parity, nullptr);
+    tc::mbar_wait(bar, parity, nullptr);  // let the MMAs drain before TMEM is freed
   }
   parity ^= 1u;
   tc::fence_after();
-  return ok;
-}
-
-// All threads: stage both K chunks and issue their MMAs; returns with the
-// second chunk's MMAs in flight (finish with tc_product_end).  The second
-// chunk's loads are in flight while the first chunk's MMAs run.
-template <bool DIAG>
-__device__ __forceinline__ bool tc_product_begin(int64_t m, int64_t ldm, const float* M, int64_t pa, int64_t pb,
-                                                 int64_t k0, TileCholSmem<float>& sm, uint32_t tmem,
-                                                 uint32_t& parity, Scalars* sc) {
-  unsigned char* ops = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm.tc_ops) + 1023) & ~uintptr_t(1023));
-  const uint32_t ops_s = tc::smem_u32(ops), bar = tc::smem_u32(&sm.mma_bar);
-  float4 v[2][4][2];
-  tc_fetch<DIAG>(M, ldm, m, pa, pb, k0, v);
-  tc_split_store<DIAG>(v, ops);
-  tc_fetch<DIAG>(M, ldm, m, pa, pb, k0 + 64, v);
-  tc::fence_proxy_async();
-  __syncthreads();
-  if (threadIdx.x == 0) tc_issue(ops_s, DIAG, tmem, true, bar);
-  const bool ok = tc_wait(bar, parity, sc);  // the planes are reused
-  tc_split_store<DIAG>(v, ops);
-  tc::fence_proxy_async();
-  if (!__syncthreads_and(ok)) return false;
-  if (threadIdx.x == 0) tc_issue(ops_s, DIAG, tmem, false, bar);
-  return true;
-}
-
-__device__ __forceinline__ bool tc_product_end(TileCholSmem<float>& sm, uint32_t& parity, Scalars* sc) {
-  const bool ok = tc_wait(tc::smem_u32(&sm.mma_bar), parity, sc);
-  return __syncthreads_and(ok);
+  const int all = __syncthreads_and(ok);
+  return all && sm.tc_ok;
 }
 
 // UPDATE epilogue: C -= D on the tile (p0, q0) in global memory, by whole
@@ -539,8 +625,6 @@ __device__ __forceinline__ bool tc_product_end(TileCholSmem<float>& sm, uint32_t
 // + 31, one row per thread, columns 64 (w / 4) .. + 63) into a staging area
 // (the operand planes are free once the MMAs completed) and applies it.  On a
 // diagonal tile only q <= p is written.
-constexpr int kStagePitch = kBig + 4;  // 16-byte rows; 8 consecutive rows in distinct bank groups
-static_assert(kBig * kStagePitch * (int)sizeof(float) <= kTcOpsBytes, "the staging area lies inside the planes");
 constexpr int kRowsPerWarp = kBig / (kThreads / 32);
 
 __device__ __forceinline__ void tc_load_rows(float4 (&x)[kRowsPerWarp], int64_t m, int64_t ldm, const float* M,
@@ -627,7 +711,7 @@ __device__ __forceinline__ void tc_sub_acc(float (&acc)[8][8], uint32_t tmem, Ti
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     k_chol_tiles(int64_t m, int64_t ldm, T* M, T* dinv, T* Uinv, const int4* __restrict__ tasks, int ntasks, int nb,
-                 int* state, unsigned* ticket, Scalars* sc) {
+                 int* state, unsigned* ticket, Scalars* sc, unsigned char* planes) {
   extern __shared__ __align__(16) unsigned char chol_tiles_smem[];
   TileCholSmem<T>& sm = *reinterpret_cast<TileCholSmem<T>*>(chol_tiles_smem);
   const int tid = threadIdx.x;
@@ -636,6 +720,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
   if constexpr (kTc) {
     if (tid == 0) {
       tc::mbar_init(tc::smem_u32(&sm.mma_bar), 1);
+      tc::mbar_init(tc::smem_u32(&sm.full_bar[0]), 1);
+      tc::mbar_init(tc::smem_u32(&sm.full_bar[1]), 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if ((tid >> 5) == 0) tc::tmem_alloc(tc::smem_u32(&sm.tmem_slot), kTcCols);
@@ -694,11 +780,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
       continue;
     }
     if (d.x == TK_UPDATE) {
-      const int64_t k0 = (int64_t)d.w * kBig;
       if constexpr (kTc) {
-        const bool ok = i == l ? tc_product_begin<true>(m, ldm, M, p0, q0, k0, sm, tmem, mma_parity, sc)
-                               : tc_product_begin<false>(m, ldm, M, p0, q0, k0, sm, tmem, mma_parity, sc);
-        if (!ok) break;
+        if (i == l) tc_product_begin<true>(planes, plane_slot(i, d.w), plane_slot(i, d.w), sm, tmem, mma_parity, sc);
+        else tc_product_begin<false>(planes, plane_slot(i, d.w), plane_slot(l, d.w), sm, tmem, mma_parity, sc);
         float4 cx[kRowsPerWarp];
         tc_load_rows(cx, m, ldm, M, p0, q0);
         if (!tc_product_end(sm, mma_parity, sc)) break;
@@ -714,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     } else if (d.x == TK_FINAL_DIAG) {
       if constexpr (kTc) {
         if (l > 0) {
-          if (!tc_product_begin<true>(m, ldm, M, p0, p0, (int64_t)(l - 1) * kBig, sm, tmem, mma_parity, sc)) break;
+          tc_product_begin<true>(planes, plane_slot(l, l - 1), plane_slot(l, l - 1), sm, tmem, mma_parity, sc);
           load_tile(acc, M, ldm, m, p0, p0, true);
           if (!tc_product_end(sm, mma_parity, sc)) break;
           tc_sub_acc(acc, tmem, sm);
@@ -730,7 +814,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     } else {
       if constexpr (kTc) {
         if (l > 0) {
-          if (!tc_product_begin<false>(m, ldm, M, p0, q0, (int64_t)(l - 1) * kBig, sm, tmem, mma_parity, sc)) break;
+          tc_product_begin<false>(planes, plane_slot(i, l - 1), plane_slot(l, l - 1), sm, tmem, mma_parity, sc);
           load_tile(acc, M, ldm, m, p0, q0, false);
           if (!tc_product_end(sm, mma_parity, sc)) break;
           tc_sub_acc(acc, tmem, sm);
@@ -747,6 +831,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
       load_diag_factor<T>(m, ldm, M, dinv, l, sm);
       trsm_sweep<T>(acc, sm);
       store_tile(acc, M, ldm, m, p0, q0, false);
+      if constexpr (kTc) tc_write_planes(acc, planes + plane_slot(i, l) * kTcTileBytes, sm);
       val = l + 1;
     }
     __threadfence();
@@ -911,7 +996,8 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
 
 template <typename T>
 cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, T* Uinv, const int4* tasks,
-                           int ntasks, int* state, unsigned* ticket, Scalars* sc) {
+                           int ntasks, int* state, unsigned* ticket, Scalars* sc, unsigned char* planes) {
+  if (sizeof(T) == 4 && !planes && chol_tile_count(m) > 1) return cudaErrorInvalidValue;
   static int per_sm = 0;  // resident CTAs per SM (per process; the attribute is per function)
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_chol_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -934,14 +1020,19 @@ cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* din
   if (grid > ntasks) grid = ntasks;
   if (grid < 2) return cudaErrorInvalidConfiguration;
   k_chol_tiles<T><<<grid, kThreads, chol_tiles_smem_bytes<T>(), st>>>(m, ldm, M, dinv, Uinv, tasks, ntasks, nb,
-                                                                     state, ticket, sc);
+                                                                     state, ticket, sc, planes);
   return cudaGetLastError();
 }
 
 template cudaError_t cholesky_tiles<float>(cudaStream_t, int64_t, int64_t, float*, float*, float*, const int4*, int,
-                                           int*, unsigned*, Scalars*);
+                                           int*, unsigned*, Scalars*, unsigned char*);
 template cudaError_t cholesky_tiles<double>(cudaStream_t, int64_t, int64_t, double*, double*, double*, const int4*,
-                                            int, int*, unsigned*, Scalars*);
+                                            int, int*, unsigned*, Scalars*, unsigned char*);
+
+int64_t chol_plane_bytes(int64_t m) {
+  const int64_t nb = chol_tile_count(m);
+  return nb * (nb - 1) / 2 * kTcTileBytes;
+}
 
 }  // namespace pdas
 

@@ -137,7 +137,10 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out);
 // row-major per tile), for trsv_lower_blk / trsv_upper_blk.
 template <typename T>
 cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, T* Uinv, const int4* tasks,
-                           int ntasks, int* state, unsigned* ticket, Scalars* sc);
+                           int ntasks, int* state, unsigned* ticket, Scalars* sc, unsigned char* planes);
+// Bytes of the BF16 operand planes of the FP32 tile factor (every tile below
+// the diagonal, 96 KB each).
+int64_t chol_plane_bytes(int64_t m);
 // The triangular solves with the FP32 tile factor (trsv_blk.cu); flags needs
 // ceil(m / 128) ints.
 cudaError_t trsv_lower_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
