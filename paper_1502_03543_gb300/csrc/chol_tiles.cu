@@ -254,14 +254,64 @@ __device__ __forceinline__ void warp_potrf(T (&row)[32], int lane, int& bad, T& 
   }
 }
 
+// S_rq -= sum_{c < 32} S_r,c0+c S_q,c0+c for the entries r >= rlo, qlo <= q < qhi
+// of the tile in shared memory, in 4 x 4 units (those wholly above the
+// diagonal skipped; entries above it inside a unit are updated and never
+// read), spread over the P threads p = 0..P-1 of the caller.
+template <typename T>
+__device__ __forceinline__ void potrf_trail(T (*S)[kBig + 1], int c0, int rlo, int qlo, int qhi, int p, int P) {
+  const int nq4 = (qhi - qlo) >> 2, nunits = ((kBig - rlo) >> 2) * nq4;
+#pragma unroll 1
+  for (int u = p; u < nunits; u += P) {
+    const int r = rlo + 4 * (u / nq4), q = qlo + 4 * (u % nq4);
+    if (q > r + 3) continue;
+    T t[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[i][j] = S[r + i][q + j];
+#pragma unroll 4
+    for (int c = 0; c < 32; ++c) {
+      T a[4], bq[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = S[r + i][c0 + c];
+        bq[i] = S[q + i][c0 + c];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[i][j] = fma(-a[i], bq[j], t[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) S[r + i][q + j] = t[i][j];
+  }
+}
+
+// The finished panel c0 .. c0 + 31 (rows r >= c0 inside the matrix, lower
+// part) to global memory, by the P threads p of the caller.
+template <typename T>
+__device__ __forceinline__ void potrf_store_panel(const T (*S)[kBig + 1], T* M, int64_t ldm, int64_t p0, int kb, int c0,
+                                                  int p, int P) {
+#pragma unroll 4
+  for (int e = p; e < (kBig - c0) * 32; e += P) {
+    const int r = c0 + (e >> 5), c = c0 + (e & 31);
+    if (r < kb && c <= r) M[(p0 + r) * ldm + p0 + c] = S[r][c];
+  }
+}
+
 // Factorisation of the diagonal tile (held in acc) through shared memory in
-// four 32-column blocks; per block:
-//   1. one warp factors the 32 x 32 diagonal block in registers (lane = row;
-//      the pivot and the column entries it needs come by warp shuffles);
-//   2. one thread per later row of the tile solves that row against it;
-//   3. every thread updates the trailing lower triangle of the tile.
-// Three block barriers per 32 columns.  Rows and columns past m (a ragged
-// last tile) carry an identity diagonal, so they factor trivially and are not
+// four 32-column blocks, right-looking with a look-ahead of one block.  Per
+// block b (columns c0 = 32 b ..):
+//   1. warp 0 factors the 32 x 32 diagonal block (warp_potrf); meanwhile the
+//      other warps apply block b - 1 to the columns past this block and
+//      store block b - 1;
+//   2. one thread per later row solves that row against the block;
+//   3. every thread applies block b to the next block's columns only.
+// Three block barriers per block.  Rows and columns past m (a ragged last
+// tile) carry an identity diagonal, so they factor trivially and are not
 // stored.  Returns false (status set) on a pivot that is not positive and
 // finite.
 template <typename T>
@@ -281,6 +331,7 @@ __device__ __forceinline__ bool tile_potrf(const T (&acc)[8][8], int64_t m, int6
     }
   if (tid == 0) s_fail = -1;
   __syncthreads();
+#pragma unroll 1
   for (int b = 0; b < 4; ++b) {
     const int c0 = 32 * b;
     if (warp == 0) {  // 1. the diagonal block
@@ -292,6 +343,9 @@ __device__ __forceinline__ bool tile_potrf(const T (&acc)[8][8], int64_t m, int6
       warp_potrf<T>(row, lane, bad, myrs, &sm.cb[0][0], &S[c0 + lane][c0]);
       sm.rcp[c0 + lane] = myrs;
       if (bad >= 0 && lane == 0) s_fail = c0 + bad;
+    } else if (b > 0) {  // 1'. block b - 1 on the columns past block b, and its store
+      potrf_trail<T>(S, c0 - 32, c0 + 32, c0 + 32, kBig, tid - 32, kThreads - 32);
+      potrf_store_panel<T>(S, M, ldm, p0, kb, c0 - 32, tid - 32, kThreads - 32);
     }
     __syncthreads();
     if (s_fail >= 0) break;
@@ -311,34 +365,16 @@ __device__ __forceinline__ bool tile_potrf(const T (&acc)[8][8], int64_t m, int6
       for (int q = 0; q < 32; ++q) S[r][c0 + q] = x[q];
     }
     __syncthreads();
-    if (nr > 0) {  // 3. trailing lower triangle: S_rq -= sum_c S_r,c0+c S_q,c0+c
-      const int nb16 = nr / 16;
-      for (int i2 = 0; i2 < nb16; ++i2) {
-        const int r = r0 + ty + 16 * i2;
-        T a[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) a[c] = S[r][c0 + c];
-        for (int j2 = 0; j2 <= i2; ++j2) {
-          const int q = r0 + tx + 16 * j2;
-          if (q <= r) {
-            T v = S[r][q];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v = fma(-a[c], S[q][c0 + c], v);
-            S[r][q] = v;
-          }
-        }
-      }
+    if (nr > 0) {  // 3. the next block's columns
+      potrf_trail<T>(S, c0, r0, r0, r0 + 32, tid, kThreads);
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (s_fail >= 0) {
     if (tid == 0 && atomicCAS(&sc->status, 0, (int)PDAS_ERR_NOT_SPD) == 0) sc->fail_index = (int)(p0 + s_fail);
     return false;
   }
-  for (int e = tid; e < kBig * kBig; e += kThreads) {
-    const int r = e >> 7, q = e & 127;
-    if (r < kb && q <= r) M[(p0 + r) * ldm + p0 + q] = S[r][q];
-  }
+  potrf_store_panel<T>(S, M, ldm, p0, kb, 96, tid, kThreads);
   if (tid < kb) dinv[p0 + tid] = sm.rcp[tid];
   return true;
 }
@@ -709,7 +745,7 @@ __device__ __forceinline__ void tc_sub_acc(float (&acc)[8][8], uint32_t tmem, Ti
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_chol_tiles(int64_t m, int64_t ldm, T* M, T* dinv, T* Uinv, const int4* __restrict__ tasks, int ntasks, int nb,
                  int* state, unsigned* ticket, Scalars* sc, unsigned char* planes) {
   extern __shared__ __align__(16) unsigned char chol_tiles_smem[];
@@ -877,15 +913,16 @@ int chol_tiles_resident() {
 
 // The task order (see the file comment): a list schedule of the task graph
 // on nproc identical workers.  Costs are per task kind, in microseconds as
-// measured on GB300 for the FP32 factor (two CTAs per SM): a product on the
-// tensor cores, diagonal or not, 10; the diagonal factorisation 50; the
-// triangular solve with its load of L_ll 26; the inverse 24.
+// measured on GB300 for the FP32 factor (one CTA per SM): an update on the
+// tensor cores, diagonal or not, 7; the diagonal task's product and
+// factorisation 35; the off-diagonal solve with its load of L_ll and the
+// write of its BF16 planes 22; the inverse 20.
 void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
   const int nb = (int)chol_tile_count(m);
   out->clear();
   if (nb <= 0 || nb > kTileCholMaxTiles) return;
   if (nproc < 1) nproc = 1;
-  constexpr double kUpd = 10.0, kUpdDiag = 10.0, kPotrf = 50.0, kTrsm = 26.0, kInv = 24.0;
+  constexpr double kUpd = 7.0, kUpdDiag = 7.0, kPotrf = 27.0, kTrsm = 22.0, kInv = 20.0;
   struct Node {
     int4 d;
     double pre, post;  // cost before / after the mid-task wait (FINAL(i, l): for L_ll)
