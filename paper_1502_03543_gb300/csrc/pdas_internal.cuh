@@ -141,12 +141,12 @@ cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* din
 // Bytes of the BF16 operand planes of the FP32 tile factor (every tile below
 // the diagonal, 96 KB each).
 int64_t chol_plane_bytes(int64_t m);
-// The triangular solves with the FP32 tile factor (trsv_blk.cu); flags needs
-// ceil(m / 128) ints.
+// The triangular solves with the FP32 tile factor (trsv_blk.cu).  The output
+// (z, y) is the hand-off between blocks; it must not alias the input.
 cudaError_t trsv_lower_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
-                           const double* v, double* z, int* flags, unsigned* ticket, Scalars* sc);
+                           const double* v, double* z, unsigned* ticket, Scalars* sc);
 cudaError_t trsv_upper_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
-                           const double* z, double* y, int* flags, unsigned* ticket, Scalars* sc);
+                           const double* z, double* y, unsigned* ticket, Scalars* sc);
 template <typename T>
 cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* v,
                        double* z, int* flags, unsigned* tickets, Scalars* sc);

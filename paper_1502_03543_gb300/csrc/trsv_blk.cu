@@ -9,11 +9,15 @@
 // diagonal tile is accurate enough; the plain FP64 form keeps substitution.
 //
 // One launch per solve.  Blocks take block rows in order from a ticket
-// counter and wait (bounded, 2 s) for the flags of the blocks they depend
-// on, which were handed out earlier: no deadlock.  Thread layout for the
-// off-diagonal tiles: warp w holds rows 16 w .. 16 w + 15, lane l columns
-// 4 l .. 4 l + 3 (16-byte loads along the rows); tiles are loaded before the
-// wait for the block they multiply.
+// counter and wait (bounded, 2 s) for the solution blocks they depend on,
+// which were handed out earlier: no deadlock.  The solution vector is filled
+// with an all-ones bit pattern before the launch (a value the solves cannot
+// produce: each entry is an FP32 sum widened to FP64, whose low 29 bits are
+// zero), and a consumer polls the entries it needs until none holds it, so
+// the hand-off from block to block is one round trip to L2, with no flag and
+// no fence.  Thread layout for the off-diagonal tiles: warp w holds rows
+// 16 w .. 16 w + 15, lane l columns 4 l .. 4 l + 3 (16-byte loads along the
+// rows); tiles are loaded before the wait for the block they multiply.
 #include "sync_util.cuh"
 #include "tile_core.cuh"
 
@@ -57,14 +61,48 @@ __device__ __forceinline__ float reduce16(float (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+constexpr unsigned long long kUnset = ~0ull;  // the fill of a solution entry not yet written
+
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// The warp waits (bounded) until none of the N entries p[k * stride] (k < N,
+// this lane's share) holds kUnset; entries with valid[k] false are not
+// waited for and read as 0.  Returns false on a timeout or a failed status.
+template <int N>
+__device__ __forceinline__ bool poll_entries(const double* p, const bool (&valid)[N], double (&out)[N], Scalars* sc) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    bool mine = true;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      out[k] = valid[k] ? ld_relaxed_f64(p + k) : 0.0;
+      mine = mine && __double_as_longlong(out[k]) != (long long)kUnset;
+    }
+    if (__all_sync(0xffffffffu, mine)) return true;
+    if (dev_failed(sc)) return false;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+
 __device__ __forceinline__ void load_u(TrsvSmem& sm, const float* __restrict__ Ub) {
   for (int e = threadIdx.x; e < kBig * kBig; e += blockDim.x) sm.U[e >> 7][e & 127] = __ldg(Ub + e);
 }
 
 // L z = v: z_b = U_b' (v_b - sum_{j<b} L_bj z_j).
-__global__ void __launch_bounds__(kThreads) k_trsv_lower_blk(int64_t m, int64_t ldm, const float* __restrict__ L,
+__global__ void __launch_bounds__(kThreads, 1) k_trsv_lower_blk(int64_t m, int64_t ldm, const float* __restrict__ L,
                                                              const float* __restrict__ Uinv,
-                                                             const double* __restrict__ v, double* z, int* flags,
+                                                             const double* __restrict__ v, double* z,
                                                              unsigned* ticket, Scalars* sc) {
   extern __shared__ __align__(16) unsigned char trsv_blk_smem[];
   TrsvSmem& sm = *reinterpret_cast<TrsvSmem*>(trsv_blk_smem);
@@ -76,30 +114,50 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower_blk(int64_t m, int64_t 
   const int64_t r0 = (int64_t)b * kBig;
   const int rb = (int)(m - r0 < kBig ? m - r0 : kBig);
   load_u(sm, Uinv + (int64_t)b * kBig * kBig);
+  const int myrow = 16 * w + ((lane >> 1) & 15);  // the row this lane finishes after the reduction
+  const float vmine = myrow < rb ? (float)v[r0 + myrow] : 0.f;  // off the dependency chain
   float part[16];
 #pragma unroll
   for (int rr = 0; rr < 16; ++rr) part[rr] = 0.f;
   bool ok = true;
-  for (int64_t j = 0; j < b; ++j) {  // tile j is full (j < b <= nb - 1)
-    float4 lv[16];
+  // Two buffers: block j + 1's tile rows and solution entries are in flight
+  // while block j's products run (entries read too early are re-polled).
+  float4 lv[2][16];
+  double zd[2][4];
+  auto fetch = [&](int64_t j, int buf) {  // tile j is full (j < b <= nb - 1)
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
       const int64_t row = r0 + 16 * w + rr;
-      lv[rr] = row < m ? __ldg(reinterpret_cast<const float4*>(L + row * ldm + j * kBig + 4 * lane))
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      lv[buf][rr] = row < m ? __ldg(reinterpret_cast<const float4*>(L + row * ldm + j * kBig + 4 * lane))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    ok = warp_wait(flags, j, sc);
-    if (!ok) break;
-    const double* zj = z + j * kBig + 4 * lane;
-    const float z0 = (float)__ldcg(zj), z1 = (float)__ldcg(zj + 1), z2 = (float)__ldcg(zj + 2),
-                z3 = (float)__ldcg(zj + 3);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) zd[buf][k] = ld_relaxed_f64(z + j * kBig + 4 * lane + k);
+  };
+  auto consume = [&](int64_t j, int buf) {
+    bool mine = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mine = mine && __double_as_longlong(zd[buf][k]) != (long long)kUnset;
+    if (!__all_sync(0xffffffffu, mine)) {
+      const bool all4[4] = {true, true, true, true};
+      if (!poll_entries<4>(z + j * kBig + 4 * lane, all4, zd[buf], sc)) return false;
+    }
+    const float z0 = (float)zd[buf][0], z1 = (float)zd[buf][1], z2 = (float)zd[buf][2], z3 = (float)zd[buf][3];
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr)
-      part[rr] = fmaf(lv[rr].x, z0, fmaf(lv[rr].y, z1, fmaf(lv[rr].z, z2, fmaf(lv[rr].w, z3, part[rr]))));
+      part[rr] = fmaf(lv[buf][rr].x, z0, fmaf(lv[buf][rr].y, z1, fmaf(lv[buf][rr].z, z2, fmaf(lv[buf][rr].w, z3, part[rr]))));
+    return true;
+  };
+  if (b > 0) fetch(0, 0);
+  for (int64_t j = 0; j < b && ok; j += 2) {
+    if (j + 1 < b) fetch(j + 1, 1);
+    ok = consume(j, 0);
+    if (!ok || j + 1 >= b) break;
+    if (j + 2 < b) fetch(j + 2, 0);
+    ok = consume(j + 1, 1);
   }
   const float tot = reduce16(part, lane);
-  const int row = 16 * w + ((lane >> 1) & 15);
-  if ((lane & 1) == 0) sm.rhs[row] = row < rb ? (float)v[r0 + row] - tot : 0.f;
+  if ((lane & 1) == 0) sm.rhs[myrow] = myrow < rb ? vmine - tot : 0.f;
   if (__syncthreads_or(!ok)) return;  // a wait gave up: the status says why
   const int c = tid & 127, h = tid >> 7;  // z_c = sum_r U_rc rhs_r, rows split in two halves
   float s = 0.f;
@@ -107,16 +165,13 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower_blk(int64_t m, int64_t 
   for (int r = 64 * h; r < 64 * h + 64; ++r) s = fmaf(sm.U[r][c], sm.rhs[r], s);
   sm.red[h][c] = s;
   __syncthreads();
-  if (tid < rb) z[r0 + tid] = (double)(sm.red[0][tid] + sm.red[1][tid]);
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release(flags + b, 1);
+  if (tid < rb) st_relaxed_f64(z + r0 + tid, (double)(sm.red[0][tid] + sm.red[1][tid]));
 }
 
 // L' y = z: y_b = U_b (z_b - sum_{k>b} L_kb' y_k); blocks go from the last.
-__global__ void __launch_bounds__(kThreads) k_trsv_upper_blk(int64_t m, int64_t ldm, const float* __restrict__ L,
+__global__ void __launch_bounds__(kThreads, 1) k_trsv_upper_blk(int64_t m, int64_t ldm, const float* __restrict__ L,
                                                              const float* __restrict__ Uinv,
-                                                             const double* __restrict__ zin, double* y, int* flags,
+                                                             const double* __restrict__ zin, double* y,
                                                              unsigned* ticket, Scalars* sc) {
   extern __shared__ __align__(16) unsigned char trsv_blk_smem[];
   TrsvSmem& sm = *reinterpret_cast<TrsvSmem*>(trsv_blk_smem);
@@ -129,28 +184,51 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_blk(int64_t m, int64_t 
   const int64_t r0 = (int64_t)b * kBig;
   const int rb = (int)(m - r0 < kBig ? m - r0 : kBig);
   load_u(sm, Uinv + (int64_t)b * kBig * kBig);
+  const float zmine = tid < rb ? (float)zin[r0 + tid] : 0.f;  // off the dependency chain
   float colp[4] = {0.f, 0.f, 0.f, 0.f};  // columns 4 lane .. 4 lane + 3 of tile b, this warp's rows
   bool ok = true;
-  for (int64_t k = nblk - 1; k > b; --k) {  // tile column b is full (b < k)
+  // Two buffers, as in the forward solve: block k - 1's tile rows and
+  // solution entries are in flight while block k's products run.  Lane l
+  // holds entry 16 w + (l & 15) of a block of y; the warp shares them.
+  float4 lv[2][16];
+  double yd[2];
+  auto fetch = [&](int64_t k, int buf) {  // tile column b is full (b < k)
     const int64_t k0 = k * kBig;
-    float4 lv[16];
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
       const int64_t row = k0 + 16 * w + rr;
-      lv[rr] = row < m ? __ldg(reinterpret_cast<const float4*>(L + row * ldm + r0 + 4 * lane))
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      lv[buf][rr] = row < m ? __ldg(reinterpret_cast<const float4*>(L + row * ldm + r0 + 4 * lane))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    ok = warp_wait(flags, k, sc);
-    if (!ok) break;
+    const int64_t mine = k0 + 16 * w + (lane & 15);
+    yd[buf] = mine < m ? ld_relaxed_f64(y + mine) : 0.0;
+  };
+  auto consume = [&](int64_t k, int buf) {
+    const int64_t k0 = k * kBig, mine = k0 + 16 * w + (lane & 15);
+    if (!__all_sync(0xffffffffu, __double_as_longlong(yd[buf]) != (long long)kUnset)) {
+      const bool inside[1] = {mine < m};
+      double one[1];
+      if (!poll_entries<1>(y + mine, inside, one, sc)) return false;
+      yd[buf] = one[0];
+    }
+    const float ymine = (float)yd[buf];
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
-      const int64_t row = k0 + 16 * w + rr;
-      const float yv = row < m ? (float)__ldcg(y + row) : 0.f;
-      colp[0] = fmaf(lv[rr].x, yv, colp[0]);
-      colp[1] = fmaf(lv[rr].y, yv, colp[1]);
-      colp[2] = fmaf(lv[rr].z, yv, colp[2]);
-      colp[3] = fmaf(lv[rr].w, yv, colp[3]);
+      const float yv = __shfl_sync(0xffffffffu, ymine, rr);
+      colp[0] = fmaf(lv[buf][rr].x, yv, colp[0]);
+      colp[1] = fmaf(lv[buf][rr].y, yv, colp[1]);
+      colp[2] = fmaf(lv[buf][rr].z, yv, colp[2]);
+      colp[3] = fmaf(lv[buf][rr].w, yv, colp[3]);
     }
+    return true;
+  };
+  if (nblk - 1 > b) fetch(nblk - 1, 0);
+  for (int64_t k = nblk - 1; k > b && ok; k -= 2) {
+    if (k - 1 > b) fetch(k - 1, 1);
+    ok = consume(k, 0);
+    if (!ok || k - 1 <= b) break;
+    if (k - 2 > b) fetch(k - 2, 0);
+    ok = consume(k - 1, 1);
   }
   *reinterpret_cast<float4*>(&sm.red[w][4 * lane]) = make_float4(colp[0], colp[1], colp[2], colp[3]);
   if (__syncthreads_or(!ok)) return;  // a wait gave up: the status says why
@@ -158,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_blk(int64_t m, int64_t 
     float s = 0.f;
 #pragma unroll
     for (int ww = 0; ww < 8; ++ww) s += sm.red[ww][tid];
-    sm.rhs[tid] = tid < rb ? (float)zin[r0 + tid] - s : 0.f;
+    sm.rhs[tid] = tid < rb ? zmine - s : 0.f;
   }
   __syncthreads();
   const int r = tid & 127, h = tid >> 7;  // y_r = sum_c U_rc rhs_c, columns split in two halves
@@ -168,10 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_blk(int64_t m, int64_t 
   __syncthreads();  // (red is reused)
   sm.red[h][r] = s;
   __syncthreads();
-  if (tid < rb) y[r0 + tid] = (double)(sm.red[0][tid] + sm.red[1][tid]);
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release(flags + b, 1);
+  if (tid < rb) st_relaxed_f64(y + r0 + tid, (double)(sm.red[0][tid] + sm.red[1][tid]));
 }
 
 cudaError_t trsv_blk_prepare() {
@@ -188,24 +263,24 @@ cudaError_t trsv_blk_prepare() {
 }  // namespace
 
 cudaError_t trsv_lower_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
-                           const double* v, double* z, int* flags, unsigned* ticket, Scalars* sc) {
+                           const double* v, double* z, unsigned* ticket, Scalars* sc) {
   const int64_t nblk = (m + kBig - 1) / kBig;
   cudaError_t e = trsv_blk_prepare();
-  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(z, 0xff, sizeof(double) * m, st);  // every entry kUnset
   if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_trsv_lower_blk<<<(unsigned)nblk, kThreads, sizeof(TrsvSmem), st>>>(m, ldm, L, Uinv, v, z, flags, ticket, sc);
+  k_trsv_lower_blk<<<(unsigned)nblk, kThreads, sizeof(TrsvSmem), st>>>(m, ldm, L, Uinv, v, z, ticket, sc);
   return cudaGetLastError();
 }
 
 cudaError_t trsv_upper_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
-                           const double* z, double* y, int* flags, unsigned* ticket, Scalars* sc) {
+                           const double* z, double* y, unsigned* ticket, Scalars* sc) {
   const int64_t nblk = (m + kBig - 1) / kBig;
   cudaError_t e = trsv_blk_prepare();
-  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0xff, sizeof(double) * m, st);  // every entry kUnset
   if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_trsv_upper_blk<<<(unsigned)nblk, kThreads, sizeof(TrsvSmem), st>>>(m, ldm, L, Uinv, z, y, flags, ticket, sc);
+  k_trsv_upper_blk<<<(unsigned)nblk, kThreads, sizeof(TrsvSmem), st>>>(m, ldm, L, Uinv, z, y, ticket, sc);
   return cudaGetLastError();
 }
 
