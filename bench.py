@@ -83,17 +83,25 @@ def fp32_simt_peak(peaks):
 
 
 def chol_roofline(form, m, ms_per_launch, peaks):
-    """Roofline record of the Cholesky factor: m^3/3 flops; the FP32 tile
-    factor of the mixed forms runs on the FP32 SIMT pipes, the FP64 form's
-    factor on the FP64 pipes."""
+    """Roofline record of the Cholesky factor: m^3/3 flops.  The FP32 tile
+    factor of the mixed forms runs its trailing products (~97% of the flops)
+    on the tensor cores as six BF16 products per FP32-grade product, so its
+    roof is the sustained BF16 peak / 6; the fraction of the FP32 SIMT peak is
+    given beside it.  The FP64 form's factor runs on the FP64 pipes."""
     flops = float(m) ** 3 / 3.0
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     if form == "fp64":
-        peak, note, kern = 1.25, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)", "blocked FP64 Cholesky (a4)"
-    else:
-        peak, note, kern = fp32_simt_peak(peaks), "FP32 SIMT from unit counts", "k_chol_tiles<float> (a4)"
-    return dict(bound="alu", achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
-                frac=round(achieved / peak, 4), traffic=None, kernel=kern, peak_note=note,
+        return dict(bound="alu", achieved=round(achieved, 3), peak=1.25, unit="TFLOP/s",
+                    frac=round(achieved / 1.25, 4), traffic=None, kernel="blocked FP64 Cholesky (a4)",
+                    peak_note="FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)",
+                    algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4))
+    peak = peaks["bf16_sus"] / 6.0
+    simt = fp32_simt_peak(peaks)
+    return dict(bound="tensor", achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
+                frac=round(achieved / peak, 4), traffic=None, kernel="k_chol_tiles<float> (a4)",
+                peak_note="FP32-grade products as 6 BF16 MMAs: bf16 dense sustained / 6, of %s; the factor "
+                          "is bound by its chain of diagonal tasks" % peaks["source"],
+                fp32_simt_peak=round(simt, 3), fp32_simt_frac=round(achieved / simt, 4),
                 algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4))
 
 

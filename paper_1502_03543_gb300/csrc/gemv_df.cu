@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part_df(int64_t m, int64_t 
       hi[k] = lo[k] = 0.f;
     }
     int it = 0;
+#pragma unroll 4
     for (int64_t p = pbeg; p < pend; ++p) {
       float a[VN];
       Vec32<T>::load(A + p * n + j, a);

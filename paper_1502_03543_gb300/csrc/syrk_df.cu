@@ -10,7 +10,9 @@
 //                                                kept as hi + lo with Knuth's TwoSum);
 // about 11 FP32 operations per term against one FP64 fused multiply-add.
 // The sum is written as hi + lo in FP64.  128 x 128 lower-triangle tiles,
-// 8 x 8 outputs per thread (as tile128_rank_k).
+// 512 threads of 4 x 8 outputs (thread (tx, ty): rows ty + 32 i, columns
+// tx + 16 j), so the 64 accumulator pairs of a thread stay in registers and
+// 16 warps per SM hide the latency of the TwoSum chains.
 #include "tile_core.cuh"
 
 namespace pdas {
@@ -34,27 +36,29 @@ struct DfSmem {
   float bl[kKc][kBig + 1];
 };
 
+constexpr int kDfThreads = 512;
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) k_syrk_df(int64_t m, int64_t n, const T* __restrict__ A,
-                                                         const float2* __restrict__ D2, double* __restrict__ M,
-                                                         int64_t ldm, const Scalars* sc) {
+__global__ void __launch_bounds__(kDfThreads, 1) k_syrk_df(int64_t m, int64_t n, const T* __restrict__ A,
+                                                           const float2* __restrict__ D2, double* __restrict__ M,
+                                                           int64_t ldm, const Scalars* sc) {
   __shared__ DfSmem sm;
   if (*(volatile const int*)&sc->status != 0) return;
   int64_t ti, tj;
   lower_tile(blockIdx.x, ti, tj);
   const int64_t p0 = ti * kBig, q0 = tj * kBig;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  constexpr int PER = (kBig * kKc) / kThreads;
-  float hi[8][8], lo[8][8];
+  constexpr int PER = (kBig * kKc) / kDfThreads;
+  float hi[4][8], lo[4][8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) hi[i][j] = lo[i][j] = 0.f;
   for (int64_t k0 = 0; k0 < n; k0 += kKc) {
     __syncthreads();
 #pragma unroll
     for (int e4 = 0; e4 < PER; ++e4) {
-      const int e = tid + e4 * kThreads;
+      const int e = tid + e4 * kDfThreads;
       const int r = e / kKc, kk = e % kKc;
       const int64_t k = k0 + kk;
       const bool kin = k < n;
@@ -71,16 +75,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_syrk_df(int64_t m, int64_t n, c
     __syncthreads();
 #pragma unroll 1
     for (int kk = 0; kk < kKc; ++kk) {
-      float a[8], bh[8], bl[8];
+      float a[4], bh[8], bl[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = sm.a[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = sm.a[kk][ty + 32 * i];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         bh[j] = sm.bh[kk][tx + 16 * j];
         bl[j] = sm.bl[kk][tx + 16 * j];
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float ph = a[i] * bh[j];
@@ -94,8 +98,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_syrk_df(int64_t m, int64_t n, c
     }
   }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t p = p0 + ty + 16 * i;
+  for (int i = 0; i < 4; ++i) {
+    const int64_t p = p0 + ty + 32 * i;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int64_t q = q0 + tx + 16 * j;
@@ -112,7 +116,7 @@ cudaError_t launch_syrk_df(cudaStream_t st, int64_t m, int64_t n, const T* A, co
   const int64_t g = (n + 255) / 256;
   k_split_d<<<(unsigned)(g < 1184 ? g : 1184), 256, 0, st>>>(n, D, D2);
   const int64_t tb = (m + kBig - 1) / kBig;
-  k_syrk_df<T><<<(unsigned)(tb * (tb + 1) / 2), kThreads, 0, st>>>(m, n, A, D2, M64, ldm, sc);
+  k_syrk_df<T><<<(unsigned)(tb * (tb + 1) / 2), kDfThreads, 0, st>>>(m, n, A, D2, M64, ldm, sc);
   return cudaGetLastError();
 }
 
