@@ -64,10 +64,15 @@ pdas_status pdas_gemv_t(pdas_handle h, const void* A, const double* u, double* o
  * min(cap, count) tasks to out as int32 quadruples {kind, i, l, k}:
  * kind 0 = last update of diagonal tile (l, l) by tile column k = l - 1 (none
  * for l = 0), then its factorisation (i = l); 1 = last update of tile (i, l),
- * i > l, then its triangular solve against L_ll; 2 = update of tile (i, l) by
- * tile columns i and l of step k <= l - 2.  Returns the count (0 for m <= 0);
- * out may be NULL to query it.  Every task comes after the tasks it waits
- * for, which is what makes the launch deadlock-free. */
+ * i >= l + 2, then its triangular solve against L_ll; 2 = update of tile
+ * (i, l) by tile columns i and l of step k <= l - 2, or of step k = l - 1 when
+ * i = l + 1; 3 = inverse of L_ll (for the blocked triangular solves); 4 =
+ * triangular solve of the sub-diagonal tile (l + 1, l) against L_ll, all its
+ * updates applied (k = l).  One CTA runs kinds 0 and 4 in the order 0(0),
+ * 4(1,0), 0(1), 4(2,1), ...; the others take the rest in list order.  Returns
+ * the count (0 for m <= 0); out may be NULL to query it.  Every task comes
+ * after the tasks it waits for, which is what makes the launch
+ * deadlock-free. */
 int64_t pdas_chol_tile_tasks(int64_t m, int32_t nproc, int32_t* out, int64_t cap);
 
 /* Size of the fixed device scratch behind pdas_gemv_t_noalloc: 8 MiB. */

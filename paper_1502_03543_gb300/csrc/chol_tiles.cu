@@ -6,21 +6,27 @@
 // With 128-row tile indices i >= l and k < l, the tasks are
 //   FINAL(l, l)    apply M_ll -= L_l,l-1 L_l,l-1', then L_ll = chol(M_ll)
 //   FINAL(i, l)    apply M_il -= L_i,l-1 L_l,l-1', wait for FINAL(l, l),
-//                  then L_il = M_il L_ll^{-T}
-//   UPDATE(i,l,k)  M_il -= L_ik L_lk'   for k <= l - 2 (rank 128)
+//                  then L_il = M_il L_ll^{-T}   (i >= l + 2)
+//   SOLVE(l+1, l)  L_l+1,l = M_l+1,l L_ll^{-T}  (all its updates applied)
+//   UPDATE(i,l,k)  M_il -= L_ik L_lk'   for k <= l - 2, and for k = l - 1
+//                  when i = l + 1 (rank 128)
 // In the FP32 factor every product L_ik L_lk' runs on the tcgen05 tensor
 // cores (BF16 operand planes, FP32 accumulation in tensor memory; see the
 // section "FP32 products on the tensor cores"); the FP64 instantiation keeps
 // SIMT products.
 // A tile's last update and its factorisation or triangular solve run in one
-// task on the tile held in registers, so the dependency chain of the
-// factorisation (FINAL(l,l) -> FINAL(l+1,l) -> FINAL(l+1,l+1) ...) has no
-// store, reload or hand-off between them.  Every tile (i, l) of the lower
-// triangle has a counter in global memory: the number of updates applied to
-// it, then l + 1 once it holds its final L values.
+// task on the tile held in registers (except the sub-diagonal tiles, see
+// below), and the dependency chain of the factorisation (FINAL(l,l) ->
+// SOLVE(l+1,l) -> FINAL(l+1,l+1) ...) runs in one CTA.  Every tile (i, l) of
+// the lower triangle has a counter in global memory: the number of updates
+// applied to it, then l + 1 once it holds its final L values.
 //
-// Block 0 runs the diagonal tasks FINAL(l, l) in order of l, so the task at
-// the head of the dependency chain never queues behind trailing updates.  The
+// Block 0 runs the dependency chain itself: FINAL(l, l), then the solve of
+// the sub-diagonal tile (l + 1, l) against L_ll while L_ll and its pivot
+// reciprocals are still in its shared memory (that tile's last update,
+// k = l - 1, is an ordinary UPDATE task), then FINAL(l + 1, l + 1), ...  The
+// head of the chain never queues behind trailing updates, and no chain link
+// crosses between CTAs.  The
 // other CTAs take the remaining tasks from a ticket counter in a fixed list
 // order.  In that order every task comes after all tasks it waits for (block
 // 0's tasks included), so the first unfinished task is always held by a
@@ -47,7 +53,7 @@ namespace pdas {
 
 namespace {
 
-enum TileTask { TK_FINAL_DIAG = 0, TK_FINAL_OFF = 1, TK_UPDATE = 2, TK_INV = 3 };
+enum TileTask { TK_FINAL_DIAG = 0, TK_FINAL_OFF = 1, TK_UPDATE = 2, TK_INV = 3, TK_CHAIN_SOLVE = 4 };
 
 // UPDATE operands: K chunks of 32 columns of two 128-row tile columns,
 // row-major with a pitch of 36 floats / 34 doubles (16-byte rows, and 16
@@ -766,22 +772,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_after();
     tmem = sm.tmem_slot;
   }
-  int chain_l = 0;  // block 0: the next diagonal task
+  int chain_step = 0;  // block 0: step 2 l is FINAL(l, l), step 2 l + 1 the solve of tile (l + 1, l)
   for (;;) {
     if (tid == 0) {  // take a task and wait for the tiles it starts from
       int go = 0;
       bool have = false;
       int4 d = make_int4(0, 0, 0, 0);
-      if (blockIdx.x == 0) {  // FINAL(l, l) in order of l
-        have = chain_l < nb;
-        d = make_int4(TK_FINAL_DIAG, chain_l, chain_l, chain_l - 1);
-        ++chain_l;
+      if (blockIdx.x == 0) {  // the diagonal chain in order
+        const int l = chain_step >> 1;
+        if (chain_step & 1) {
+          have = l + 1 < nb;
+          d = make_int4(TK_CHAIN_SOLVE, l + 1, l, l);
+        } else {
+          have = l < nb;
+          d = make_int4(TK_FINAL_DIAG, l, l, l - 1);
+        }
+        ++chain_step;
       } else {  // the other tasks in list order
         for (;;) {
           const unsigned t = atomicAdd(ticket, 1u);
           if (t >= (unsigned)ntasks) break;
           d = tasks[t];
-          if (d.x != TK_FINAL_DIAG) {
+          if (d.x != TK_FINAL_DIAG && d.x != TK_CHAIN_SOLVE) {
             have = true;
             break;
           }
@@ -795,6 +807,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                wait_at_least(state + i * nb + l, (int)k, sc);
         else if (d.x == TK_INV)
           go = wait_at_least(state + l * nb + l, (int)l + 1, sc);
+        else if (d.x == TK_CHAIN_SOLVE)  // every update of the tile applied (L_ll is this block's own)
+          go = wait_at_least(state + i * nb + l, (int)l, sc);
         else if (l == 0)
           go = 1;
         else
@@ -813,6 +827,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (d.x == TK_INV) {
       tile_inverse<T>(acc, m, ldm, M, dinv, Uinv, l, sm);
       __syncthreads();  // (shared memory is reused by the next task; no counter to publish)
+      continue;
+    }
+    if (d.x == TK_CHAIN_SOLVE) {  // block 0, right after FINAL(l, l): L_ll and 1 / L_cc are still in shared memory
+      load_tile(acc, M, ldm, m, p0, q0, false);
+      trsm_sweep<T>(acc, sm);
+      store_tile(acc, M, ldm, m, p0, q0, false);
+      if constexpr (kTc) tc_write_planes(acc, planes + plane_slot(i, l) * kTcTileBytes, sm);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release(state + (int64_t)i * nb + l, l + 1);
       continue;
     }
     if (d.x == TK_UPDATE) {
@@ -922,17 +946,18 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
   out->clear();
   if (nb <= 0 || nb > kTileCholMaxTiles) return;
   if (nproc < 1) nproc = 1;
-  constexpr double kUpd = 7.0, kUpdDiag = 7.0, kPotrf = 27.0, kTrsm = 22.0, kInv = 20.0;
+  constexpr double kUpd = 7.0, kUpdDiag = 7.0, kPotrf = 27.0, kTrsm = 22.0, kChain = 19.0, kInv = 20.0;
   struct Node {
     int4 d;
     double pre, post;  // cost before / after the mid-task wait (FINAL(i, l): for L_ll)
-    int mid;           // FINAL(l, l) for FINAL(i, l), i > l; else -1
+    int mid;           // FINAL(l, l) for FINAL(i, l), i > l + 1; else -1
     int npred;
   };
   std::vector<Node> nodes;
   std::vector<std::vector<int>> succ;
-  // index maps: FINAL(i, l) -> fidx[i nb + l]; UPDATE(i, l, k) -> ubase[l nb + k] + i - l
-  std::vector<int> fidx((size_t)nb * nb, -1), ubase((size_t)nb * nb, -1);
+  // index maps: the task that finishes tile (i, l) -> fidx[i nb + l]; UPDATE(i, l, k) with
+  // k <= l - 2 -> ubase[l nb + k] + i - l, and UPDATE(l + 1, l, l - 1) -> subupd[l]
+  std::vector<int> fidx((size_t)nb * nb, -1), ubase((size_t)nb * nb, -1), subupd(nb, -1);
   auto add = [&](int4 d, double pre, double post) {
     nodes.push_back(Node{d, pre, post, -1, 0});
     return (int)nodes.size() - 1;
@@ -940,18 +965,20 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
   for (int l = 0; l < nb; ++l) {
     fidx[(size_t)l * nb + l] = add(make_int4(TK_FINAL_DIAG, l, l, l - 1), (l ? kUpdDiag : 0.0) + kPotrf, 0.0);
     add(make_int4(TK_INV, l, l, 0), kInv, 0.0);
-    for (int i = l + 1; i < nb; ++i) fidx[(size_t)i * nb + l] = add(make_int4(TK_FINAL_OFF, i, l, l - 1), l ? kUpd : 0.0, kTrsm);
+    if (l + 1 < nb) fidx[(size_t)(l + 1) * nb + l] = add(make_int4(TK_CHAIN_SOLVE, l + 1, l, l), kChain, 0.0);
+    for (int i = l + 2; i < nb; ++i) fidx[(size_t)i * nb + l] = add(make_int4(TK_FINAL_OFF, i, l, l - 1), l ? kUpd : 0.0, kTrsm);
     for (int k = 0; k + 2 <= l; ++k) {
       ubase[(size_t)l * nb + k] = (int)nodes.size();
       for (int i = l; i < nb; ++i) add(make_int4(TK_UPDATE, i, l, k), i == l ? kUpdDiag : kUpd, 0.0);
     }
+    if (l >= 1 && l + 1 < nb) subupd[l] = add(make_int4(TK_UPDATE, l + 1, l, l - 1), kUpd, 0.0);
   }
   succ.resize(nodes.size());
   auto edge = [&](int a, int b) {
     succ[a].push_back(b);
     ++nodes[b].npred;
   };
-  auto upd = [&](int i, int l, int k) { return ubase[(size_t)l * nb + k] + (i - l); };
+  auto upd = [&](int i, int l, int k) { return k == l - 1 ? subupd[l] : ubase[(size_t)l * nb + k] + (i - l); };
   for (int v = 0; v < (int)nodes.size(); ++v) {
     const int4 d = nodes[v].d;
     const int i = d.y, l = d.z, k = d.w;
@@ -961,6 +988,9 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
       edge(fidx[(size_t)i * nb + k], v);
       if (l != i) edge(fidx[(size_t)l * nb + k], v);
       if (k > 0) edge(upd(i, l, k - 1), v);
+    } else if (d.x == TK_CHAIN_SOLVE) {  // every update of (l + 1, l) applied, L_ll final
+      edge(fidx[(size_t)l * nb + l], v);
+      if (l >= 1) edge(upd(i, l, l - 1), v);
     } else {
       if (l > 0) {
         edge(fidx[(size_t)i * nb + l - 1], v);
@@ -970,14 +1000,29 @@ void chol_tile_tasks(int64_t m, int nproc, std::vector<int4>* out) {
       if (d.x == TK_FINAL_OFF) nodes[v].mid = fidx[(size_t)l * nb + l];
     }
   }
-  // bottom levels (nodes were created in a topological order of the start
-  // edges; the mid edge FINAL(l,l) -> FINAL(i,l) also goes forward)
+  // bottom levels, over a topological order of the start and mid edges
   const int N = (int)nodes.size();
-  std::vector<double> bl(N, 0.0);
   std::vector<std::vector<int>> midsucc(N);
   for (int v = 0; v < N; ++v)
     if (nodes[v].mid >= 0) midsucc[nodes[v].mid].push_back(v);
-  for (int v = N - 1; v >= 0; --v) {
+  std::vector<int> indeg(N, 0), topo;
+  topo.reserve(N);
+  for (int v = 0; v < N; ++v) {
+    for (int w : succ[v]) ++indeg[w];
+    for (int w : midsucc[v]) ++indeg[w];
+  }
+  for (int v = 0; v < N; ++v)
+    if (indeg[v] == 0) topo.push_back(v);
+  for (size_t h = 0; h < topo.size(); ++h) {
+    const int v = topo[h];
+    for (int w : succ[v])
+      if (--indeg[w] == 0) topo.push_back(w);
+    for (int w : midsucc[v])
+      if (--indeg[w] == 0) topo.push_back(w);
+  }
+  std::vector<double> bl(N, 0.0);
+  for (int h = (int)topo.size() - 1; h >= 0; --h) {
+    const int v = topo[h];
     double best = 0.0;
     for (int w : succ[v]) best = std::max(best, bl[w]);
     for (int w : midsucc[v]) best = std::max(best, bl[w]);
