@@ -40,6 +40,7 @@
 // trailing updates around it.  A non-positive pivot records PDAS_ERR_NOT_SPD
 // and its index; the other CTAs see the status and stop.
 #include <algorithm>
+#include <type_traits>
 #include <queue>
 #include <vector>
 
@@ -47,6 +48,7 @@
 
 #include "sync_util.cuh"
 #include "tc_util.cuh"
+#include "df_util.cuh"
 #include "tile_core.cuh"
 
 namespace pdas {
@@ -119,6 +121,15 @@ __device__ __forceinline__ bool pivot_bad(T d) {
   return !(d > T(0)) || !isfinite(d);
 }
 
+// One element from global memory through L2 (the tile counters order it after
+// its producer's release).
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ dfloat ld_cg(const dfloat* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return dfloat(v.x, v.y);
+}
+
 // Thread (tx, ty) holds rows ty + 16 i and columns tx + 16 j of a tile.  On a
 // diagonal tile only the lower triangle is read and written.
 template <typename T>
@@ -131,7 +142,7 @@ __device__ __forceinline__ void load_tile(T (&acc)[8][8], const T* M, int64_t ld
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int64_t q = q0 + tx + 16 * j;
-      acc[i][j] = (p < m && q < m && (!diag || q <= p)) ? __ldcg(M + p * ldm + q) : T(0);
+      acc[i][j] = (p < m && q < m && (!diag || q <= p)) ? ld_cg(M + p * ldm + q) : T(0);
     }
   }
 }
@@ -397,6 +408,14 @@ struct Vec16Reg<float> {
   __device__ static V make(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
 };
 template <>
+struct Vec16Reg<dfloat> {
+  using V = float4;
+  static constexpr int N = 2;
+  __device__ static V load(const dfloat* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+  __device__ static dfloat get(const V& v, int k) { return k == 0 ? dfloat(v.x, v.y) : dfloat(v.z, v.w); }
+  __device__ static V make(const dfloat (&a)[2]) { return make_float4(a[0].hi, a[0].lo, a[1].hi, a[1].lo); }
+};
+template <>
 struct Vec16Reg<double> {
   using V = double2;
   static constexpr int N = 2;
@@ -432,7 +451,7 @@ __device__ __forceinline__ void load_diag_factor(int64_t m, int64_t ldm, const T
       } else {
         T a[VN];
 #pragma unroll
-        for (int k = 0; k < VN; ++k) a[k] = (c + k < r && r < kb) ? __ldcg(src + k) : T(0);
+        for (int k = 0; k < VN; ++k) a[k] = (c + k < r && r < kb) ? ld_cg(src + k) : T(0);
         buf[u] = R::make(a);
       }
     }
@@ -443,7 +462,7 @@ __device__ __forceinline__ void load_diag_factor(int64_t m, int64_t ldm, const T
       for (int k = 0; k < VN; ++k) sm.ls[r][c + k] = c + k < r ? R::get(buf[u], k) : T(0);
     }
   }
-  if (tid < kBig) sm.rcp[tid] = tid < kb ? __ldcg(dinv + q0 + tid) : T(1);
+  if (tid < kBig) sm.rcp[tid] = tid < kb ? ld_cg(dinv + q0 + tid) : T(1);
   __syncthreads();
 }
 
@@ -824,8 +843,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t p0 = (int64_t)i * kBig, q0 = (int64_t)l * kBig;
     T acc[8][8];
     int val;
-    if (d.x == TK_INV) {
-      tile_inverse<T>(acc, m, ldm, M, dinv, Uinv, l, sm);
+    if (d.x == TK_INV) {  // (the double-float factor's solves substitute: no inverses)
+      if constexpr (!std::is_same<T, dfloat>::value) tile_inverse<T>(acc, m, ldm, M, dinv, Uinv, l, sm);
       __syncthreads();  // (shared memory is reused by the next task; no counter to publish)
       continue;
     }
@@ -1110,6 +1129,51 @@ template cudaError_t cholesky_tiles<float>(cudaStream_t, int64_t, int64_t, float
                                            int*, unsigned*, Scalars*, unsigned char*);
 template cudaError_t cholesky_tiles<double>(cudaStream_t, int64_t, int64_t, double*, double*, double*, const int4*,
                                             int, int*, unsigned*, Scalars*, unsigned char*);
+
+template cudaError_t cholesky_tiles<dfloat>(cudaStream_t, int64_t, int64_t, dfloat*, dfloat*, dfloat*, const int4*,
+                                            int, int*, unsigned*, Scalars*, unsigned char*);
+
+namespace {
+
+// The lower triangle of the FP64 matrix M (leading dimension ldm) as
+// double-float pairs in place (each 8-byte entry becomes hi, lo), or back.
+__global__ void k_df_convert(int64_t m, int64_t ldm, double* M, int to_df) {
+  const int64_t total = m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / m, q = e % m;
+    if (q > p) continue;
+    double* a = M + p * ldm + q;
+    if (to_df) {
+      const dfloat v = df_from_double(*a);
+      *reinterpret_cast<float2*>(a) = make_float2(v.hi, v.lo);
+    } else {
+      const float2 v = *reinterpret_cast<const float2*>(a);
+      *a = df_to_double(dfloat(v.x, v.y));
+    }
+  }
+}
+__global__ void k_df_to_double(int64_t n, double* v) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const float2 w = *reinterpret_cast<const float2*>(v + j);
+    v[j] = df_to_double(dfloat(w.x, w.y));
+  }
+}
+
+}  // namespace
+
+cudaError_t cholesky_tiles_df(cudaStream_t st, int64_t m, int64_t ldm, double* M, double* dinv, const int4* tasks,
+                              int ntasks, int* state, unsigned* ticket, Scalars* sc) {
+  const unsigned g = (unsigned)std::min<int64_t>((m * m + 255) / 256, 4736);
+  k_df_convert<<<g, 256, 0, st>>>(m, ldm, M, 1);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cholesky_tiles<dfloat>(st, m, ldm, reinterpret_cast<dfloat*>(M), reinterpret_cast<dfloat*>(dinv), nullptr,
+                               tasks, ntasks, state, ticket, sc, nullptr);
+  if (e != cudaSuccess) return e;
+  k_df_convert<<<g, 256, 0, st>>>(m, ldm, M, 0);
+  k_df_to_double<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1184), 256, 0, st>>>(m, dinv);
+  return cudaGetLastError();
+}
 
 int64_t chol_plane_bytes(int64_t m) {
   const int64_t nb = chol_tile_count(m);

@@ -141,6 +141,13 @@ cudaError_t cholesky_tiles(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* din
 // Bytes of the BF16 operand planes of the FP32 tile factor (every tile below
 // the diagonal, 96 KB each).
 int64_t chol_plane_bytes(int64_t m);
+// The double-float tile factor of the FP64 matrix M (FP64 tier of the mixed
+// forms): M's lower triangle is turned into double-float pairs in place,
+// factored by the tile Cholesky on the FP32 pipes (task list as the FP32
+// factor's), and turned back into the FP64 factor L and FP64 pivot
+// reciprocals dinv.  A pivot that is not positive sets PDAS_ERR_NOT_SPD.
+cudaError_t cholesky_tiles_df(cudaStream_t st, int64_t m, int64_t ldm, double* M, double* dinv, const int4* tasks,
+                              int ntasks, int* state, unsigned* ticket, Scalars* sc);
 // The triangular solves with the FP32 tile factor (trsv_blk.cu).  The output
 // (z, y) is the hand-off between blocks; it must not alias the input.
 cudaError_t trsv_lower_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
