@@ -62,7 +62,10 @@ _SIGNATURES = {
     "or_theta": ([_F64, _F64], _F64),
     "or_step": ([_I64, _I64, _F64] + [_P] * 6, None),
     "or_rel_gap": ([_I64, _I64, _P, _P, _P, _P], _F64),
-    "or_solve": ([_I64, _I64] + [_P] * 6 + [_F64, _F64, _I32] + [_P] * 4, _I32),
+    "or_solve": ([_I64, _I64] + [_P] * 6 + [_F64, _F64, _I32] + [_P] * 4 + [_I32, _P], _I32),
+    "or_direction_infeasible": ([_I64, _I64] + [_P] * 12, _I64),
+    "or_residuals": ([_I64, _I64] + [_P] * 7, None),
+    "or_theta_infeasible": ([_F64, _F64], _F64),
 }
 
 
@@ -225,6 +228,36 @@ class Oracle:
             out.update(M=M, L=L)
         return out
 
+    def direction_infeasible(self, A, b, c, x, y, s):
+        """Newton direction of the infeasible-start variant: Eq. (3) with the
+        residuals r_p = b - A x and r_d = c - A' y - s as right-hand sides of
+        its first two rows, reduced as in Section V.
+
+        Returns a dict with dx, dy, ds, D, r (= b + A D r_d), rd (= r_d) and
+        fail (-1 or the failing pivot index)."""
+        A = _f64(A)
+        m, n = A.shape
+        b, c = _f64(b, (m,)), _f64(c, (n,))
+        x, y, s = _f64(x, (n,)), _f64(y, (m,)), _f64(s, (n,))
+        dx, ds, D, rd = np.empty(n), np.empty(n), np.empty(n), np.empty(n)
+        dy, r = np.empty(m), np.empty(m)
+        fail = int(self.lib.or_direction_infeasible(m, n, _p(A), _p(b), _p(c), _p(x), _p(y), _p(s), _p(dx), _p(dy),
+                                                    _p(ds), _p(D), _p(r), _p(rd)))
+        return dict(dx=dx, dy=dy, ds=ds, D=D, r=r, rd=rd, fail=fail)
+
+    def residuals(self, A, b, c, x, y, s):
+        """(||b - A x||_inf / (1 + ||b||_inf), ||c - A' y - s||_inf / (1 + ||c||_inf))."""
+        A = _f64(A)
+        m, n = A.shape
+        out = np.empty(2)
+        self.lib.or_residuals(m, n, _p(A), _p(_f64(b, (m,))), _p(_f64(c, (n,))), _p(_f64(x, (n,))),
+                              _p(_f64(y, (m,))), _p(_f64(s, (n,))), _p(out))
+        return float(out[0]), float(out[1])
+
+    def theta_infeasible(self, psi_value, alpha):
+        """Step length of the infeasible-start variant: min(1, alpha / psi)."""
+        return float(self.lib.or_theta_infeasible(float(psi_value), float(alpha)))
+
     def psi(self, x, s, dx, ds):
         """psi = max{phi(-X^{-1} dx), phi(-S^{-1} ds)}, phi(u) = max_j u_j (Section III)."""
         x = _f64(x)
@@ -248,26 +281,33 @@ class Oracle:
         b, c, x, y = _f64(b), _f64(c), _f64(x), _f64(y)
         return float(self.lib.or_rel_gap(b.size, c.size, _p(b), _p(c), _p(x), _p(y)))
 
-    def solve(self, A, b, c, x0, y0, s0, alpha=0.95, tol=1e-8, max_iter=500, keep_iterates=False):
+    def solve(self, A, b, c, x0, y0, s0, alpha=0.95, tol=1e-8, max_iter=500, keep_iterates=False,
+              infeasible=False):
         """Run the Primal-Dual Affine Scaling algorithm (Section III).
 
         Returns a dict: status (one of the codes above), iters, x, y, s,
         trace (iters x 4: psi, theta, rel_gap after the step, max D / min D),
         fail_index and, if keep_iterates, iterates (iters x (2n+m): x | y | s
-        after each step)."""
+        after each step).  infeasible=True runs the infeasible-start variant
+        (direction_infeasible, theta_infeasible, stop on the gap and both
+        relative residuals) and adds res_trace (iters x 2: the residuals of
+        ``residuals`` after each step)."""
         A = _f64(A)
         m, n = A.shape
         x, y, s = _f64(x0, (n,)).copy(), _f64(y0, (m,)).copy(), _f64(s0, (n,)).copy()
         b, c = _f64(b, (m,)), _f64(c, (n,))
         trace = np.zeros((max_iter, 4))
         its = np.zeros((max_iter, 2 * n + m)) if keep_iterates else None
+        res_trace = np.zeros((max_iter, 2))
         iters = ctypes.c_int(0)
         fail = ctypes.c_int64(-1)
         status = int(self.lib.or_solve(m, n, _p(A), _p(b), _p(c), _p(x), _p(y), _p(s), float(alpha), float(tol),
                                        int(max_iter), ctypes.addressof(iters), _p(trace), _p(its),
-                                       ctypes.addressof(fail)))
+                                       ctypes.addressof(fail), int(bool(infeasible)), _p(res_trace)))
         k = iters.value
         out = dict(status=status, iters=k, x=x, y=y, s=s, trace=trace[:k], fail_index=fail.value)
+        if infeasible:
+            out["res_trace"] = res_trace[:k]
         if keep_iterates:
             out["iterates"] = its[:k]
         return out
@@ -285,6 +325,9 @@ cholesky = default.cholesky
 forward = default.forward
 backward = default.backward
 direction = default.direction
+direction_infeasible = default.direction_infeasible
+residuals = default.residuals
+theta_infeasible = default.theta_infeasible
 psi = default.psi
 theta = default.theta
 step = default.step

@@ -27,6 +27,16 @@
  *       solver stops after the step.  Otherwise theta = alpha / psi.
  *   R10 The paper gives no iteration cap; max_iter is an argument, and the
  *       run is declared stalled after 5 consecutive steps with theta < 1e-12.
+ *   R11 Infeasible-start variant (not in the paper, which assumes a feasible
+ *       interior start): the rows A dx = 0 and A' dy + ds = 0 of Eq. (3)
+ *       take the residuals r_p = b - A x and r_d = c - A' y - s as their
+ *       right-hand sides.  The reduction of Section V then gives
+ *       (A D A') dy = b + A D r_d, ds = r_d - A' dy, dx = D(-ds) - x; from a
+ *       feasible start it is the paper's system.  A full step from an
+ *       infeasible point does not end at an optimum, so the variant steps
+ *       theta = min(1, alpha / psi) (the iterate stays interior), never stops
+ *       on psi, and stops when |rel_gap|, ||r_p||_inf / (1 + ||b||_inf) and
+ *       ||r_d||_inf / (1 + ||c||_inf) are all below tol.
  *
  * Arithmetic: every sum runs left to right in increasing index order, in
  * FP64, with no fused multiply-add (build with -ffp-contract=off).  OpenMP is
@@ -190,6 +200,69 @@ int64_t or_direction(int64_t m, int64_t n, const double* A, const double* x, con
   return fail;
 }
 
+/* Newton direction of the infeasible-start variant (reading R11):
+ *   D = x/s, r_d = c - A' y - s, r = b + A (D r_d), M = A D A', M dy = r,
+ *   w = A' dy, ds = r_d - w, dx = D(-ds) - x.
+ * D_out, r_out, rd_out may be NULL.  Returns -1, or the failing pivot. */
+int64_t or_direction_infeasible(int64_t m, int64_t n, const double* A, const double* b, const double* c,
+                                const double* x, const double* y, const double* s, double* dx, double* dy,
+                                double* ds, double* D_out, double* r_out, double* rd_out) {
+  double* D = (double*)malloc((size_t)n * sizeof(double));
+  double* rd = (double*)malloc((size_t)n * sizeof(double));
+  double* u = (double*)malloc((size_t)n * sizeof(double));
+  double* w = (double*)malloc((size_t)n * sizeof(double));
+  double* r = (double*)malloc((size_t)m * sizeof(double));
+  double* z = (double*)malloc((size_t)m * sizeof(double));
+  double* M = (double*)malloc((size_t)(m * m) * sizeof(double));
+  double* L = (double*)malloc((size_t)(m * m) * sizeof(double));
+  or_scaling(n, x, s, D);
+  or_gemv_t(m, n, A, y, w);
+  for (int64_t j = 0; j < n; ++j) {
+    rd[j] = (c[j] - w[j]) - s[j];
+    u[j] = D[j] * rd[j];
+  }
+  or_gemv(m, n, A, u, z);
+  for (int64_t p = 0; p < m; ++p) r[p] = b[p] + z[p];
+  or_normal_matrix(m, n, A, D, M);
+  int64_t fail = or_cholesky(m, M, L);
+  if (fail < 0) {
+    or_forward(m, L, r, z);
+    or_backward(m, L, z, dy);
+    or_gemv_t(m, n, A, dy, w);
+    for (int64_t j = 0; j < n; ++j) {
+      ds[j] = rd[j] - w[j];
+      dx[j] = -D[j] * ds[j] - x[j]; /* = D(-ds) - x exactly */
+    }
+  }
+  if (D_out) memcpy(D_out, D, (size_t)n * sizeof(double));
+  if (r_out) memcpy(r_out, r, (size_t)m * sizeof(double));
+  if (rd_out) memcpy(rd_out, rd, (size_t)n * sizeof(double));
+  free(D); free(rd); free(u); free(w); free(r); free(z); free(M); free(L);
+  return fail;
+}
+
+/* Relative residuals of (x, y, s) (reading R11):
+ * out[0] = ||b - A x||_inf / (1 + ||b||_inf), out[1] = ||c - A' y - s||_inf / (1 + ||c||_inf). */
+void or_residuals(int64_t m, int64_t n, const double* A, const double* b, const double* c, const double* x,
+                  const double* y, const double* s, double* out) {
+  double* t = (double*)malloc((size_t)m * sizeof(double));
+  double* w = (double*)malloc((size_t)n * sizeof(double));
+  or_gemv(m, n, A, x, t);
+  or_gemv_t(m, n, A, y, w);
+  double rp = 0.0, bn = 0.0, rdn = 0.0, cn = 0.0;
+  for (int64_t p = 0; p < m; ++p) {
+    rp = fmax(rp, fabs(b[p] - t[p]));
+    bn = fmax(bn, fabs(b[p]));
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    rdn = fmax(rdn, fabs((c[j] - w[j]) - s[j]));
+    cn = fmax(cn, fabs(c[j]));
+  }
+  out[0] = rp / (1.0 + bn);
+  out[1] = rdn / (1.0 + cn);
+  free(t); free(w);
+}
+
 /* psi = max{ phi(-X^{-1} dx), phi(-S^{-1} ds) }, phi(u) = max_j u_j
  * (Section III, reading R1). */
 double or_psi(int64_t n, const double* x, const double* s, const double* dx, const double* ds) {
@@ -205,6 +278,9 @@ double or_psi(int64_t n, const double* x, const double* s, const double* dx, con
 
 /* Step length of the algorithm: alpha/psi, or 1 when psi <= 1 (reading R4). */
 double or_theta(double psi, double alpha) { return psi <= 1.0 ? 1.0 : alpha / psi; }
+
+/* Step length of the infeasible-start variant (reading R11): min(1, alpha/psi). */
+double or_theta_infeasible(double psi, double alpha) { return psi <= alpha ? 1.0 : alpha / psi; }
 
 /* (x,y,s) += theta (dx,dy,ds). */
 void or_step(int64_t m, int64_t n, double theta, double* x, double* y, double* s, const double* dx,
@@ -236,10 +312,13 @@ double or_rel_gap(int64_t m, int64_t n, const double* b, const double* c, const 
  * [x (n) | y (m) | s (n)].  Both must hold max_iter records.
  * *iters_out = number of Newton directions computed.
  * *fail_index_out = failing pivot index on OR_NOT_SPD, else -1.
+ * infeasible != 0 runs the infeasible-start variant (reading R11); then
+ * res_trace, if not NULL, receives per iteration the 2 relative residuals
+ * of or_residuals after the step.
  * Returns one of the OR_* codes above. */
 int or_solve(int64_t m, int64_t n, const double* A, const double* b, const double* c, double* x, double* y,
              double* s, double alpha, double tol, int max_iter, int* iters_out, double* trace,
-             double* iterates, int64_t* fail_index_out) {
+             double* iterates, int64_t* fail_index_out, int infeasible, double* res_trace) {
   double* dx = (double*)malloc((size_t)n * sizeof(double));
   double* dy = (double*)malloc((size_t)m * sizeof(double));
   double* ds = (double*)malloc((size_t)n * sizeof(double));
@@ -247,7 +326,8 @@ int or_solve(int64_t m, int64_t n, const double* A, const double* b, const doubl
   int status = OR_MAX_ITER, small_steps = 0, k;
   *fail_index_out = -1;
   for (k = 0; k < max_iter; ++k) {
-    int64_t fail = or_direction(m, n, A, x, s, dx, dy, ds, D, NULL, NULL, NULL);
+    int64_t fail = infeasible ? or_direction_infeasible(m, n, A, b, c, x, y, s, dx, dy, ds, D, NULL, NULL)
+                              : or_direction(m, n, A, x, s, dx, dy, ds, D, NULL, NULL, NULL);
     if (fail >= 0) {
       *fail_index_out = fail;
       status = OR_NOT_SPD;
@@ -263,9 +343,17 @@ int or_solve(int64_t m, int64_t n, const double* A, const double* b, const doubl
       break;
     }
     double psi = or_psi(n, x, s, dx, ds);
-    double theta = or_theta(psi, alpha);
+    double theta = infeasible ? or_theta_infeasible(psi, alpha) : or_theta(psi, alpha);
     or_step(m, n, theta, x, y, s, dx, dy, ds);
     double gap = or_rel_gap(m, n, b, c, x, y);
+    double res[2] = {0.0, 0.0};
+    if (infeasible) {
+      or_residuals(m, n, A, b, c, x, y, s, res);
+      if (res_trace) {
+        res_trace[2 * k + 0] = res[0];
+        res_trace[2 * k + 1] = res[1];
+      }
+    }
     if (trace) {
       double dmax = D[0], dmin = D[0];
       for (int64_t j = 1; j < n; ++j) {
@@ -283,12 +371,17 @@ int or_solve(int64_t m, int64_t n, const double* A, const double* b, const doubl
       memcpy(it + n, y, (size_t)m * sizeof(double));
       memcpy(it + n + m, s, (size_t)n * sizeof(double));
     }
-    if (psi <= 1.0) {
+    if (infeasible) {
+      if (fabs(gap) < tol && res[0] < tol && res[1] < tol) {
+        status = OR_OPTIMAL;
+        ++k;
+        break;
+      }
+    } else if (psi <= 1.0) {
       status = OR_OPTIMAL_EXACT;
       ++k;
       break;
-    }
-    if (gap < tol) {
+    } else if (gap < tol) {
       status = OR_OPTIMAL;
       ++k;
       break;

@@ -2,8 +2,9 @@
 something other than the oracle itself -- a hand-solved LP, brute-force basis
 enumeration, the m=1 closed form, the identities that Eq. (3) fixes, the
 Sherman-Morrison recurrence of Section V-A used as an independent solver, the
-exact gap recurrence of a feasible step, and library routines for the special
-cases.  ``test_planted_mistakes_fail_a_pin`` compiles mutated copies of the C
+exact gap recurrence of a feasible step, the full Newton system of the
+infeasible-start variant solved by LAPACK, and library routines for the
+special cases.  ``test_planted_mistakes_fail_a_pin`` compiles mutated copies of the C
 oracle and checks that each planted mistake trips at least one pin.
 """
 import itertools
@@ -336,9 +337,103 @@ def pin_not_spd(o):
                                                                                            res["fail_index"])
 
 
+def infeasible_start(lp, seed):
+    """A seeded interior point that satisfies neither A x = b nor A'y + s = c."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.5, 2.0, lp.n), rng.standard_normal(lp.m), rng.uniform(0.5, 2.0, lp.n)
+
+
+def pin_infeasible_newton_system(o, m=4, n=9, seed=6):
+    """Infeasible-start variant: the direction is the solution of the full
+    (2n + m) x (2n + m) Newton system of Eq. (3) with the residuals
+    b - A x and c - A'y - s on its right-hand side, solved here by LAPACK
+    (numpy.linalg.solve), at an infeasible point and along a run."""
+    lp = lpgen.generate(m, n, seed=seed)
+    A = lp.A64
+    x, y, s = infeasible_start(lp, seed)
+    worst = 0.0
+    for _ in range(4):
+        K = np.zeros((2 * n + m, 2 * n + m))
+        K[:m, :n] = A                                  # A dx            = b - A x
+        K[m:m + n, n:n + m] = A.T                      # A' dy + ds      = c - A'y - s
+        K[m:m + n, n + m:] = np.eye(n)
+        K[m + n:, :n] = np.diag(s)                     # S dx + X ds     = -X s
+        K[m + n:, n + m:] = np.diag(x)
+        rhs = np.concatenate([lp.b - A @ x, lp.c - A.T @ y - s, -x * s])
+        ref = np.linalg.solve(K, rhs)
+        d = o.direction_infeasible(A, lp.b, lp.c, x, y, s)
+        got = np.concatenate([d["dx"], d["dy"], d["ds"]])
+        worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
+        th = 0.5 / max(np.max(-d["dx"] / x), np.max(-d["ds"] / s), 1.0)
+        x, y, s = x + th * d["dx"], y + th * d["dy"], s + th * d["ds"]
+    return worst < 1e-10, "%.1e" % worst
+
+
+def pin_infeasible_feasible_start(o, seed=2):
+    """From a feasible start the variant's system is the paper's: the same
+    direction as ``direction`` to rounding."""
+    lp = lpgen.generate(10, 25, seed=seed)
+    d0 = o.direction(lp.A64, lp.x0, lp.s0)
+    d1 = o.direction_infeasible(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+    err = max(np.abs(d1[k] - d0[k]).max() / np.abs(d0[k]).max() for k in ("dx", "dy", "ds"))
+    return err < 1e-11, "%.1e" % err
+
+
+def pin_infeasible_runs(o, seeds=(0, 1, 2)):
+    """Runs of the variant from infeasible points: the residuals shrink by
+    (1 - theta_k) per step (the first two rows of Eq. (3); up to the solve's
+    residual, which grows with max D / min D near the optimum), the
+    iterate keeps at least the fraction 1 - alpha of each coordinate, and the
+    run ends at the brute-force optimal vertex with both residuals (computed
+    here) below tol."""
+    ok, det = True, []
+    # starts in [0.5, 2], and starts scaled by 0.1 (y = 0) that are still far
+    # from feasible when the gap first falls below tol
+    cases = [((m, n), seed, 1.0, 1e-9) for (m, n), seed in itertools.product(TINY, seeds)]
+    cases += [((1, 3), 1, 0.1, 1e-6), ((4, 8), 0, 0.1, 1e-6), ((2, 8), 0, 0.1, 1e-6)]
+    for (m, n), seed, scale, tol in cases:
+        lp = lpgen.generate(m, n, seed=seed)
+        x, y, s = infeasible_start(lp, 100 + seed)
+        if scale != 1.0:
+            x, y, s = scale * x, 0.0 * y, scale * s
+        res = o.solve(lp.A64, lp.b, lp.c, x, y, s, alpha=ALPHA, tol=tol, keep_iterates=True, infeasible=True)
+        pts = [(x, y, s)] + [(r[:n], r[n:n + m], r[n + m:]) for r in res["iterates"]]
+        rp = [lp.b - lp.A64 @ p[0] for p in pts]
+        rd = [lp.c - lp.A64.T @ p[1] - p[2] for p in pts]
+        rec, frac = 0.0, True
+        for k, th in enumerate(res["trace"][:, 1]):
+            rec = max(rec, np.abs(rp[k + 1] - (1 - th) * rp[k]).max() / (1 + np.abs(rp[0]).max()),
+                      np.abs(rd[k + 1] - (1 - th) * rd[k]).max() / (1 + np.abs(rd[0]).max()))
+            frac &= bool(np.all(pts[k + 1][0] >= (1 - ALPHA) * pts[k][0] * (1 - 1e-12))
+                         and np.all(pts[k + 1][2] >= (1 - ALPHA) * pts[k][2] * (1 - 1e-12)))
+        opt, _ = brute_force_optimum(lp.A64, lp.b, lp.c)
+        cx = float(lp.c @ res["x"])
+        pres = np.abs(rp[-1]).max() / (1 + np.abs(lp.b).max())
+        dres = np.abs(rd[-1]).max() / (1 + np.abs(lp.c).max())
+        good = (res["status"] == oracle.OPTIMAL and rec < 1e-8 and frac and pres < tol and dres < tol
+                and abs(cx - opt) <= 10 * tol * (1 + abs(opt)))
+        ok &= bool(good)
+        if not good:
+            det.append("m=%d n=%d seed=%d status=%d rec=%.1e frac=%s pres=%.1e dres=%.1e cx=%.12g opt=%.12g"
+                       % (m, n, seed, res["status"], rec, frac, pres, dres, cx, opt))
+    return ok, "; ".join(det)
+
+
+def pin_residuals(o, seed=3):
+    """The relative residuals against numpy's products."""
+    lp = lpgen.generate(7, 20, seed=seed)
+    x, y, s = infeasible_start(lp, seed)
+    got = o.residuals(lp.A64, lp.b, lp.c, x, y, s)
+    want = (np.abs(lp.b - lp.A64 @ x).max() / (1 + np.abs(lp.b).max()),
+            np.abs(lp.c - lp.A64.T @ y - s).max() / (1 + np.abs(lp.c).max()))
+    err = max(abs(g - w) / w for g, w in zip(got, want))
+    return err < 1e-13, "%.1e" % err
+
+
 PINS = [pin_textbook_lp, pin_full_step_branch, pin_brute_force, pin_m1_closed_form, pin_newton_identities, pin_sherman_morrison,
         pin_normal_matrix, pin_cholesky, pin_triangular, pin_gemv, pin_psi_theta_step, pin_run_invariants,
-        pin_backward_error, pin_not_spd]
+        pin_backward_error, pin_not_spd, pin_infeasible_newton_system, pin_infeasible_feasible_start,
+        pin_infeasible_runs, pin_residuals]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -382,6 +477,15 @@ MUTANTS = [
     ("step y sign", "y[p] = y[p] + theta * dy[p];", "y[p] = y[p] - theta * dy[p];"),
     ("gap sign", "return (cx - by) / (1.0 + fabs(cx));", "return (cx + by) / (1.0 + fabs(cx));"),
     ("psi test strict", "if (psi <= 1.0) {", "if (psi < 0.0) {"),
+    # the infeasible-start variant
+    ("variant r_d sign of s", "rd[j] = (c[j] - w[j]) - s[j];", "rd[j] = (c[j] - w[j]) + s[j];"),
+    ("variant rhs drops A D r_d", "r[p] = b[p] + z[p];", "r[p] = b[p];"),
+    ("variant rhs uses A x", "r[p] = b[p] + z[p];", "r[p] = b[p] - z[p];"),
+    ("variant ds drops r_d", "ds[j] = rd[j] - w[j];", "ds[j] = -w[j];"),
+    ("variant u drops D", "u[j] = D[j] * rd[j];", "u[j] = rd[j];"),
+    ("variant theta overshoots", "psi <= alpha ? 1.0 : alpha / psi", "psi <= 1.0 ? 1.0 : 1.0 / psi"),
+    ("variant stop ignores residuals", "fabs(gap) < tol && res[0] < tol && res[1] < tol", "fabs(gap) < tol"),
+    ("residual norm of b", "bn = fmax(bn, fabs(b[p]));", "bn = fmax(bn, fabs(t[p]));"),
 ]
 
 
