@@ -58,7 +58,7 @@ def syrk_roofline(form, m, n, splits, ms_per_launch, peaks, workload=None):
     lower-triangle product, m(m+1)/2 entries of n multiply-adds (m^2 n flops,
     FMA = 2); the tensor-core forms execute that product once per split term
     of D.*A, reported separately as executed work."""
-    terms = splits if form in ("bf16_ir", "tf32_ir") else 1
+    terms = splits if form == "bf16_ir" else 1
     flops = float(m) * (m + 1) * n
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     if form == "bf16_ir":
@@ -290,7 +290,7 @@ def run_normal_only(args):
     prof = S.profile_read()
     S.close()
     ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
-    splits = args.splits or 3
+    splits = (args.splits or 3) if args.form == "bf16_ir" else 1
     peaks = load_peaks()
     roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, peaks, args.workload)
     out = dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits, ms_per_launch=ms,
@@ -333,7 +333,7 @@ def run_ours(args):
     if args.dspread is not None:
         opts["dspread_refactor"] = args.dspread
     S = P.Solver(m, n, args.form, a_dtype, stream=stream, **opts)
-    splits = S.options.splits or 3
+    splits = (S.options.splits or 3) if args.form == "bf16_ir" else 1
 
     def restart():
         x.copy_(x0)

@@ -57,7 +57,8 @@ typedef enum {
 /* Precision forms of the normal-equations solve. */
 typedef enum {
   PDAS_FP64 = 0,    /* M = A D A' formed and factored in FP64                          */
-  PDAS_TF32_IR = 1, /* M formed on tcgen05 tensor cores from TF32 operands, FP32 factor,
+  PDAS_TF32_IR = 1, /* M formed on tcgen05 tensor cores from TF32 operands (A and D.*A
+                       rounded to TF32 each call; A stored as FP64 or FP32), FP32 factor,
                        FP64 refinement of dy                                            */
   PDAS_BF16_IR = 2, /* as TF32_IR with BF16 operands (needs A stored as BF16)            */
   PDAS_FP32_IR = 3  /* M formed with FP32 SIMT arithmetic, FP32 factor, FP64 refinement  */
@@ -76,8 +77,8 @@ typedef struct {
                               iteration once max(D)/min(D) exceeds this (e.g. 1e8); <= 0 disables
                               the rule, leaving the switch to factor or refinement failure    (0) */
   void* stream;            /* cudaStream_t for all work; NULL = the legacy default stream      */
-  int splits;              /* tensor-core forms: number of low-precision terms of D.*A (1..3);
-                              0 = form default (3)                                              */
+  int splits;              /* PDAS_BF16_IR: number of BF16 terms of D.*A (1..3), 0 = 3;
+                              PDAS_TF32_IR takes one term (0 or 1; more: PDAS_ERR_UNSUPPORTED) */
   double stall_theta;      /* step length below which a step counts as stalled          (1e-12) */
   int stall_count;         /* consecutive stalled steps that end pdas_solve                  (5) */
   double refine_be;        /* refinement also stops when the normwise backward error

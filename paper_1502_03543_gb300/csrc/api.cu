@@ -656,7 +656,8 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
       opt.stall_count < 1 || !(opt.stall_theta >= 0))
     return PDAS_ERR_ARG;
   if (opt.form == PDAS_BF16_IR && opt.a_dtype != PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
-  if (opt.form == PDAS_TF32_IR && opt.a_dtype == PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
+  // TF32 form: one TF32 term of D.*A (A itself is rounded to TF32), FP64 or FP32 storage
+  if (opt.form == PDAS_TF32_IR && (opt.a_dtype == PDAS_A_BF16 || opt.splits > 1)) return PDAS_ERR_UNSUPPORTED;
   pdas_ctx* h = new (std::nothrow) pdas_ctx();
   if (!h) return PDAS_ERR_CUDA;
   h->m = m;

@@ -1,5 +1,12 @@
 // syrk_tc.cu -- the normal matrix M = A D A' (Section V) on the tcgen05
-// tensor cores, for the BF16 mixed-precision form.
+// tensor cores, for the BF16 and TF32 mixed-precision forms.
+//
+// TF32 form (A stored in FP64 or FP32): A and B = D.*A are rounded once per
+// call to TF32 (FP32 containers, 10 stored mantissa bits, round to nearest
+// even) and M = A_tf32 B_tf32' takes one tcgen05.mma.kind::tf32 term; each
+// operand carries 2^-11 relative error, which the FP64 refinement removes
+// from the direction.  The rest of this header describes the BF16 form; the
+// TF32 kernel is the same pipeline with 32 FP32 elements per 128-byte row.
 //
 // D is folded into one operand: B = D.*A (row q: B_qj = A_qj D_j) is split
 // into `splits` BF16 terms B = B_0 + B_1 (+ B_2), each carrying the next 8
@@ -43,10 +50,10 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 128;
-constexpr int BK = 64;
+constexpr int BK = 64;        // K elements of one 128-byte operand row (BF16)
+constexpr int BK_TF32 = 32;   // the same for TF32 (4-byte containers)
 constexpr int KC_BLOCKS = 2;  // K steps of BK per accumulation chunk (KC = 128)
-constexpr int UMMA_K = 16;
-constexpr uint32_t TILE_BYTES = BM * BK * 2;  // one 128 x 64 BF16 tile (A and each B_t)
+constexpr uint32_t TILE_BYTES = BM * 128;     // one 128-row x 128-byte tile (A and each B_t)
 constexpr uint32_t RING_BYTES = 192 * 1024;
 constexpr uint32_t TMEM_COLS = 256;           // two chunk buffers of BN columns
 constexpr int NUM_THREADS = 192;
@@ -60,14 +67,16 @@ struct Ring {
 
 using namespace tc;
 constexpr uint32_t kIdescBf16 = idesc_bf16(BM, BN);
+constexpr uint32_t kIdescTf32 = idesc_tf32(BM, BN);
 
-template <int S>
+template <int S, bool TF32 = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
               const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
               const int2* __restrict__ tiles, int nk, int64_t m, int64_t ldm, float* __restrict__ M, Scalars* sc) {
   constexpr uint32_t STAGE_BYTES = Ring<S>::STAGE_BYTES;
   constexpr int STAGES = Ring<S>::STAGES;
+  constexpr int EK = TF32 ? BK_TF32 : BK;  // K elements per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -118,10 +127,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         const uint32_t dst = sbase + s * STAGE_BYTES;
         mbar_expect_tx(full(s), STAGE_BYTES);
-        tma_load_2d(dst, &tmA, kb * BK, p0, full(s));
-        tma_load_2d(dst + TILE_BYTES, &tmB0, kb * BK, q0, full(s));
-        if (S > 1) tma_load_2d(dst + 2 * TILE_BYTES, &tmB1, kb * BK, q0, full(s));
-        if (S > 2) tma_load_2d(dst + 3 * TILE_BYTES, &tmB2, kb * BK, q0, full(s));
+        tma_load_2d(dst, &tmA, kb * EK, p0, full(s));
+        tma_load_2d(dst + TILE_BYTES, &tmB0, kb * EK, q0, full(s));
+        if (S > 1) tma_load_2d(dst + 2 * TILE_BYTES, &tmB1, kb * EK, q0, full(s));
+        if (S > 2) tma_load_2d(dst + 3 * TILE_BYTES, &tmB2, kb * EK, q0, full(s));
         issued = kb + 1;
       }
       if (*abort_flag) {  // let every issued copy land before the CTA can exit
@@ -152,8 +161,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         for (int t = 0; t < S; ++t) {
           const uint64_t bd = sdesc_sw128(sbase + s * STAGE_BYTES + (1 + t) * TILE_BYTES);
 #pragma unroll
-          for (int k = 0; k < BK / UMMA_K; ++k)  // advance 32 bytes (16 BF16) along K per MMA
-            umma_f16(d, ad + 2 * k, bd + 2 * k, kIdescBf16, (chunk_start && t == 0 && k == 0) ? 0u : 1u);
+          for (int k = 0; k < 4; ++k) {  // advance 32 bytes (16 BF16 or 8 TF32) along K per MMA
+            const uint32_t accum = (chunk_start && t == 0 && k == 0) ? 0u : 1u;
+            if constexpr (TF32) umma_tf32(d, ad + 2 * k, bd + 2 * k, kIdescTf32, accum);
+            else umma_f16(d, ad + 2 * k, bd + 2 * k, kIdescBf16, accum);
+          }
         }
         umma_commit(empty(s));
         if ((kb % KC_BLOCKS) == KC_BLOCKS - 1 || kb == nk - 1) umma_commit(chunk_full(buf));
@@ -274,6 +286,30 @@ __global__ void k_fold_split(int64_t m, int64_t n, int64_t kpad, const __nv_bflo
   }
 }
 
+// Round an FP32 value to TF32 (10 stored mantissa bits), to nearest with ties
+// to even: add one less than half the spacing of the TF32 grid, plus the
+// lowest kept bit, then clear the 13 dropped bits.  Inf stays inf, a finite
+// value above the largest TF32 number rounds to inf.
+__device__ __forceinline__ float round_tf32(float f) {
+  uint32_t u = __float_as_uint(f);
+  u += 0xfffu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xffffe000u);
+}
+
+// TF32 operands: opa = tf32(A), opb = tf32(fl32(A_pj D_j)) with the product in
+// FP64 (exact for FP32 A), both with row stride kpad.
+template <typename T>
+__global__ void k_fold_tf32(int64_t m, int64_t n, int64_t kpad, const T* __restrict__ A,
+                            const double* __restrict__ D, float* __restrict__ opa, float* __restrict__ opb) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / n, j = e - p * n;
+    const double a = (double)A[e];
+    opa[p * kpad + j] = round_tf32((float)a);
+    opb[p * kpad + j] = round_tf32((float)(a * D[j]));
+  }
+}
+
 // ---- host side ---------------------------------------------------------------
 struct TcHost {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -301,15 +337,17 @@ cudaError_t get_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
   return cudaSuccess;
 }
 
-// 2D BF16 tensor map: dims {n (K, innermost), m}, row stride in elements,
-// box {BK, box_rows}, 128-byte swizzle, zero fill out of bounds.
+// 2D BF16 (or, with tf32, FP32) tensor map: dims {n (K, innermost), m}, row
+// stride in elements, box {one 128-byte row, box_rows}, 128-byte swizzle,
+// zero fill out of bounds.
 cudaError_t encode_bf16(TcHost* hs, CUtensorMap* map, const void* base, int64_t m, int64_t n, int64_t row_stride,
-                        int box_rows) {
+                        int box_rows, bool tf32 = false) {
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
-  cuuint64_t strides[1] = {(cuuint64_t)(row_stride * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(row_stride * (tf32 ? 4 : 2))};
+  cuuint32_t box[2] = {(cuuint32_t)(tf32 ? BK_TF32 : BK), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = hs->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+  CUresult r = hs->encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void*>(base), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -318,11 +356,14 @@ cudaError_t encode_bf16(TcHost* hs, CUtensorMap* map, const void* base, int64_t 
 }  // namespace
 
 cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int splits, int64_t m, int64_t n) {
-  if (form != PDAS_BF16_IR || a_dtype != PDAS_A_BF16) return cudaErrorNotSupported;
+  const bool tf32 = form == PDAS_TF32_IR;
+  if (tf32 ? (a_dtype != PDAS_A_F64 && a_dtype != PDAS_A_F32) || splits > 1
+           : (form != PDAS_BF16_IR || a_dtype != PDAS_A_BF16))
+    return cudaErrorNotSupported;
   if (m > ((int64_t)1 << 30) / BM || n > ((int64_t)1 << 31) - BK) return cudaErrorNotSupported;
   w->form = form;
   w->a_dtype = a_dtype;
-  w->splits = splits > 0 ? splits : 3;
+  w->splits = tf32 ? 1 : splits > 0 ? splits : 3;
   w->m = m;
   w->n = n;
   w->kpad = (n + BK - 1) / BK * BK;
@@ -332,8 +373,9 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   w->host = hs;
   cudaError_t e = get_encoder(&hs->encode);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&w->opb, sizeof(__nv_bfloat16) * (size_t)w->splits * m * w->kpad);
-  if (e == cudaSuccess && n % 8 != 0) e = cudaMalloc(&w->opa, sizeof(__nv_bfloat16) * (size_t)m * w->kpad);
+  const size_t esz = tf32 ? sizeof(float) : sizeof(__nv_bfloat16);
+  e = cudaMalloc(&w->opb, esz * (size_t)w->splits * m * w->kpad);
+  if (e == cudaSuccess && (tf32 || n % 8 != 0)) e = cudaMalloc(&w->opa, esz * (size_t)m * w->kpad);
   if (e == cudaSuccess) e = cudaMalloc(&hs->D32, sizeof(float) * (size_t)((n + 7) / 8 * 8));
   // Lower-triangle tile list ((I, J) with some row p >= some column q),
   // ordered by G x G super-tiles with G ~ sqrt(#SMs): the CTAs resident at
@@ -360,12 +402,14 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   if (e == cudaSuccess) e = cudaMemcpy(hs->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
   for (int t = 0; e == cudaSuccess && t < 3; ++t) {
     const int tt = t < w->splits ? t : 0;  // unused maps alias term 0
-    e = encode_bf16(hs, &hs->mapB[t], (const __nv_bfloat16*)w->opb + (size_t)tt * m * w->kpad, m, n, w->kpad, BN);
+    e = encode_bf16(hs, &hs->mapB[t], (const uint8_t*)w->opb + esz * tt * m * w->kpad, m, n, w->kpad, BN, tf32);
   }
-  if (e == cudaSuccess && w->opa) e = encode_bf16(hs, &hs->mapA_copy, w->opa, m, n, w->kpad, BM);
+  if (e == cudaSuccess && w->opa) e = encode_bf16(hs, &hs->mapA_copy, w->opa, m, n, w->kpad, BM, tf32);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_syrk_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   return e;
 }
 
@@ -386,6 +430,18 @@ cudaError_t tc_prepare(cudaStream_t st, TcWorkspace* w, const void* A, const dou
   if (reinterpret_cast<uintptr_t>(A) % 16 != 0) return cudaErrorInvalidValue;
   TcHost* hs = static_cast<TcHost*>(w->host);
   const int64_t m = w->m, n = w->n;
+  if (w->form == PDAS_TF32_IR) {
+    const int64_t work = m * n;
+    const unsigned grid = (unsigned)((work + 255) / 256 < 4736 ? (work + 255) / 256 : 4736);
+    if (w->a_dtype == PDAS_A_F64)
+      k_fold_tf32<double><<<grid, 256, 0, st>>>(m, n, w->kpad, static_cast<const double*>(A), D,
+                                                static_cast<float*>(w->opa), static_cast<float*>(w->opb));
+    else
+      k_fold_tf32<float><<<grid, 256, 0, st>>>(m, n, w->kpad, static_cast<const float*>(A), D,
+                                               static_cast<float*>(w->opa), static_cast<float*>(w->opb));
+    *launches = 1;
+    return cudaGetLastError();
+  }
   const bool direct = (n % 8 == 0);
   k_d32<<<(unsigned)((n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184), 256, 0, st>>>(n, D, hs->D32);
   const int64_t work = direct ? m * (n / 8) : m * n;
@@ -403,6 +459,15 @@ cudaError_t tc_syrk(cudaStream_t st, TcWorkspace* w, const void* A, float* M32, 
   *launches = 0;
   TcHost* hs = static_cast<TcHost*>(w->host);
   const int64_t m = w->m, n = w->n;
+  Scalars* scw = const_cast<Scalars*>(sc);
+  const dim3 grid((unsigned)hs->ntiles);
+  if (w->form == PDAS_TF32_IR) {
+    const int nk = (int)((n + BK_TF32 - 1) / BK_TF32);
+    k_syrk_tc<1, true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapA_copy, hs->mapB[0], hs->mapB[1], hs->mapB[2],
+                                                              hs->tiles, nk, m, ldm, M32, scw);
+    *launches = 1;
+    return cudaGetLastError();
+  }
   CUtensorMap mapA;
   if (n % 8 == 0) {
     cudaError_t e = encode_bf16(hs, &mapA, A, m, n, n, BM);
@@ -411,8 +476,6 @@ cudaError_t tc_syrk(cudaStream_t st, TcWorkspace* w, const void* A, float* M32, 
     mapA = hs->mapA_copy;
   }
   const int nk = (int)((n + BK - 1) / BK);
-  Scalars* scw = const_cast<Scalars*>(sc);
-  const dim3 grid((unsigned)hs->ntiles);
   if (w->splits == 1)
     k_syrk_tc<1><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mapA, hs->mapB[0], hs->mapB[1], hs->mapB[2], hs->tiles, nk,
                                                         m, ldm, M32, scw);

@@ -80,6 +80,15 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A[smem] B[smem]' (M x N x 8, TF32 in (32-bit containers), FP32 accumulate); one thread issues.
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::
+          "r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // The mbarrier at bar gets one arrival once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -109,9 +118,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // Shared-memory matrix descriptor: K-major operand tile, rows of 128 bytes
-// (64 BF16) with the 128-byte swizzle (16-byte chunk c of row r stored at
+// (64 BF16 or 32 TF32) with the 128-byte swizzle (16-byte chunk c of row r stored at
 // chunk c ^ (r % 8)); 8-row groups 1024 bytes apart; base 1024-aligned.
-// Advancing the start address by 32 bytes moves 16 elements along K.
+// Advancing the start address by 32 bytes moves one MMA step along K
+// (16 BF16 or 8 TF32 elements).
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address, 16-byte units
   d |= (uint64_t)1 << 16;                             // leading byte offset (unused when swizzled)
@@ -122,8 +132,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 }
 
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+// Bits 4-5: accumulator type (1 = FP32); 7-9 and 10-12: A and B type (kind::f16:
+// 1 = BF16; kind::tf32: 2 = TF32); 17-22: N / 8; 24-28: M / 16.
 constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Instruction descriptor: TF32 x TF32 -> FP32 (kind::tf32), both operands K-major, M x N.
+constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 }  // namespace tc

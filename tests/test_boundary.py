@@ -74,6 +74,14 @@ def test_host_side_validation_without_gpu(lib):
     bad = N.Options.from_buffer_copy(o)
     bad.form, bad.a_dtype = N.BF16_IR, N.A_F64
     assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    # TF32 operands: FP64 or FP32 storage, one term of D.*A
+    bad = N.Options.from_buffer_copy(o)
+    bad.form, bad.a_dtype = N.TF32_IR, N.A_BF16
+    assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    bad = N.Options.from_buffer_copy(o)
+    bad.form, bad.splits = N.TF32_IR, 2
+    assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    assert not h.value
     # null handle / pointers
     assert L.pdas_step(None, None, None, None, None, None, None, 0.5, None) == N.ERR_ARG
     assert L.pdas_solve(None, None, None, None, None, None, None, 0.5, 1e-8, None, None) == N.ERR_ARG

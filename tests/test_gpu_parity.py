@@ -445,6 +445,82 @@ def test_bf16_ir_solve_512x2048(pdas, dspread):  # with and without the max(D)/m
     assert np.linalg.norm(lp.A64.T @ yh + sh - lp.c) <= 1e-12 * np.linalg.norm(lp.c)
 
 
+def tf32_bound(A64, D, n):
+    """|M_tf32 - M| elementwise.  A and D.*A are each rounded to FP32 and then
+    to TF32 (u = 2^-11, round to nearest even), so a product carries at most
+    (1 + 2^-11 + 2^-24)^2 - 1 < 2^-10 + 2^-20 relative error; each 64-long
+    chunk takes 8 tensor-core accumulation steps (u = 2^-23, truncating) and
+    the chunk sums are added in round-to-nearest FP32 (u = 2^-24)."""
+    rep = 2.0 ** -10 + 2.0 ** -20
+    acc = gamma(9, 2.0 ** -23) + gamma(n // 64 + 2, 2.0 ** -24)
+    return (rep + acc + rep * acc) * ((np.abs(A64) * D) @ np.abs(A64).T)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("m,n", TC_SHAPES)
+def test_normal_matrix_tf32_tensor_cores(pdas, m, n, storage):
+    """TF32 form (tcgen05 kind::tf32): the lower triangle of M = A D A'
+    against the FP64 oracle within the TF32 rounding bound, and its scaled
+    error near 2^-10."""
+    lp = lpgen.generate(m, n, seed=7 * m + n, storage=storage)
+    rng = np.random.default_rng(12)
+    x, s = rng.uniform(0.01, 10, n), rng.uniform(0.01, 10, n)
+    with pdas.Solver(m, n, "tf32_ir", TORCH_DT[storage]) as S:
+        S.form_normal(dev_A(lp), dv(x), dv(s))
+        M = host(S.copy_matrix()).astype(np.float64)
+    D = oracle.scaling(x, s)
+    ref = oracle.normal_matrix(lp.A64, D)
+    low = np.tril_indices(m)
+    assert np.all(np.abs(M[low] - ref[low]) <= tf32_bound(lp.A64, D, n)[low])
+    assert scaled_error(M, ref) <= 4e-3
+
+
+def test_tf32_rounding_is_to_nearest_even(pdas):
+    """Entries chosen so that A and D.*A are exact in TF32 or sit exactly on a
+    tie: M = A D A' of a 1 x n problem must equal the sum of the TF32 values
+    rounded to nearest even (ties: 1 + 2^-11 -> 1, 1 + 3 * 2^-11 -> 1 + 2^-9)."""
+    n = 8
+    a = np.array([1.0, 1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 1 + 2.0 ** -10, 0.5, -0.25, 0.0, 1 + 2.0 ** -12])
+    a_tf32 = np.array([1.0, 1.0, 1 + 2.0 ** -9, 1 + 2.0 ** -10, 0.5, -0.25, 0.0, 1.0])
+    # every product and partial sum is a multiple of 2^-20 below 8: exact in FP32
+    x, s = np.ones(n), np.ones(n)  # D = 1: D.*A = A
+    with pdas.Solver(1, n, "tf32_ir", torch.float64) as S:
+        S.form_normal(dv(a.reshape(1, n)), dv(x), dv(s))
+        M = host(S.copy_matrix()).astype(np.float64)
+    assert M[0, 0] == float(np.sum(a_tf32 * a_tf32))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tf32_ir_solve_matches_oracle(pdas, seed):
+    lp = lpgen.generate(64, 128, seed=seed, storage="f64")
+    ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    with pdas.Solver(lp.m, lp.n, "tf32_ir", torch.float64) as S:
+        out = S.solve(dev_A(lp), dv(lp.b), dv(lp.c), x, y, s, alpha=0.95, tol=1e-8)
+    assert out["status"] == 1
+    obj_ref = float(lp.c @ ref["x"])
+    assert abs(float(lp.c @ host(x)) - obj_ref) <= 1e-8 * abs(obj_ref)
+    assert out["iters"] == ref["iters"]
+
+
+def test_tf32_ir_c2_first_iterations(pdas):
+    """2048 x 8192 FP64-stored A in the TF32 form: the refined direction makes
+    the first two iterates agree with the oracle's to 1e-9 normwise."""
+    lp = lpgen.workload("dense_2048x8192_f64", 0)
+    A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    xo, yo, so = lp.x0.copy(), lp.y0.copy(), lp.s0.copy()
+    with pdas.Solver(lp.m, lp.n, "tf32_ir", torch.float64) as S:
+        for k in range(2):
+            st, info = S.step(A, b, c, x, y, s, alpha=0.95)
+            assert not info["used_fp64"]
+            d = oracle.direction(lp.A64, xo, so)
+            th = oracle.theta(oracle.psi(xo, so, d["dx"], d["ds"]), 0.95)
+            xo, yo, so = oracle.step(xo, yo, so, d["dx"], d["dy"], d["ds"], th)
+            for g, o in ((x, xo), (y, yo), (s, so)):
+                assert np.linalg.norm(host(g) - o) <= 1e-9 * np.linalg.norm(o), k
+
+
 def test_full_size_bf16_tensor_core_sampled(pdas):
     """8192 x 32768, the benchmark's configuration (BF16 tensor-core form,
     2 split terms): sampled entries of M against the oracle one by one, and
