@@ -53,12 +53,22 @@ def load_peaks():
 SYRK_TRAFFIC = {("dense_8192x32768_bf16_colscaled", 3): 10.32e9 + 0.131e9}
 
 
+def form_terms(form, splits):
+    """Products per K step of the tensor-core normal matrix: BF16, the split
+    terms of D.*A (default 3); TF32, 3 (TF32 x 3, the default) or 1."""
+    if form == "bf16_ir":
+        return splits or 3
+    if form == "tf32_ir":
+        return 1 if splits == 1 else 3
+    return 1
+
+
 def syrk_roofline(form, m, n, splits, ms_per_launch, peaks, workload=None):
     """Roofline record of the normal-matrix kernel.  Algorithmic work is one
     lower-triangle product, m(m+1)/2 entries of n multiply-adds (m^2 n flops,
     FMA = 2); the tensor-core forms execute that product once per split term
     of D.*A, reported separately as executed work."""
-    terms = splits if form == "bf16_ir" else 1
+    terms = splits if form in ("bf16_ir", "tf32_ir") else 1
     flops = float(m) * (m + 1) * n
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     if form == "bf16_ir":
@@ -290,7 +300,7 @@ def run_normal_only(args):
     prof = S.profile_read()
     S.close()
     ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
-    splits = (args.splits or 3) if args.form == "bf16_ir" else 1
+    splits = form_terms(args.form, args.splits)
     peaks = load_peaks()
     roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, peaks, args.workload)
     out = dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits, ms_per_launch=ms,
@@ -333,7 +343,7 @@ def run_ours(args):
     if args.dspread is not None:
         opts["dspread_refactor"] = args.dspread
     S = P.Solver(m, n, args.form, a_dtype, stream=stream, **opts)
-    splits = (S.options.splits or 3) if args.form == "bf16_ir" else 1
+    splits = form_terms(args.form, S.options.splits)
 
     def restart():
         x.copy_(x0)

@@ -77,8 +77,10 @@ typedef struct {
                               iteration once max(D)/min(D) exceeds this (e.g. 1e8); <= 0 disables
                               the rule, leaving the switch to factor or refinement failure    (0) */
   void* stream;            /* cudaStream_t for all work; NULL = the legacy default stream      */
-  int splits;              /* PDAS_BF16_IR: number of BF16 terms of D.*A (1..3), 0 = 3;
-                              PDAS_TF32_IR takes one term (0 or 1; more: PDAS_ERR_UNSUPPORTED) */
+  int splits;              /* PDAS_BF16_IR: number of BF16 terms of D.*A (1..3), 0 = 3.
+                              PDAS_TF32_IR: 0 or 3 = TF32 x 3 (A and D.*A split into hi + lo
+                              TF32 parts, products hi hi + hi lo + lo hi: FP32-grade M); 1 = one
+                              TF32 product (both rounded to TF32); 2: PDAS_ERR_UNSUPPORTED    */
   double stall_theta;      /* step length below which a step counts as stalled          (1e-12) */
   int stall_count;         /* consecutive stalled steps that end pdas_solve                  (5) */
   double refine_be;        /* refinement also stops when the normwise backward error
@@ -95,12 +97,24 @@ typedef struct {
                               several times faster on GB300; 1 = FP64.  The right-hand side,
                               the true residuals that decide acceptance and A' dy are FP64
                               either way                                                  (0) */
+  int infeasible;          /* 0: the paper's system, which assumes a feasible interior start
+                              (A x = b, A'y + s = c) and takes A x as the right-hand side of
+                              the normal equations.  1: infeasible-start variant for any
+                              interior (x, s) > 0: the rows A dx = 0 and A'dy + ds = 0 of
+                              Eq. (3) take the residuals r_p = b - A x and r_d = c - A'y - s,
+                              so (A D A') dy = b + A D r_d, ds = r_d - A'dy, dx = D(-ds) - x;
+                              the step is theta = min(1, alpha/psi) (the iterate stays
+                              interior; psi <= 1 ends nothing), and pdas_solve stops when
+                              |rel_gap|, pres and dres (pdas_iter_info) are all below tol.
+                              The variant has no centring term: from starts far from
+                              feasibility it can stall at the boundary (PDAS_STALLED)   (0) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */
 typedef struct {
   double psi;           /* psi_k of the algorithm (Section III)                 */
-  double theta;         /* step length used: alpha/psi, or 1 when psi <= 1      */
+  double theta;         /* step length used: alpha/psi, or 1 when psi <= 1 (infeasible-start
+                           variant: min(1, alpha/psi))                          */
   double rel_gap;       /* (c'x - b'y)/(1+|c'x|) after the step                 */
   double cx, by, xs;    /* c'x, b'y, x's after the step                         */
   double dmax, dmin;    /* max and min of D = x/s before the step               */
@@ -113,6 +127,8 @@ typedef struct {
   int64_t factor_columns; /* columns of A that formed the factor (n unless dropped) */
   int normal_form;      /* arithmetic of the normal matrix: 0 tcgen05 tensor cores, 1 FP32 SIMT,
                            2 double-float (FP32 pairs, ~48-bit) on the FP32 pipes, 3 FP64        */
+  double pres, dres;    /* infeasible-start variant: ||b - A x||_inf / (1 + ||b||_inf) and
+                           ||c - A'y - s||_inf / (1 + ||c||_inf) after the step (else 0)        */
 } pdas_iter_info;
 
 /* Stages of one iteration, for pdas_profile. */

@@ -48,6 +48,17 @@ pdas_status pdas_factor_solve(pdas_handle h, const double* rhs, double* out);
 pdas_status pdas_direction(pdas_handle h, const void* A, const double* x, const double* s, double* dx, double* dy,
                            double* ds, pdas_iter_info* info);
 
+/* The Newton direction of the infeasible-start variant at (x, y, s) (handle
+ * created with opt.infeasible = 1, else PDAS_ERR_ARG): Eq. (3) with the
+ * residuals r_p = b - A x and r_d = c - A'y - s as the right-hand sides of
+ * its first two rows, reduced as in Section V: (A D A') dy = b + A D r_d,
+ * ds = r_d - A' dy, dx = D(-ds) - x, with the handle's precision form and
+ * refinement.  b (m), c (n), x, s (n), y (m): device doubles, unchanged.
+ * dx, ds: n; dy: m.  info may be NULL (psi, theta, gap fields are not set). */
+pdas_status pdas_direction_infeasible(pdas_handle h, const void* A, const double* b, const double* c,
+                                      const double* x, const double* y, const double* s, double* dx, double* dy,
+                                      double* ds, pdas_iter_info* info);
+
 /* out (m) = A v (n), FP64 accumulation of exactly widened A: the right-hand
  * side A x of the normal equations.  On a mixed-form handle with A stored as
  * FP32 / BF16 (and exact_passes off) this is the double-float pass of the

@@ -165,6 +165,20 @@ class Solver:
         self._check(st, "pdas_direction")
         return dx, dy, ds, info.as_dict()
 
+    def direction_infeasible(self, A, b, c, x, y, s):
+        """Newton direction of the infeasible-start variant at (x, y, s)
+        (handle created with infeasible=1): returns (dx, dy, ds, info dict)."""
+        dev = x.device
+        dx = torch.empty(self.n, dtype=torch.float64, device=dev)
+        ds = torch.empty(self.n, dtype=torch.float64, device=dev)
+        dy = torch.empty(self.m, dtype=torch.float64, device=dev)
+        info = N.IterInfo()
+        st = N.lib().pdas_direction_infeasible(self._h, self._A(A), self._vm(b, "b"), self._vn(c, "c"),
+                                               self._vn(x, "x"), self._vm(y, "y"), self._vn(s, "s"), _ptr(dx),
+                                               _ptr(dy), _ptr(ds), ctypes.byref(info))
+        self._check(st, "pdas_direction_infeasible")
+        return dx, dy, ds, info.as_dict()
+
     def backward(self, A, x, y, s, dL_dx, want_dA=True):
         """Sensitivities of L(x*) at the final iterate (x, y, s): returns
         (dL/dA or None, dL/db, dL/dc), FP64 (pdas_backward)."""

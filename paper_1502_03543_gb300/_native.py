@@ -36,6 +36,7 @@ class Options(ctypes.Structure):
         ("drop_tol", ctypes.c_double),
         ("drop_keep", ctypes.c_double),
         ("exact_passes", ctypes.c_int),
+        ("infeasible", ctypes.c_int),
     ]
 
 
@@ -55,6 +56,8 @@ class IterInfo(ctypes.Structure):
         ("fp64_reason", ctypes.c_int),
         ("factor_columns", ctypes.c_int64),
         ("normal_form", ctypes.c_int),
+        ("pres", ctypes.c_double),
+        ("dres", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -106,6 +109,7 @@ SIGNATURES = {
     "pdas_factor": ([_H], _I),
     "pdas_factor_solve": ([_H, _P, _P], _I),
     "pdas_direction": ([_H, _P, _P, _P, _P, _P, _P, ctypes.POINTER(IterInfo)], _I),
+    "pdas_direction_infeasible": ([_H] + [_P] * 9 + [ctypes.POINTER(IterInfo)], _I),
     "pdas_gemv": ([_H, _P, _P, _P], _I),
     "pdas_gemv_t": ([_H, _P, _P, _P], _I),
     "pdas_gemv_t_noalloc": ([_I64, _I64, _I, _P, _P, _P, _P], _I),

@@ -33,6 +33,7 @@ struct pdas_ctx {
   // FP64 vectors
   double *D = nullptr, *r = nullptr, *dy = nullptr, *dx = nullptr, *ds = nullptr, *w = nullptr, *u = nullptr;
   double *z = nullptr, *rho = nullptr, *delta = nullptr, *kp = nullptr, *kq = nullptr, *kz = nullptr;
+  double* rd = nullptr;       // infeasible-start variant: dual residual c - A'y - s (n)
   double* part = nullptr;     // reduction partials (kPartMax)
   double* gt_part = nullptr;  // gemv_t partials, gt_chunks x n
   int gt_chunks = 1;
@@ -235,7 +236,7 @@ pdas_status gemv(pdas_ctx* h, const void* A, const double* v, const double* base
 
 // w = A' u, then the finish mode (see launch_gemv_t_finish).
 pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const double* x, double* o0, double* o1,
-                   double* o2, bool df = false) {
+                   double* o2, bool df = false, const double* rd = nullptr) {
   if (df) {
     KL(launch_split_pairs(h->st, h->m, u, h->pairs), 1);
     if (h->opt.a_dtype == PDAS_A_F32)
@@ -244,7 +245,7 @@ pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const 
     else
       KL(launch_gemv_t_df<__nv_bfloat16>(h->st, h->m, h->n, (const __nv_bfloat16*)A, h->pairs, h->gt_part,
                                          h->gt_chunks, h->gt_rows), 1);
-    KL(launch_gemv_t_finish(h->st, h->n, h->gt_chunks, h->gt_part, mode, x, h->D, o0, o1, o2, h->sc), 1);
+    KL(launch_gemv_t_finish(h->st, h->n, h->gt_chunks, h->gt_part, mode, x, h->D, o0, o1, o2, h->sc, rd), 1);
     return PDAS_OK;
   }
   pdas_status s = with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
@@ -253,7 +254,7 @@ pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const 
     return PDAS_OK;
   });
   if (s != PDAS_OK) return s;
-  KL(launch_gemv_t_finish(h->st, h->n, h->gt_chunks, h->gt_part, mode, x, h->D, o0, o1, o2, h->sc), 1);
+  KL(launch_gemv_t_finish(h->st, h->n, h->gt_chunks, h->gt_part, mode, x, h->D, o0, o1, o2, h->sc, rd), 1);
   return PDAS_OK;
 }
 
@@ -493,13 +494,30 @@ pdas_status refine(pdas_ctx* h, const void* A, int* ok) {
   return PDAS_OK;
 }
 
-// One Newton direction at (x, s): fills h->D, h->r, h->dy, h->dx, h->ds.
-pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double* s) {
+// The right-hand side of the normal equations at (x, s): D = x/s, then
+// r = A x (a2; the paper's system, which assumes A x = b and A'y + s = c),
+// or, for the infeasible-start variant (iv != null: y, b, c), the dual
+// residual rd = c - A'y - s and r = b + A D rd.
+struct Infeasible {
+  const double *y, *b, *c;
+};
+pdas_status normal_rhs(pdas_ctx* h, const void* A, const double* x, const double* s, const Infeasible* iv) {
+  pdas_status st;
+  KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
+  if (!iv) return gemv(h, A, x, nullptr, h->r, 0);  // r = A x
+  if ((st = gemv_t(h, A, iv->y, 0, nullptr, h->w, nullptr, nullptr)) != PDAS_OK) return st;  // w = A'y
+  KL(launch_dual_residual(h->st, h->n, iv->c, s, h->w, h->D, h->rd, h->u, h->sc), 1);     // rd, u = -D rd
+  return gemv(h, A, h->u, iv->b, h->r, 0);                                                // r = b - A u
+}
+
+// One Newton direction at (x, s): fills h->D, h->r, h->dy, h->dx, h->ds (and
+// h->rd for the infeasible-start variant, iv != null).
+pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double* s, const Infeasible* iv = nullptr) {
   pdas_status st;
   if ((st = reset_status(h)) != PDAS_OK) return st;
+  const double* rd = iv ? h->rd : nullptr;
   STAGE(h, PDAS_STAGE_RHS);
-  KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
-  if ((st = gemv(h, A, x, nullptr, h->r, 0)) != PDAS_OK) return st;  // r = A x (a2)
+  if ((st = normal_rhs(h, A, x, s, iv)) != PDAS_OK) return st;
   STAGE_END(h);
   if (is_mixed(h) && !h->refactored && h->opt.dspread_refactor > 0) {
     if ((st = read_scalars(h)) != PDAS_OK) return st;
@@ -532,7 +550,7 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
       h->last_sweeps = 0;
       h->last_resid = 0.0;
       STAGE(h, PDAS_STAGE_DIR);
-      if ((st = gemv_t(h, A, h->dy, 1, x, h->dx, h->ds, nullptr)) != PDAS_OK) return st;  // a7
+      if ((st = gemv_t(h, A, h->dy, 1, x, h->dx, h->ds, nullptr, false, rd)) != PDAS_OK) return st;  // a7
       STAGE_END(h);
       return PDAS_OK;
     }
@@ -549,8 +567,7 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
       if (!h->refactored) h->switch_reason = 2;
       h->refactored = 1;
       if ((st = reset_status(h)) != PDAS_OK) return st;
-      KL(launch_scaling(h->st, h->n, x, s, h->D, h->part, h->tickets, h->sc), 1);
-      if ((st = gemv(h, A, x, nullptr, h->r, 0)) != PDAS_OK) return st;
+      if ((st = normal_rhs(h, A, x, s, iv)) != PDAS_OK) return st;
       continue;
     }
     if (st != PDAS_OK) return st;
@@ -561,7 +578,7 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
       // w = A' dy of the accepted dy is in h->w: dx = D w - x, ds = -w.  (An
       // FP64 factor is the last tier: its refined direction is used as is.)
       STAGE(h, PDAS_STAGE_DIR);
-      KL(launch_gemv_t_finish(h->st, h->n, 0, nullptr, 3, x, h->D, h->dx, h->ds, h->w, h->sc), 1);
+      KL(launch_gemv_t_finish(h->st, h->n, 0, nullptr, 3, x, h->D, h->dx, h->ds, h->w, h->sc, rd), 1);
       STAGE_END(h);
       return PDAS_OK;
     }
@@ -595,6 +612,10 @@ void fill_info(pdas_ctx* h, pdas_iter_info* info, bool stepped) {
     info->cx = s.cx;
     info->by = s.by;
     info->xs = s.xs;
+    if (h->opt.infeasible) {
+      info->pres = s.pres;
+      info->dres = s.dres;
+    }
   }
 }
 
@@ -620,6 +641,7 @@ void pdas_default_options(pdas_options* opt) {
   opt->splits = 0;
   opt->stall_theta = 1e-12;
   opt->stall_count = 5;
+  opt->infeasible = 0;
 }
 
 const char* pdas_status_str(pdas_status st) {
@@ -652,12 +674,12 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (opt.a_dtype < PDAS_A_F64 || opt.a_dtype > PDAS_A_BF16) return PDAS_ERR_ARG;
   if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) ||
       !(opt.drop_tol >= 0) || !(opt.drop_keep >= 1.0) || opt.splits < 0 || (opt.exact_passes & ~1) ||
-      opt.splits > 3 ||
+      opt.splits > 3 || (opt.infeasible & ~1) ||
       opt.stall_count < 1 || !(opt.stall_theta >= 0))
     return PDAS_ERR_ARG;
   if (opt.form == PDAS_BF16_IR && opt.a_dtype != PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
-  // TF32 form: one TF32 term of D.*A (A itself is rounded to TF32), FP64 or FP32 storage
-  if (opt.form == PDAS_TF32_IR && (opt.a_dtype == PDAS_A_BF16 || opt.splits > 1)) return PDAS_ERR_UNSUPPORTED;
+  // TF32 form: TF32 x 3 (splits 0 or 3) or one TF32 product (splits 1); FP64 or FP32 storage
+  if (opt.form == PDAS_TF32_IR && (opt.a_dtype == PDAS_A_BF16 || opt.splits == 2)) return PDAS_ERR_UNSUPPORTED;
   pdas_ctx* h = new (std::nothrow) pdas_ctx();
   if (!h) return PDAS_ERR_CUDA;
   h->m = m;
@@ -691,6 +713,7 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   al((void**)&h->kp, sizeof(double) * m);
   al((void**)&h->kq, sizeof(double) * m);
   al((void**)&h->kz, sizeof(double) * m);
+  if (opt.infeasible) al((void**)&h->rd, sizeof(double) * n);
   al((void**)&h->part, sizeof(double) * kPartMax * 4);
   al((void**)&h->gt_part, sizeof(double) * n * h->gt_chunks);
   al((void**)&h->tickets, sizeof(unsigned) * T_COUNT);
@@ -747,7 +770,7 @@ void pdas_destroy(pdas_handle h) {
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   double* vecs[] = {h->D, h->r, h->dy, h->dx, h->ds, h->w, h->u, h->z, h->rho, h->delta, h->kp, h->kq, h->kz,
-                    h->part, h->gt_part, h->M64};
+                    h->part, h->gt_part, h->M64, h->rd};
   for (double* p : vecs)
     if (p) cudaFree(p);
   if (h->M32) cudaFree(h->M32);
@@ -820,23 +843,50 @@ pdas_status pdas_direction(pdas_handle h, const void* A, const double* x, const 
   return st;
 }
 
+pdas_status pdas_direction_infeasible(pdas_handle h, const void* A, const double* b, const double* c,
+                                      const double* x, const double* y, const double* s, double* dx, double* dy,
+                                      double* ds, pdas_iter_info* info) {
+  if (!h || check_vec_args(A, x, s) != PDAS_OK || !b || !c || !y || !dx || !dy || !ds) return PDAS_ERR_ARG;
+  if (!h->opt.infeasible) return PDAS_ERR_ARG;
+  h->err_index = -1;
+  const Infeasible iv{y, b, c};
+  pdas_status st = direction(h, A, x, s, &iv);
+  if (st != PDAS_OK) return st;
+  CK(cudaMemcpyAsync(dx, h->dx, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(ds, h->ds, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(dy, h->dy, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
+  if ((st = read_scalars(h)) != PDAS_OK) return st;
+  st = device_status(h);
+  fill_info(h, info, false);
+  return st;
+}
+
 pdas_status pdas_step(pdas_handle h, const void* A, const double* b, const double* c, double* x, double* y,
                       double* s, double alpha, pdas_iter_info* info) {
   if (!h || check_vec_args(A, x, s) != PDAS_OK || !b || !c || !y) return PDAS_ERR_ARG;
   if (!(alpha > 0.0 && alpha < 1.0)) return PDAS_ERR_ARG;
   h->err_index = -1;
-  pdas_status st = direction(h, A, x, s);
+  const bool variant = h->opt.infeasible != 0;
+  const Infeasible iv{y, b, c};
+  pdas_status st = direction(h, A, x, s, variant ? &iv : nullptr);
   if (st != PDAS_OK) return st;
   STAGE(h, PDAS_STAGE_STEP);
-  KL(launch_psi(h->st, h->n, x, s, h->dx, h->ds, alpha, h->part, h->tickets, h->sc), 1);
+  KL(launch_psi(h->st, h->n, x, s, h->dx, h->ds, alpha, h->part, h->tickets, h->sc, variant), 1);
   KL(launch_step(h->st, h->m, h->n, b, c, x, y, s, h->dx, h->dy, h->ds, h->part, h->tickets, h->sc), 1);
+  if (variant) {  // residuals of the new iterate: b - A x and c - A'y - s
+    if ((st = gemv(h, A, x, b, h->rho, -1)) != PDAS_OK) return st;
+    if ((st = gemv_t(h, A, y, 0, nullptr, h->w, nullptr, nullptr)) != PDAS_OK) return st;
+    KL(launch_residual_norms(h->st, h->m, h->n, b, h->rho, c, h->w, s, h->part, h->tickets, h->sc), 1);
+  }
   STAGE_END(h);
   if ((st = read_scalars(h)) != PDAS_OK) return st;
   st = device_status(h);
   fill_info(h, info, st == PDAS_OK);
   if (st != PDAS_OK) return st;
-  h->last_rel_gap = h->sc_host->rel_gap;
-  return h->sc_host->psi <= 1.0 ? PDAS_OPTIMAL_EXACT : PDAS_OK;
+  h->last_rel_gap = variant ? fmax(fabs(h->sc_host->rel_gap), fmax(h->sc_host->pres, h->sc_host->dres))
+                            : h->sc_host->rel_gap;
+  // a full step ends the paper's method at an optimum; the variant's never does
+  return !variant && h->sc_host->psi <= 1.0 ? PDAS_OPTIMAL_EXACT : PDAS_OK;
 }
 
 pdas_status pdas_solve(pdas_handle h, const void* A, const double* b, const double* c, double* x, double* y,
@@ -869,7 +919,8 @@ pdas_status pdas_solve(pdas_handle h, const void* A, const double* b, const doub
       ++k;
       break;
     }
-    if (gap < tol) {
+    const bool converged = h->opt.infeasible ? fabs(gap) < tol && info.pres < tol && info.dres < tol : gap < tol;
+    if (converged) {
       result = PDAS_OPTIMAL;
       ++k;
       break;

@@ -34,6 +34,7 @@ struct Scalars {
   double dot_a, dot_b; // dot products of the refinement Krylov steps
   double mnorm;        // max_p M_pp of the formed normal matrix (a lower bound on ||M||)
   double dynorm;       // ||dy||_inf
+  double pres, dres;   // infeasible-start variant: relative primal and dual residuals
   int status;          // 0, or a pdas_status error detected on the device
   int fail_index;      // failing pivot for PDAS_ERR_NOT_SPD
   int bad_iterate;     // nonzero if some x_j <= 0 or s_j <= 0 (or not finite)
@@ -42,7 +43,7 @@ struct Scalars {
 
 // Counters for the "last block finishes the reduction" pattern and the
 // triangular-solve tickets.
-enum Ticket { T_SCALING = 0, T_PSI, T_STEP, T_NORM, T_NORM2, T_DOT, T_TRSV, T_CHOL, T_COUNT = 8 };
+enum Ticket { T_SCALING = 0, T_PSI, T_STEP, T_NORM, T_NORM2, T_DOT, T_TRSV, T_CHOL, T_RES, T_COUNT = 9 };
 
 // ---- exact widening of the stored A ---------------------------------------
 __device__ __forceinline__ double widen(double v) { return v; }
@@ -94,13 +95,25 @@ cudaError_t launch_gemv_t_df(cudaStream_t st, int64_t m, int64_t n, const T* A, 
 //   1: direction: out0 = dx = D w - x, out1 = ds = -w, out2 = w (may be null)
 //   2: scaled:    out0 = D w, out2 = w (may be null)
 //   3: direction from a w already in out2 (chunks, part unused)
+// With rd (modes 1 and 3, the infeasible-start variant) ds = rd - w instead of -w.
 cudaError_t launch_gemv_t_finish(cudaStream_t st, int64_t n, int chunks, const double* part, int mode,
                                  const double* x, const double* D, double* out0, double* out1, double* out2,
-                                 const Scalars* sc);
+                                 const Scalars* sc, const double* rd = nullptr);
+// Infeasible-start variant: rd = (c - w) - s (w = A'y) and nu = -(D rd), so
+// that b - A nu = b + A D rd is the right-hand side of the normal equations.
+cudaError_t launch_dual_residual(cudaStream_t st, int64_t n, const double* c, const double* s, const double* w,
+                                 const double* D, double* rd, double* nu, const Scalars* sc);
+// sc->pres = max|rp| / (1 + max|b|) with rp = b - A x (m), sc->dres =
+// max|(c - w) - s| / (1 + max|c|) with w = A'y (n).
+cudaError_t launch_residual_norms(cudaStream_t st, int64_t m, int64_t n, const double* b, const double* rp,
+                                  const double* c, const double* w, const double* s, double* part,
+                                  unsigned* tickets, Scalars* sc);
 cudaError_t launch_scaling(cudaStream_t st, int64_t n, const double* x, const double* s, double* D, double* part,
                            unsigned* tickets, Scalars* sc);
+// capped: theta = min(1, alpha/psi) (infeasible-start variant) instead of 1 when psi <= 1.
 cudaError_t launch_psi(cudaStream_t st, int64_t n, const double* x, const double* s, const double* dx,
-                       const double* ds, double alpha, double* part, unsigned* tickets, Scalars* sc);
+                       const double* ds, double alpha, double* part, unsigned* tickets, Scalars* sc,
+                       bool capped = false);
 cudaError_t launch_step(cudaStream_t st, int64_t m, int64_t n, const double* b, const double* c, double* x,
                         double* y, double* s, const double* dx, const double* dy, const double* ds, double* part,
                         unsigned* tickets, Scalars* sc);

@@ -5,8 +5,12 @@
 // call to TF32 (FP32 containers, 10 stored mantissa bits, round to nearest
 // even) and M = A_tf32 B_tf32' takes one tcgen05.mma.kind::tf32 term; each
 // operand carries 2^-11 relative error, which the FP64 refinement removes
-// from the direction.  The rest of this header describes the BF16 form; the
-// TF32 kernel is the same pipeline with 32 FP32 elements per 128-byte row.
+// from the direction.  With three terms (TF32 x 3) both operands are split,
+// A = A_0 + A_1 and B = B_0 + B_1 (hi and lo TF32 parts, ~2^-22 relative
+// left over), and M ~= A_0 B_0' + A_0 B_1' + A_1 B_0': every product is exact
+// in FP32, so M is FP32-grade.  The rest of this header describes the BF16
+// form; the TF32 kernel is the same pipeline with 32 FP32 elements per
+// 128-byte row.
 //
 // D is folded into one operand: B = D.*A (row q: B_qj = A_qj D_j) is split
 // into `splits` BF16 terms B = B_0 + B_1 (+ B_2), each carrying the next 8
@@ -59,9 +63,9 @@ constexpr uint32_t TMEM_COLS = 256;           // two chunk buffers of BN columns
 constexpr int NUM_THREADS = 192;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)RING_BYTES + 512;
 
-template <int S>
+template <int TILES>  // operand tiles per stage
 struct Ring {
-  static constexpr uint32_t STAGE_BYTES = TILE_BYTES * (1 + S);
+  static constexpr uint32_t STAGE_BYTES = TILE_BYTES * TILES;
   static constexpr int STAGES = (int)(RING_BYTES / STAGE_BYTES);
 };
 
@@ -69,13 +73,19 @@ using namespace tc;
 constexpr uint32_t kIdescBf16 = idesc_bf16(BM, BN);
 constexpr uint32_t kIdescTf32 = idesc_tf32(BM, BN);
 
-template <int S, bool TF32 = false>
+// S terms B_t of D.*A.  ALO (TF32 x 3): A = A_0 + A_1 in two planes as well,
+// S = 2, the stage holds A_0 | B_0 | B_1 | A_1 (A_1 through the tmB2 map) and
+// the products are A_0 B_0' + A_0 B_1' + A_1 B_0' (A_1 B_1' is below the
+// rounding of the rest).
+template <int S, bool TF32 = false, bool ALO = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
               const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
               const int2* __restrict__ tiles, int nk, int64_t m, int64_t ldm, float* __restrict__ M, Scalars* sc) {
-  constexpr uint32_t STAGE_BYTES = Ring<S>::STAGE_BYTES;
-  constexpr int STAGES = Ring<S>::STAGES;
+  static_assert(!ALO || S == 2, "the split-A form pairs two planes of A with two of D.*A");
+  constexpr uint32_t STAGE_BYTES = Ring<1 + S + (ALO ? 1 : 0)>::STAGE_BYTES;
+  constexpr int STAGES = Ring<1 + S + (ALO ? 1 : 0)>::STAGES;
+  constexpr int NP = ALO ? 3 : S;  // MMA products per K step
   constexpr int EK = TF32 ? BK_TF32 : BK;  // K elements per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -131,6 +141,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tma_load_2d(dst + TILE_BYTES, &tmB0, kb * EK, q0, full(s));
         if (S > 1) tma_load_2d(dst + 2 * TILE_BYTES, &tmB1, kb * EK, q0, full(s));
         if (S > 2) tma_load_2d(dst + 3 * TILE_BYTES, &tmB2, kb * EK, q0, full(s));
+        if (ALO) tma_load_2d(dst + (1 + S) * TILE_BYTES, &tmB2, kb * EK, p0, full(s));  // A_1
         issued = kb + 1;
       }
       if (*abort_flag) {  // let every issued copy land before the CTA can exit
@@ -156,10 +167,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * BN);
-        const uint64_t ad = sdesc_sw128(sbase + s * STAGE_BYTES);
 #pragma unroll
-        for (int t = 0; t < S; ++t) {
-          const uint64_t bd = sdesc_sw128(sbase + s * STAGE_BYTES + (1 + t) * TILE_BYTES);
+        for (int t = 0; t < NP; ++t) {
+          const int ia = (ALO && t == 2) ? 1 + S : 0;      // tile of A_0 or A_1
+          const int ib = 1 + ((ALO && t == 2) ? 0 : t);   // tile of B_t
+          const uint64_t ad = sdesc_sw128(sbase + s * STAGE_BYTES + ia * TILE_BYTES);
+          const uint64_t bd = sdesc_sw128(sbase + s * STAGE_BYTES + ib * TILE_BYTES);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {  // advance 32 bytes (16 BF16 or 8 TF32) along K per MMA
             const uint32_t accum = (chunk_start && t == 0 && k == 0) ? 0u : 1u;
@@ -297,16 +310,25 @@ __device__ __forceinline__ float round_tf32(float f) {
 }
 
 // TF32 operands: opa = tf32(A), opb = tf32(fl32(A_pj D_j)) with the product in
-// FP64 (exact for FP32 A), both with row stride kpad.
+// FP64 (exact for FP32 A), both with row stride kpad.  split: a second plane
+// of each (at plane stride m kpad) takes the rest, tf32(fl32(v) - tf32(fl32(v)))
+// (the difference is exact in FP32).
 template <typename T>
 __global__ void k_fold_tf32(int64_t m, int64_t n, int64_t kpad, const T* __restrict__ A,
-                            const double* __restrict__ D, float* __restrict__ opa, float* __restrict__ opb) {
-  const int64_t total = m * n;
+                            const double* __restrict__ D, float* __restrict__ opa, float* __restrict__ opb,
+                            int split) {
+  const int64_t total = m * n, plane = m * kpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = e / n, j = e - p * n;
+    const int64_t p = e / n, j = e - p * n, o = p * kpad + j;
     const double a = (double)A[e];
-    opa[p * kpad + j] = round_tf32((float)a);
-    opb[p * kpad + j] = round_tf32((float)(a * D[j]));
+    const float a32 = (float)a, b32 = (float)(a * D[j]);
+    const float a0 = round_tf32(a32), b0 = round_tf32(b32);
+    opa[o] = a0;
+    opb[o] = b0;
+    if (split) {
+      opa[plane + o] = round_tf32(a32 - a0);
+      opb[plane + o] = round_tf32(b32 - b0);
+    }
   }
 }
 
@@ -357,13 +379,13 @@ cudaError_t encode_bf16(TcHost* hs, CUtensorMap* map, const void* base, int64_t 
 
 cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int splits, int64_t m, int64_t n) {
   const bool tf32 = form == PDAS_TF32_IR;
-  if (tf32 ? (a_dtype != PDAS_A_F64 && a_dtype != PDAS_A_F32) || splits > 1
+  if (tf32 ? (a_dtype != PDAS_A_F64 && a_dtype != PDAS_A_F32) || splits == 2 || splits > 3
            : (form != PDAS_BF16_IR || a_dtype != PDAS_A_BF16))
     return cudaErrorNotSupported;
   if (m > ((int64_t)1 << 30) / BM || n > ((int64_t)1 << 31) - BK) return cudaErrorNotSupported;
   w->form = form;
   w->a_dtype = a_dtype;
-  w->splits = tf32 ? 1 : splits > 0 ? splits : 3;
+  w->splits = tf32 ? (splits == 1 ? 1 : 3) : splits > 0 ? splits : 3;
   w->m = m;
   w->n = n;
   w->kpad = (n + BK - 1) / BK * BK;
@@ -374,8 +396,12 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   cudaError_t e = get_encoder(&hs->encode);
   if (e != cudaSuccess) return e;
   const size_t esz = tf32 ? sizeof(float) : sizeof(__nv_bfloat16);
-  e = cudaMalloc(&w->opb, esz * (size_t)w->splits * m * w->kpad);
-  if (e == cudaSuccess && (tf32 || n % 8 != 0)) e = cudaMalloc(&w->opa, esz * (size_t)m * w->kpad);
+  // planes: BF16, splits terms of D.*A (and a padded copy of A if its rows are
+  // not 16-byte aligned); TF32, one plane of each operand, or two (TF32 x 3)
+  const int bplanes = tf32 ? (w->splits == 3 ? 2 : 1) : w->splits;
+  const int aplanes = tf32 ? bplanes : 1;
+  e = cudaMalloc(&w->opb, esz * (size_t)bplanes * m * w->kpad);
+  if (e == cudaSuccess && (tf32 || n % 8 != 0)) e = cudaMalloc(&w->opa, esz * (size_t)aplanes * m * w->kpad);
   if (e == cudaSuccess) e = cudaMalloc(&hs->D32, sizeof(float) * (size_t)((n + 7) / 8 * 8));
   // Lower-triangle tile list ((I, J) with some row p >= some column q),
   // ordered by G x G super-tiles with G ~ sqrt(#SMs): the CTAs resident at
@@ -401,8 +427,11 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   if (e == cudaSuccess) e = cudaMalloc(&hs->tiles, sizeof(int2) * tl.size());
   if (e == cudaSuccess) e = cudaMemcpy(hs->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
   for (int t = 0; e == cudaSuccess && t < 3; ++t) {
-    const int tt = t < w->splits ? t : 0;  // unused maps alias term 0
-    e = encode_bf16(hs, &hs->mapB[t], (const uint8_t*)w->opb + esz * tt * m * w->kpad, m, n, w->kpad, BN, tf32);
+    const int tt = t < bplanes ? t : 0;  // unused maps alias term 0
+    if (tf32 && bplanes == 2 && t == 2)  // TF32 x 3: the third map carries A_1
+      e = encode_bf16(hs, &hs->mapB[t], (const uint8_t*)w->opa + esz * m * w->kpad, m, n, w->kpad, BM, tf32);
+    else
+      e = encode_bf16(hs, &hs->mapB[t], (const uint8_t*)w->opb + esz * tt * m * w->kpad, m, n, w->kpad, BN, tf32);
   }
   if (e == cudaSuccess && w->opa) e = encode_bf16(hs, &hs->mapA_copy, w->opa, m, n, w->kpad, BM, tf32);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
@@ -410,6 +439,9 @@ cudaError_t tc_workspace_create(TcWorkspace* w, int form, int a_dtype, int split
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_syrk_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_syrk_tc<2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
   return e;
 }
 
@@ -433,12 +465,13 @@ cudaError_t tc_prepare(cudaStream_t st, TcWorkspace* w, const void* A, const dou
   if (w->form == PDAS_TF32_IR) {
     const int64_t work = m * n;
     const unsigned grid = (unsigned)((work + 255) / 256 < 4736 ? (work + 255) / 256 : 4736);
+    const int split = w->splits == 3 ? 1 : 0;
     if (w->a_dtype == PDAS_A_F64)
       k_fold_tf32<double><<<grid, 256, 0, st>>>(m, n, w->kpad, static_cast<const double*>(A), D,
-                                                static_cast<float*>(w->opa), static_cast<float*>(w->opb));
+                                                static_cast<float*>(w->opa), static_cast<float*>(w->opb), split);
     else
       k_fold_tf32<float><<<grid, 256, 0, st>>>(m, n, w->kpad, static_cast<const float*>(A), D,
-                                               static_cast<float*>(w->opa), static_cast<float*>(w->opb));
+                                               static_cast<float*>(w->opa), static_cast<float*>(w->opb), split);
     *launches = 1;
     return cudaGetLastError();
   }
@@ -463,8 +496,12 @@ cudaError_t tc_syrk(cudaStream_t st, TcWorkspace* w, const void* A, float* M32, 
   const dim3 grid((unsigned)hs->ntiles);
   if (w->form == PDAS_TF32_IR) {
     const int nk = (int)((n + BK_TF32 - 1) / BK_TF32);
-    k_syrk_tc<1, true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapA_copy, hs->mapB[0], hs->mapB[1], hs->mapB[2],
-                                                              hs->tiles, nk, m, ldm, M32, scw);
+    if (w->splits == 3)
+      k_syrk_tc<2, true, true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapA_copy, hs->mapB[0], hs->mapB[1],
+                                                                      hs->mapB[2], hs->tiles, nk, m, ldm, M32, scw);
+    else
+      k_syrk_tc<1, true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapA_copy, hs->mapB[0], hs->mapB[1],
+                                                                hs->mapB[2], hs->tiles, nk, m, ldm, M32, scw);
     *launches = 1;
     return cudaGetLastError();
   }

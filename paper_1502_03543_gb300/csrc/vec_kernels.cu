@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(int64_t m, int64_t n, 
 __global__ void __launch_bounds__(kThreads) k_gemv_t_finish(int64_t n, int chunks, const double* __restrict__ part,
                                                             int mode, const double* __restrict__ x,
                                                             const double* __restrict__ D, double* out0,
-                                                            double* out1, double* out2, const Scalars* sc) {
+                                                            double* out1, double* out2, const Scalars* sc,
+                                                            const double* __restrict__ rd) {
   if (failed(sc)) return;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     double w = 0.0;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_finish(int64_t n, int chunk
     if (mode == 0) {
       out0[j] = w;
     } else if (mode == 1 || mode == 3) {
-      const double ds = -w;
+      const double ds = rd ? rd[j] - w : -w;
       out0[j] = D[j] * (-ds) - x[j];  // dx = D(-ds) - x
       out1[j] = ds;
       if (out2 && mode == 1) out2[j] = w;
@@ -213,12 +214,66 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_finish(int64_t n, int chunk
   }
 }
 
+// Infeasible-start variant: the dual residual rd = c - A'y - s (w = A'y) of
+// the second row of Eq. (3), and nu = -(D rd) for the right-hand side
+// b - A nu = b + A D rd of the normal equations.
+__global__ void k_dual_residual(int64_t n, const double* __restrict__ c, const double* __restrict__ s,
+                                const double* __restrict__ w, const double* __restrict__ D, double* __restrict__ rd,
+                                double* __restrict__ nu, const Scalars* sc) {
+  if (failed(sc)) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double r = (c[j] - w[j]) - s[j];
+    rd[j] = r;
+    nu[j] = -(D[j] * r);
+  }
+}
+
+// Relative residuals of the iterate: max|rp| / (1 + max|b|) and
+// max|(c - w) - s| / (1 + max|c|), four maxima per block, combined in block
+// order by the last block.  NaN propagates as Inf.
+__global__ void __launch_bounds__(kThreads) k_residual_norms(int64_t m, int64_t n, const double* __restrict__ b,
+                                                             const double* __restrict__ rp,
+                                                             const double* __restrict__ c,
+                                                             const double* __restrict__ w,
+                                                             const double* __restrict__ s, double* part,
+                                                             unsigned* tickets, Scalars* sc) {
+  __shared__ double sm[32];
+  if (failed(sc)) return;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};  // |rp|, |b|, |rd|, |c|
+  auto upd = [](double& acc, double a) { acc = (a == a) ? fmax(acc, fabs(a)) : INFINITY; };
+  const int64_t len = n > m ? n : m;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    if (j < m) {
+      upd(v[0], rp[j]);
+      upd(v[1], b[j]);
+    }
+    if (j < n) {
+      upd(v[2], (c[j] - w[j]) - s[j]);
+      upd(v[3], c[j]);
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    const double r = block_reduce<1>(v[k], sm);
+    if (threadIdx.x == 0) part[4 * blockIdx.x + k] = r;
+  }
+  if (!last_block(tickets + T_RES)) return;
+  if (threadIdx.x == 0) {
+    double g[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < (int)gridDim.x; ++i)
+      for (int k = 0; k < 4; ++k) g[k] = fmax(g[k], __ldcg(part + 4 * i + k));
+    sc->pres = g[0] / (1.0 + g[1]);
+    sc->dres = g[2] / (1.0 + g[3]);
+    tickets[T_RES] = 0;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// a8: psi = max_j max(-dx_j/x_j, -ds_j/s_j); theta = alpha/psi, or 1 if psi <= 1.
+// a8: psi = max_j max(-dx_j/x_j, -ds_j/s_j); theta = alpha/psi, or 1 if psi <= 1
+// (capped, the infeasible-start variant: min(1, alpha/psi)).
 __global__ void __launch_bounds__(kThreads) k_psi(int64_t n, const double* __restrict__ x,
                                                   const double* __restrict__ s, const double* __restrict__ dx,
                                                   const double* __restrict__ ds, double alpha, double* part,
-                                                  unsigned* tickets, Scalars* sc) {
+                                                  unsigned* tickets, Scalars* sc, int capped) {
   __shared__ double sm[32];
   if (failed(sc)) return;
   double mx = -INFINITY;
@@ -244,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_psi(int64_t n, const double* __res
   g = block_reduce<1>(g, sm);
   if (threadIdx.x == 0) {
     sc->psi = g;
-    sc->theta = g <= 1.0 ? 1.0 : alpha / g;
+    sc->theta = capped ? (g <= alpha ? 1.0 : alpha / g) : (g <= 1.0 ? 1.0 : alpha / g);
     if (gbad) sc->status = PDAS_ERR_NONFINITE;
     tickets[T_PSI] = 0;
   }
@@ -512,8 +567,21 @@ cudaError_t launch_gemv_t(cudaStream_t st, int64_t m, int64_t n, const T* A, con
 
 cudaError_t launch_gemv_t_finish(cudaStream_t st, int64_t n, int chunks, const double* part, int mode,
                                  const double* x, const double* D, double* out0, double* out1, double* out2,
-                                 const Scalars* sc) {
-  k_gemv_t_finish<<<grid_for(n), kThreads, 0, st>>>(n, chunks, part, mode, x, D, out0, out1, out2, sc);
+                                 const Scalars* sc, const double* rd) {
+  k_gemv_t_finish<<<grid_for(n), kThreads, 0, st>>>(n, chunks, part, mode, x, D, out0, out1, out2, sc, rd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dual_residual(cudaStream_t st, int64_t n, const double* c, const double* s, const double* w,
+                                 const double* D, double* rd, double* nu, const Scalars* sc) {
+  k_dual_residual<<<grid_for(n), kThreads, 0, st>>>(n, c, s, w, D, rd, nu, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norms(cudaStream_t st, int64_t m, int64_t n, const double* b, const double* rp,
+                                  const double* c, const double* w, const double* s, double* part,
+                                  unsigned* tickets, Scalars* sc) {
+  k_residual_norms<<<grid_for(n > m ? n : m, 4), kThreads, 0, st>>>(m, n, b, rp, c, w, s, part, tickets, sc);
   return cudaGetLastError();
 }
 
@@ -525,8 +593,9 @@ cudaError_t launch_scaling(cudaStream_t st, int64_t n, const double* x, const do
 }
 
 cudaError_t launch_psi(cudaStream_t st, int64_t n, const double* x, const double* s, const double* dx,
-                       const double* ds, double alpha, double* part, unsigned* tickets, Scalars* sc) {
-  k_psi<<<grid_for(n, 4), kThreads, 0, st>>>(n, x, s, dx, ds, alpha, part, tickets, sc);
+                       const double* ds, double alpha, double* part, unsigned* tickets, Scalars* sc,
+                       bool capped) {
+  k_psi<<<grid_for(n, 4), kThreads, 0, st>>>(n, x, s, dx, ds, alpha, part, tickets, sc, capped ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ def test_host_side_validation_without_gpu(lib):
     L.pdas_default_options(ctypes.byref(o))
     assert o.max_iter == 500 and o.refine_tol == 1e-14 and o.dspread_refactor == 0.0 and o.form == N.FP64
     assert o.refine_be == 1e-14 and o.drop_tol == 1e-10 and o.drop_keep == 1.25 and o.refine_max == 40
-    assert o.exact_passes == 0
+    assert o.exact_passes == 0 and o.infeasible == 0
     h = ctypes.c_void_p()
     # m < n and m >= 1 (Section I)
     assert L.pdas_create(10, 10, ctypes.byref(o), ctypes.byref(h)) == N.ERR_ARG
@@ -68,13 +68,16 @@ def test_host_side_validation_without_gpu(lib):
     bad.exact_passes = 2
     assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_ARG
     bad = N.Options.from_buffer_copy(o)
+    bad.infeasible = 2
+    assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_ARG
+    bad = N.Options.from_buffer_copy(o)
     bad.refine_tol = -1.0
     assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_ARG
     # BF16 operands need BF16 storage
     bad = N.Options.from_buffer_copy(o)
     bad.form, bad.a_dtype = N.BF16_IR, N.A_F64
     assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_UNSUPPORTED
-    # TF32 operands: FP64 or FP32 storage, one term of D.*A
+    # TF32 operands: FP64 or FP32 storage, one product or TF32 x 3
     bad = N.Options.from_buffer_copy(o)
     bad.form, bad.a_dtype = N.TF32_IR, N.A_BF16
     assert L.pdas_create(3, 5, ctypes.byref(bad), ctypes.byref(h)) == N.ERR_UNSUPPORTED

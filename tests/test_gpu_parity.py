@@ -445,34 +445,38 @@ def test_bf16_ir_solve_512x2048(pdas, dspread):  # with and without the max(D)/m
     assert np.linalg.norm(lp.A64.T @ yh + sh - lp.c) <= 1e-12 * np.linalg.norm(lp.c)
 
 
-def tf32_bound(A64, D, n):
-    """|M_tf32 - M| elementwise.  A and D.*A are each rounded to FP32 and then
-    to TF32 (u = 2^-11, round to nearest even), so a product carries at most
-    (1 + 2^-11 + 2^-24)^2 - 1 < 2^-10 + 2^-20 relative error; each 64-long
-    chunk takes 8 tensor-core accumulation steps (u = 2^-23, truncating) and
-    the chunk sums are added in round-to-nearest FP32 (u = 2^-24)."""
-    rep = 2.0 ** -10 + 2.0 ** -20
-    acc = gamma(9, 2.0 ** -23) + gamma(n // 64 + 2, 2.0 ** -24)
+def tf32_bound(A64, D, n, splits=1):
+    """|M_tf32 - M| elementwise.  One term: A and D.*A are each rounded to
+    FP32 and then to TF32 (u = 2^-11, round to nearest even), so a product
+    carries at most (1 + 2^-11 + 2^-24)^2 - 1 < 2^-10 + 2^-20 relative error.
+    TF32 x 3: each operand is hi + lo with |v - hi - lo| <= 2^-24 |v| +
+    2^-22 |v| and the dropped lo x lo product is below 2^-22 |a b|: < 2^-20
+    together.  Each 64-long chunk takes 8 (24) tensor-core accumulation steps
+    (u = 2^-23, truncating) and the chunk sums are added in round-to-nearest
+    FP32 (u = 2^-24)."""
+    rep = 2.0 ** -10 + 2.0 ** -20 if splits == 1 else 2.0 ** -20
+    acc = gamma(8 * splits + 1, 2.0 ** -23) + gamma(n // 64 + 2, 2.0 ** -24)
     return (rep + acc + rep * acc) * ((np.abs(A64) * D) @ np.abs(A64).T)
 
 
+@pytest.mark.parametrize("splits", [1, 3])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("m,n", TC_SHAPES)
-def test_normal_matrix_tf32_tensor_cores(pdas, m, n, storage):
-    """TF32 form (tcgen05 kind::tf32): the lower triangle of M = A D A'
-    against the FP64 oracle within the TF32 rounding bound, and its scaled
-    error near 2^-10."""
+def test_normal_matrix_tf32_tensor_cores(pdas, m, n, storage, splits):
+    """TF32 form (tcgen05 kind::tf32, one product or TF32 x 3): the lower
+    triangle of M = A D A' against the FP64 oracle within the rounding bound,
+    and its scaled error near 2^-10 (one product) or FP32 level (three)."""
     lp = lpgen.generate(m, n, seed=7 * m + n, storage=storage)
     rng = np.random.default_rng(12)
     x, s = rng.uniform(0.01, 10, n), rng.uniform(0.01, 10, n)
-    with pdas.Solver(m, n, "tf32_ir", TORCH_DT[storage]) as S:
+    with pdas.Solver(m, n, "tf32_ir", TORCH_DT[storage], splits=splits) as S:
         S.form_normal(dev_A(lp), dv(x), dv(s))
         M = host(S.copy_matrix()).astype(np.float64)
     D = oracle.scaling(x, s)
     ref = oracle.normal_matrix(lp.A64, D)
     low = np.tril_indices(m)
-    assert np.all(np.abs(M[low] - ref[low]) <= tf32_bound(lp.A64, D, n)[low])
-    assert scaled_error(M, ref) <= 4e-3
+    assert np.all(np.abs(M[low] - ref[low]) <= tf32_bound(lp.A64, D, n, splits)[low])
+    assert scaled_error(M, ref) <= {1: 4e-3, 3: 1e-5}[splits]
 
 
 def test_tf32_rounding_is_to_nearest_even(pdas):
@@ -484,18 +488,19 @@ def test_tf32_rounding_is_to_nearest_even(pdas):
     a_tf32 = np.array([1.0, 1.0, 1 + 2.0 ** -9, 1 + 2.0 ** -10, 0.5, -0.25, 0.0, 1.0])
     # every product and partial sum is a multiple of 2^-20 below 8: exact in FP32
     x, s = np.ones(n), np.ones(n)  # D = 1: D.*A = A
-    with pdas.Solver(1, n, "tf32_ir", torch.float64) as S:
+    with pdas.Solver(1, n, "tf32_ir", torch.float64, splits=1) as S:
         S.form_normal(dv(a.reshape(1, n)), dv(x), dv(s))
         M = host(S.copy_matrix()).astype(np.float64)
     assert M[0, 0] == float(np.sum(a_tf32 * a_tf32))
 
 
+@pytest.mark.parametrize("splits", [1, 3])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_tf32_ir_solve_matches_oracle(pdas, seed):
+def test_tf32_ir_solve_matches_oracle(pdas, seed, splits):
     lp = lpgen.generate(64, 128, seed=seed, storage="f64")
     ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
     x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
-    with pdas.Solver(lp.m, lp.n, "tf32_ir", torch.float64) as S:
+    with pdas.Solver(lp.m, lp.n, "tf32_ir", torch.float64, splits=splits) as S:
         out = S.solve(dev_A(lp), dv(lp.b), dv(lp.c), x, y, s, alpha=0.95, tol=1e-8)
     assert out["status"] == 1
     obj_ref = float(lp.c @ ref["x"])
@@ -503,14 +508,15 @@ def test_tf32_ir_solve_matches_oracle(pdas, seed):
     assert out["iters"] == ref["iters"]
 
 
-def test_tf32_ir_c2_first_iterations(pdas):
+@pytest.mark.parametrize("splits", [1, 3])
+def test_tf32_ir_c2_first_iterations(pdas, splits):
     """2048 x 8192 FP64-stored A in the TF32 form: the refined direction makes
     the first two iterates agree with the oracle's to 1e-9 normwise."""
     lp = lpgen.workload("dense_2048x8192_f64", 0)
     A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
     x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
     xo, yo, so = lp.x0.copy(), lp.y0.copy(), lp.s0.copy()
-    with pdas.Solver(lp.m, lp.n, "tf32_ir", torch.float64) as S:
+    with pdas.Solver(lp.m, lp.n, "tf32_ir", torch.float64, splits=splits) as S:
         for k in range(2):
             st, info = S.step(A, b, c, x, y, s, alpha=0.95)
             assert not info["used_fp64"]
@@ -519,6 +525,91 @@ def test_tf32_ir_c2_first_iterations(pdas):
             xo, yo, so = oracle.step(xo, yo, so, d["dx"], d["dy"], d["ds"], th)
             for g, o in ((x, xo), (y, yo), (s, so)):
                 assert np.linalg.norm(host(g) - o) <= 1e-9 * np.linalg.norm(o), k
+
+
+def infeasible_point(lp, seed):
+    """A seeded interior point with A x != b and A'y + s != c."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.5, 2.0, lp.n), rng.standard_normal(lp.m), rng.uniform(0.5, 2.0, lp.n)
+
+
+@pytest.mark.parametrize("form,storage", [("fp64", "f64"), ("fp32_ir", "f32"), ("bf16_ir", "bf16"),
+                                          ("tf32_ir", "f64")])
+def test_infeasible_direction_matches_oracle(pdas, form, storage):
+    """Infeasible-start variant: the direction at an infeasible interior point
+    against the oracle's, normwise to 1e-9 (the mixed forms refine dy to the
+    FP64 backward-error level), and the residual rows of Eq. (3)."""
+    lp = lpgen.generate(130, 520, seed=21, storage=storage)
+    x, y, s = infeasible_point(lp, 5)
+    ref = oracle.direction_infeasible(lp.A64, lp.b, lp.c, x, y, s)
+    with pdas.Solver(lp.m, lp.n, form, TORCH_DT[storage], infeasible=1) as S:
+        dx, dy, ds, info = S.direction_infeasible(dev_A(lp), dv(lp.b), dv(lp.c), dv(x), dv(y), dv(s))
+    for got, want in ((dx, ref["dx"]), (dy, ref["dy"]), (ds, ref["ds"])):
+        assert np.linalg.norm(host(got) - want) <= 1e-9 * np.linalg.norm(want)
+    A = lp.A64
+    assert np.abs(A @ host(dx) - (lp.b - A @ x)).max() <= 1e-9 * (1 + np.abs(lp.b).max())
+    assert np.abs(A.T @ host(dy) + host(ds) - (lp.c - A.T @ y - s)).max() <= 1e-12 * (1 + np.abs(lp.c).max())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_infeasible_fp64_iterates_match_oracle(pdas, seed):
+    """FP64 form, infeasible start at 64 x 128: every iterate normwise to 1e-9
+    of the oracle's, the same iteration count, and the reported residuals."""
+    lp = lpgen.workload("dense_64x128_f64", seed)
+    x0, y0, s0 = infeasible_point(lp, 50 + seed)
+    ref = oracle.solve(lp.A64, lp.b, lp.c, x0, y0, s0, tol=1e-8, keep_iterates=True, infeasible=True)
+    assert ref["status"] == oracle.OPTIMAL
+    n, m = lp.n, lp.m
+    A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+    x, y, s = dv(x0), dv(y0), dv(s0)
+    with pdas.Solver(m, n, "fp64", infeasible=1) as S:
+        for k in range(ref["iters"]):
+            st, info = S.step(A, b, c, x, y, s, alpha=0.95)
+            assert st == 0
+            it = ref["iterates"][k]
+            for g, o in ((x, it[:n]), (y, it[n:n + m]), (s, it[n + m:])):
+                assert np.linalg.norm(host(g) - o) <= 1e-9 * np.linalg.norm(o), k
+            # the reported residuals are those of the GPU's iterate (sums
+            # that cancel: rounding ~ n u |A| |x| / (1 + |b|)), and track the
+            # oracle's run until they reach the floor that the solves'
+            # forward error sets (~1e-10 here), where the two runs' rounding
+            # decides them
+            pres, dres = oracle.residuals(lp.A64, lp.b, lp.c, host(x), host(y), host(s))
+            assert abs(info["pres"] - pres) <= 1e-9 * pres + 1e-13, k
+            assert abs(info["dres"] - dres) <= 1e-9 * dres + 1e-13, k
+            pres_o, dres_o = ref["res_trace"][k]
+            assert abs(info["pres"] - pres_o) <= 1e-3 * pres_o + 1e-10, k
+            assert abs(info["dres"] - dres_o) <= 1e-3 * dres_o + 1e-10, k
+        x, y, s = dv(x0), dv(y0), dv(s0)
+        out = S.solve(A, b, c, x, y, s, alpha=0.95, tol=1e-8)
+    assert out["status"] == 1 and out["iters"] == ref["iters"]
+
+
+@pytest.mark.parametrize("form,storage", [("bf16_ir", "bf16"), ("fp32_ir", "f32"), ("tf32_ir", "f64")])
+def test_infeasible_mixed_solve(pdas, form, storage):
+    """Mixed forms from an infeasible start at 512 x 2048: the oracle's optimal
+    objective to 1e-8 and both residuals below the tolerance."""
+    lp = lpgen.generate(512, 2048, seed=3, storage=storage, scaled=storage == "bf16")
+    x0, y0, s0 = infeasible_point(lp, 8)
+    ref = oracle.solve(lp.A64, lp.b, lp.c, x0, y0, s0, tol=1e-8, infeasible=True)
+    assert ref["status"] == oracle.OPTIMAL
+    x, y, s = dv(x0), dv(y0), dv(s0)
+    with pdas.Solver(lp.m, lp.n, form, TORCH_DT[storage], infeasible=1) as S:
+        out = S.solve(dev_A(lp), dv(lp.b), dv(lp.c), x, y, s, alpha=0.95, tol=1e-8)
+    assert out["status"] == 1
+    obj_ref = float(lp.c @ ref["x"])
+    assert abs(float(lp.c @ host(x)) - obj_ref) <= 1e-8 * abs(obj_ref)
+    pres, dres = oracle.residuals(lp.A64, lp.b, lp.c, host(x), host(y), host(s))
+    assert pres < 1e-8 and dres < 1e-8
+    assert abs(out["iters"] - ref["iters"]) <= 1
+
+
+def test_infeasible_entry_needs_the_option(pdas):
+    lp = lpgen.generate(5, 12, seed=1)
+    x, y, s = infeasible_point(lp, 1)
+    with pdas.Solver(lp.m, lp.n, "fp64") as S:
+        with pytest.raises(pdas.PdasError):
+            S.direction_infeasible(dev_A(lp), dv(lp.b), dv(lp.c), dv(x), dv(y), dv(s))
 
 
 def test_full_size_bf16_tensor_core_sampled(pdas):
