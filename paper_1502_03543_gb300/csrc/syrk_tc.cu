@@ -22,17 +22,21 @@
 // its error grows with the number of accumulation steps in one direction
 // (measured on GB300: 1.5e-4 relative at K = 32768 against 1e-6 for an IEEE
 // FP32 dot product).  The K loop is therefore cut into chunks of KC = 128
-// elements: each chunk is summed on the tensor core into a fresh TMEM buffer
-// (two buffers alternate), and the epilogue warps add the chunk sums, with
-// round-to-nearest FP32, into a master accumulator held in registers.
+// elements (64 for TF32): each chunk is summed on the tensor core into a
+// fresh TMEM buffer (two buffers alternate), and the epilogue warps add the
+// chunk sums, with round-to-nearest FP32, into a master accumulator held in
+// registers.
 //
-// Kernel k_syrk_tc<S>: one CTA per 128 x 128 lower-triangle tile, 6 warps:
-//   warp 0      TMA producer: per K step of 64 (one 128-byte swizzle row) the
-//               A tile and the S tiles of B_t, 128 x 64 each, into a ring of
-//               STAGES (= 192 KB / (16 KB (1 + S))) stages;
+// Kernel k_syrk_tc<S, TF32, ALO>: one CTA per 128 x 128 lower-triangle tile,
+// 6 warps:
+//   warp 0      TMA producer: per K step of one 128-byte swizzle row (64 BF16
+//               or 32 TF32 elements) the A tile (and A_1 for TF32 x 3) and
+//               the S tiles of B_t, 16 KB each, into a ring of
+//               STAGES (= 192 KB / (16 KB x tiles per stage)) stages;
 //   warp 1      allocates 256 TMEM columns; one lane issues
-//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
-//               into the current chunk buffer and commits chunk and stage;
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16) or
+//               .kind::tf32 (K=8), four per product and K step, into the
+//               current chunk buffer and commits chunk and stage;
 //   warps 2..5  warp w owns TMEM lanes 32*(w%4)..: drains each chunk
 //               (tcgen05.ld) into its 128-float master row, frees the
 //               buffer, and finally writes the rows p >= q of M.
