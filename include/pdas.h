@@ -58,8 +58,8 @@ typedef enum {
 typedef enum {
   PDAS_FP64 = 0,    /* M = A D A' formed and factored in FP64                          */
   PDAS_TF32_IR = 1, /* M formed on tcgen05 tensor cores from TF32 operands (A and D.*A
-                       rounded to TF32 each call; A stored as FP64 or FP32), FP32 factor,
-                       FP64 refinement of dy                                            */
+                       split into TF32 parts each call, see splits; A stored as FP64 or
+                       FP32), FP32 factor, FP64 refinement of dy                         */
   PDAS_BF16_IR = 2, /* as TF32_IR with BF16 operands (needs A stored as BF16)            */
   PDAS_FP32_IR = 3  /* M formed with FP32 SIMT arithmetic, FP32 factor, FP64 refinement  */
 } pdas_form;
@@ -166,12 +166,16 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt, pdas_hand
  * y (m), s (n).  A: m x n device array; b (m), c (n): device doubles, used
  * for the gap.  0 < alpha < 1 (Section III).  info may be NULL.
  * Returns PDAS_OK to continue, PDAS_OPTIMAL_EXACT if psi <= 1, or an error;
- * on an error the iterate is left as it was before the call. */
+ * on an error the iterate is left as it was before the call.  With
+ * opt.infeasible the step is the variant's (see pdas_options): the residual
+ * right-hand sides, theta = min(1, alpha/psi), never PDAS_OPTIMAL_EXACT, and
+ * info->pres / dres hold the new iterate's relative residuals. */
 pdas_status pdas_step(pdas_handle h, const void* A, const double* b, const double* c, double* x, double* y,
                       double* s, double alpha, pdas_iter_info* info);
 
 /* Runs the algorithm of Section III from the interior point (x, y, s) until
- * the relative gap drops below tol (tested after each step), psi <= 1, the
+ * the relative gap drops below tol (tested after each step; with
+ * opt.infeasible, |gap| and both relative residuals below tol), psi <= 1, the
  * direction vanishes, stall, or max_iter.  x, y, s are updated in place to
  * the final iterate.  iters_out, rel_gap_out may be NULL.  Checks x > 0 and
  * s > 0 first (PDAS_ERR_NOT_INTERIOR, nothing modified). */
