@@ -51,7 +51,7 @@ typedef enum {
   PDAS_ERR_NONFINITE = -4,  /* NaN or Inf met in the iterate, direction or psi */
   PDAS_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up              */
   PDAS_ERR_CUDA = -6,       /* a CUDA runtime call failed (message: pdas_last_error_message) */
-  PDAS_ERR_UNSUPPORTED = -7 /* entry point or option not available in this build */
+  PDAS_ERR_UNSUPPORTED = -7 /* entry point or option not available in this library */
 } pdas_status;
 
 /* Precision forms of the normal-equations solve. */

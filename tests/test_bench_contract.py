@@ -1,6 +1,6 @@
 """The benchmark's JSON contract, checked on the CPU: the reference arm
-(the oracle timed on the host cores) prints one line with the keys the
-driver reads, and the roofline helpers report what they claim."""
+(the oracle timed on the host cores) prints one line with the keys its
+readers expect, and the roofline helpers report what they claim."""
 import json
 import os
 import subprocess
