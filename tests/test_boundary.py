@@ -100,3 +100,14 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(N, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         N.lib()
+
+
+def test_binding_refuses_host_tensors():
+    """No CPU fallback: the binding accepts device tensors only, and checks
+    dtype, size and contiguity before anything reaches the library."""
+    import torch
+    from paper_1502_03543_gb300 import _ptr
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        _ptr(torch.zeros(4, dtype=torch.float64), torch.float64, 4, "x")
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        _ptr([0.0] * 4, torch.float64, 4, "x")
