@@ -486,6 +486,10 @@ MUTANTS = [
     ("variant theta overshoots", "psi <= alpha ? 1.0 : alpha / psi", "psi <= 1.0 ? 1.0 : 1.0 / psi"),
     ("variant stop ignores residuals", "fabs(gap) < tol && res[0] < tol && res[1] < tol", "fabs(gap) < tol"),
     ("residual norm of b", "bn = fmax(bn, fabs(b[p]));", "bn = fmax(bn, fabs(t[p]));"),
+    ("dual residual norm sign of s", "rdn = fmax(rdn, fabs((c[j] - w[j]) - s[j]));",
+     "rdn = fmax(rdn, fabs((c[j] - w[j]) + s[j]));"),
+    ("primal residual norm uses b only", "rp = fmax(rp, fabs(b[p] - t[p]));", "rp = fmax(rp, fabs(b[p]));"),
+    ("variant theta full step at psi <= 1", "psi <= alpha ? 1.0 : alpha / psi", "psi <= 1.0 ? 1.0 : alpha / psi"),
 ]
 
 
