@@ -1,18 +1,27 @@
-"""Benchmark: Newton iterations per second of the primal-dual affine scaling
-solve (one step = one pass of the whole per-iteration path: D = x/s, r = A x,
-M = A D A', Cholesky, triangular solves / FP64 refinement, directions, psi and
-the step) on the dense LP m = 8192, n = 32768 with A stored in BF16
-(columns scaled by U(0.1, 10)), seeded synthetic data.
+"""Benchmark: Newton iterations per second and time to a relative gap of
+1e-8 of the primal-dual affine scaling solve on the dense LP m = 8192,
+n = 32768 with A stored in BF16 (columns scaled by U(0.1, 10)), seeded
+synthetic data; the mixed-precision form (tensor-core normal matrix, FP32
+factor, FP64 refinement) beside the plain FP64 GPU form.
+
+One step = one pass of the whole per-iteration path: D = x/s, r = A x,
+M = A D A', Cholesky, triangular solves and FP64 refinement, directions,
+psi and the step.  `value` times K such steps of the mixed form from the
+seeded start (the first K iterations of a solve, restarted after
+convergence); the line also carries both forms' full solves to the gap
+(time to gap, iterations, objective, whole-solve iterations per second).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on a bounded sample of the same workload instead.  --gpus N > 1 (under
-torchrun) runs N independent replicas, one LP per GPU: the single-LP path
-does not shard.
+(full Newton iterations from the same seeded start) instead.  --gpus N > 1
+(under torchrun) runs N independent replicas, one LP per GPU: the single-LP
+path does not shard.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,6 +41,7 @@ METRIC = "Newton iters/s & time-to-gap-1e-8, mixed vs FP64 GPU, m=8192 n=32768"
 UNIT = "Newton iters/s"
 DEFAULT_WORKLOAD = "dense_8192x32768_bf16_colscaled"
 ALPHA = 0.95
+CSRC = os.path.join(ROOT, "paper_1502_03543_gb300", "csrc")
 
 FORM_DTYPE_LABEL = {"fp64": "f64", "fp32_ir": "f32-f64", "bf16_ir": "bf16-f32-f64", "tf32_ir": "tf32-f32-f64"}
 
@@ -46,14 +56,63 @@ def load_peaks():
     return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, source="fallback")
 
 
-# DRAM bytes (read + write) per launch of the normal-matrix kernel from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of
-# `bench.py --kernel normal` on this workload; profiles/syrk_tc_bf16x3_8192x32768.md.
-# Valid only for the kernel as captured.  The kernel's source has changed
-# since (the TF32 template parameters; the BF16 loads and tile order are as
-# captured), so the roofline reports traffic as null and this figure under
-# traffic_at_capture until a new capture.
-SYRK_TRAFFIC_AT_CAPTURE = {("dense_8192x32768_bf16_colscaled", 3): 10.32e9 + 0.131e9}
+def probe_peaks(device="cuda", n=8192):
+    """Dense matmul peaks of the dtypes without a measured figure:
+    torch.matmul (cuBLAS) at n^3, best of a few launches timed with CUDA
+    events after one warm-up: TF32 (FP32 with TF32 allowed), FP32 (TF32
+    off) and FP64.  Returns TFLOP/s (2 n^3 flops per product)."""
+    import torch
+    saved = torch.backends.cuda.matmul.allow_tf32
+    out = {}
+    try:
+        for name, dt, tf32, reps in (("tf32", torch.float32, True, 10), ("fp32", torch.float32, False, 5),
+                                     ("fp64", torch.float64, False, 3)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            g = torch.Generator(device=device).manual_seed(7)
+            a = torch.randn(n, n, dtype=dt, device=device, generator=g)
+            b = torch.randn(n, n, dtype=dt, device=device, generator=g)
+            c = torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = math.inf
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = round(2.0 * n ** 3 / (best * 1e-3) / 1e12, 2)
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = saved
+        torch.cuda.empty_cache()
+    out["how"] = "torch.matmul %d^3 per dtype, best of 10/5/3 after one warm-up, CUDA events, in this run" % n
+    return out
+
+
+# DRAM bytes (read + write) per launch of the BF16 normal-matrix kernel from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, a single
+# pass, one launch) of `bench.py --kernel normal --steps 1 --warmup 1` on this
+# workload.  Valid only for the kernel source it was captured on: the digest
+# of its sources must match, else the roofline reports traffic as null.
+SYRK_TRAFFIC_CAPTURES = {("dense_8192x32768_bf16_colscaled", 3): dict(bytes=10270291456 + 132332800,
+                                                                       digest="2ab6bed042edf37a")}
+SYRK_SOURCES = ("syrk_tc.cu", "syrk_tc.cuh", "tc_util.cuh")
+
+
+def syrk_source_digest():
+    h = hashlib.sha1()
+    for f in SYRK_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def syrk_traffic(workload, terms):
+    cap = SYRK_TRAFFIC_CAPTURES.get((workload, terms))
+    if cap and cap["digest"] == syrk_source_digest():
+        return float(cap["bytes"])
+    return None
 
 
 def form_terms(form, splits):
@@ -66,57 +125,85 @@ def form_terms(form, splits):
     return 1
 
 
+def fp32_simt_peak(peaks):
+    """152 SMs x 128 FP32 lanes x 2 flops x the maximum SM clock (TFLOP/s)."""
+    return 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+
+
 def syrk_roofline(form, m, n, splits, ms_per_launch, peaks, workload=None):
     """Roofline record of the normal-matrix kernel.  Algorithmic work is one
-    lower-triangle product, m(m+1)/2 entries of n multiply-adds (m^2 n flops,
-    FMA = 2); the tensor-core forms execute that product once per split term
-    of D.*A, reported separately as executed work."""
+    lower-triangle product, m(m+1)/2 entries of n multiply-adds (m(m+1)n
+    flops, FMA = 2); the tensor-core forms execute that product once per
+    split term of D.*A, reported separately as executed work.  Peaks: BF16
+    sustained from MEASURED_PEAKS.json; TF32, FP32 and FP64 from this run's
+    matmul probe when present."""
     terms = splits if form in ("bf16_ir", "tf32_ir") else 1
     flops = float(m) * (m + 1) * n
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     if form == "bf16_ir":
         bound, peak, note = "tensor", peaks["bf16_sus"], "bf16 dense, sustained, of %s" % peaks["source"]
     elif form == "tf32_ir":
-        bound, peak, note = "tensor", peaks["bf16_sus"] * 1.1 / 2.25, "tf32 = bf16 sustained x 1.1/2.25 nominal ratio"
+        if "tf32" in peaks:
+            bound, peak, note = "tensor", peaks["tf32"], "tf32 dense, burst, of measured (matmul probe)"
+        else:
+            bound, peak, note = "tensor", peaks["bf16_sus"] * 1.1 / 2.25, "tf32 = bf16 sustained x 1.1/2.25 nominal"
     elif form == "fp32_ir":
-        bound, peak, note = "alu", fp32_simt_peak(peaks), "FP32 SIMT from unit counts"
+        if "fp32" in peaks:
+            bound, peak, note = "alu", peaks["fp32"], "fp32 dense, burst, of measured (matmul probe)"
+        else:
+            bound, peak, note = "alu", fp32_simt_peak(peaks), "fp32 SIMT from unit counts"
     else:
-        bound, peak, note = "alu", 1.25, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
-    traffic = None
-    captured = SYRK_TRAFFIC_AT_CAPTURE.get((workload, terms)) if form == "bf16_ir" else None
-    return dict(bound=bound, achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
-                frac=round(achieved / peak, 4), traffic=traffic, kernel="normal-matrix k_syrk_tc (a3)",
-                peak_note=note, algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4),
-                split_terms=terms, executed_flops_per_launch=flops * terms,
-                executed_frac=round(achieved * terms / peak, 4), traffic_at_capture=captured)
-
-
-def fp32_simt_peak(peaks):
-    """152 SMs x 128 FP32 lanes x 2 flops x the maximum SM clock (TFLOP/s)."""
-    return 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        if "fp64" in peaks:
+            bound, peak, note = "alu", peaks["fp64"], "fp64 dense, burst, of measured (matmul probe)"
+        else:
+            bound, peak, note = "alu", 1.25, "fp64 nominal 1.25 TFLOP/s"
+    traffic = syrk_traffic(workload, terms) if form == "bf16_ir" else None
+    rec = dict(bound=bound, achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
+               frac=round(achieved / peak, 4), traffic=traffic, kernel="normal-matrix k_syrk_tc (a3)",
+               peak_note=note, algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4),
+               split_terms=terms, executed_flops_per_launch=flops * terms,
+               executed_frac=round(achieved * terms / peak, 4))
+    if traffic is not None:
+        # algorithmic bytes: A, the split planes of D.*A (terms), the lower triangle of M (FP32)
+        alg = 2.0 * m * n * (1 + terms) + 4.0 * m * (m + 1) / 2
+        rec["traffic_note"] = ("ncu dram bytes read+write per launch; algorithmic %.3g B (A, %d planes of D.*A, lower M),"
+                               " ratio %.2f" % (alg, terms, traffic / alg))
+    return rec
 
 
 def chol_roofline(form, m, ms_per_launch, peaks):
     """Roofline record of the Cholesky factor: m^3/3 flops.  The FP32 tile
     factor of the mixed forms runs its trailing products (~97% of the flops)
     on the tensor cores as six BF16 products per FP32-grade product, so its
-    roof is the sustained BF16 peak / 6; the fraction of the FP32 SIMT peak is
+    roof is the sustained BF16 peak / 6; the fraction of the FP32 peak is
     given beside it.  The FP64 form's factor runs on the FP64 pipes."""
     flops = float(m) ** 3 / 3.0
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     if form == "fp64":
-        return dict(bound="alu", achieved=round(achieved, 3), peak=1.25, unit="TFLOP/s",
-                    frac=round(achieved / 1.25, 4), traffic=None, kernel="blocked FP64 Cholesky (a4)",
-                    peak_note="FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)",
-                    algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4))
+        peak = peaks.get("fp64", 1.25)
+        note = "fp64 dense, burst, of measured (matmul probe)" if "fp64" in peaks else "fp64 nominal 1.25 TFLOP/s"
+        return dict(bound="alu", achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
+                    frac=round(achieved / peak, 4), traffic=None, kernel="blocked FP64 Cholesky (a4)",
+                    peak_note=note, algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4))
     peak = peaks["bf16_sus"] / 6.0
-    simt = fp32_simt_peak(peaks)
+    simt = peaks.get("fp32", fp32_simt_peak(peaks))
     return dict(bound="tensor", achieved=round(achieved, 3), peak=round(peak, 3), unit="TFLOP/s",
                 frac=round(achieved / peak, 4), traffic=None, kernel="k_chol_tiles<float> (a4)",
                 peak_note="FP32-grade products as 6 BF16 MMAs: bf16 dense sustained / 6, of %s; the factor "
                           "is bound by its chain of diagonal tasks" % peaks["source"],
-                fp32_simt_peak=round(simt, 3), fp32_simt_frac=round(achieved / simt, 4),
+                fp32_peak=round(simt, 3), fp32_frac=round(achieved / simt, 4),
                 algorithmic_flops_per_launch=flops, ms_per_launch=round(ms_per_launch, 4))
+
+
+def stop_margin(gap, tol):
+    """|log10(|gap| / tol)| of a finished solve: how far its last gap sits
+    from the stop threshold (a run within 1e-3 of it is flagged: one more or
+    one fewer iteration there is rounding, not the method).  A negative gap
+    (c'x < b'y: the iterate has drifted off primal feasibility) is measured
+    by its magnitude and reported beside it."""
+    if not (gap != 0 and tol > 0) or math.isnan(gap):
+        return None
+    return abs(math.log10(abs(gap) / tol))
 
 
 class ClockSampler:
@@ -171,54 +258,25 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(rows))
 
 
-def oracle_sample(lp, band_rows=64, chol_m=2048):
-    """Time the FP64 CPU oracle on a bounded sample of one Newton iteration of
-    this LP and project the full iteration.  Returns (seconds per iteration,
-    cores, description)."""
+def oracle_iterations(lp, count, budget_s=None):
+    """Full Newton iterations of the FP64 CPU oracle from the seeded start
+    (direction, psi, theta, step: the algorithm of Section III, nothing
+    projected), timed one by one.  Runs `count` iterations, or, when the
+    first one shows that `count` would not fit budget_s, as many as fit (at
+    least one).  Returns (list of seconds per iteration, threads used)."""
     import oracle
     A64 = lp.A64
-    m, n = A64.shape
-    x, s = lp.x0, lp.s0
-    t = {}
-    t0 = time.perf_counter()
-    D = oracle.scaling(x, s)
-    r = oracle.gemv(A64, x)
-    t["rhs"] = time.perf_counter() - t0
-    # normal matrix: a band of the last rows (the longest), scaled by entries
-    band = min(band_rows, m)
-    p0 = m - band
-    t0 = time.perf_counter()
-    oracle.normal_rows(A64, D, p0, m)
-    t_band = time.perf_counter() - t0
-    band_entries = sum(p + 1 for p in range(p0, m))
-    t["normal"] = t_band * (m * (m + 1) / 2) / band_entries
-    # Cholesky and triangular solves on a chol_m x chol_m normal matrix of the
-    # same family, scaled by (m / chol_m)^3 and (m / chol_m)^2
-    mc = min(chol_m, m)
-    nc = min(n, 4 * mc)
-    Mc = oracle.normal_matrix(A64[:mc, :nc], D[:nc])
-    t0 = time.perf_counter()
-    Lc, fail = oracle.cholesky(Mc)
-    t["factor"] = (time.perf_counter() - t0) * (m / mc) ** 3
-    t0 = time.perf_counter()
-    oracle.backward(Lc, oracle.forward(Lc, r[:mc]))
-    t["solve"] = (time.perf_counter() - t0) * (m / mc) ** 2
-    t0 = time.perf_counter()
-    dy = np.zeros(m)
-    w = oracle.gemv_t(A64, dy)
-    ds = -w
-    dx = D * w - x
-    t["direction"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    p = oracle.psi(x, s, dx, ds)
-    oracle.step(x, lp.y0, s, dx, dy, ds, oracle.theta(p, ALPHA))
-    t["step"] = time.perf_counter() - t0
-    total = sum(t.values())
-    desc = ("one Newton iteration at %dx%d projected from: full A x, A'dy, psi and step; normal-matrix rows "
-            "%d..%d (%d of %d lower entries) scaled by entry count; Cholesky + triangular solves of a %dx%d "
-            "normal matrix scaled by (m/%d)^3 and ^2" % (m, n, p0, m - 1, band_entries, m * (m + 1) // 2, mc, mc,
-                                                          mc))
-    return total, oracle.threads(), desc, {k: round(v, 3) for k, v in t.items()}
+    x, y, s = lp.x0.copy(), lp.y0.copy(), lp.s0.copy()
+    secs = []
+    while len(secs) < count:
+        t0 = time.perf_counter()
+        d = oracle.direction(A64, x, s)
+        th = oracle.theta(oracle.psi(x, s, d["dx"], d["ds"]), ALPHA)
+        x, y, s = oracle.step(x, y, s, d["dx"], d["dy"], d["ds"], th)
+        secs.append(time.perf_counter() - t0)
+        if budget_s is not None and len(secs) == 1 and count > 1:
+            count = max(1, min(count, int(budget_s // max(secs[0], 1e-9))))
+    return secs, oracle.threads()
 
 
 def replica_rate(local_elapsed, steps, world, device="cpu"):
@@ -241,23 +299,49 @@ def dist_info():
     return world, rank, local
 
 
+def bench_config(lp, workload, form, splits, world):
+    """The config dict of both arms: the workload and the form it is run in."""
+    return dict(workload=workload, m=lp.m, n=lp.n, a_storage=lp.storage, form=form,
+                splits=splits if form in ("bf16_ir", "tf32_ir") else None, alpha=ALPHA,
+                tol=lpgen.WORKLOADS[workload]["tol"],
+                steps_from="seeded interior start: the first K iterations of a solve (restart after convergence)",
+                l2="inputs larger than L2 (A is %d MB)" % (lp.m * lp.n * lp.A_store.itemsize // 2 ** 20),
+                parallelism="replicas" if world > 1 else "single")
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, timed on the
+    host cores over full Newton iterations from the seeded start.  Each step
+    is one whole iteration; W warm-up iterations and K timed ones are run
+    when the first iteration shows that they fit --ref-budget seconds, else
+    as many timed iterations as fit (at least one) and no warm-up.  `steps`
+    and `warmup` report what was run."""
     world, rank, _ = dist_info()
     if rank != 0:
         return
     lp = lpgen.workload(args.workload, seed=0)
-    samples = []
-    for i in range(args.warmup + args.steps):
-        sec, cores, desc, parts = oracle_sample(lp, band_rows=16, chol_m=1024)
-        if i >= args.warmup:
-            samples.append(sec)
-    sec = sum(samples) / len(samples)
+    secs, cores = oracle_iterations(lp, 1)
+    first = secs[0]
+    if (args.warmup + args.steps) * first <= args.ref_budget:
+        warm = args.warmup
+        secs, cores = oracle_iterations(lp, args.warmup + args.steps)
+        timed = secs[warm:]
+    else:
+        warm = 0
+        timed, cores = oracle_iterations(lp, args.steps, budget_s=args.ref_budget)
+    sec = sum(timed) / len(timed)
     value = 1.0 / sec
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+    splits = form_terms(args.form, args.splits)
+    sample = ("%d full Newton iteration(s) %d..%d of the solve from the seeded start at %dx%d, each timed whole "
+              "(direction, psi, step), after %d untimed" % (len(timed), warm, warm + len(timed) - 1, lp.m, lp.n,
+                                                             warm))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=len(timed), warmup=warm,
                 ms_per_step=sec * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
-                config=dict(workload=args.workload, m=lp.m, n=lp.n, alpha=ALPHA, l2="inputs larger than L2"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle", sample=desc),
+                config=bench_config(lp, args.workload, args.form, splits, world),
+                requested=dict(steps=args.steps, warmup=args.warmup, budget_s=args.ref_budget),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle", sample=sample,
+                                  seconds_per_iteration=[round(t, 3) for t in timed]),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
@@ -315,6 +399,32 @@ def run_normal_only(args):
     print(json.dumps(out))
 
 
+def timed_solve(P, torch, lp, A, a_dtype, form, stream, tol, opts):
+    """One full solve from the seeded start through pdas_solve, timed with
+    CUDA events on the handle's stream, with the library's per-stage times."""
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    b, c = dv(lp.b), dv(lp.c)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    with P.Solver(lp.m, lp.n, form, a_dtype, stream=stream, **opts) as S:
+        torch.cuda.synchronize()
+        S.profile_enable(True)
+        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ta.record(stream)
+        out = S.solve(A, b, c, x, y, s, alpha=ALPHA, tol=tol)
+        tb.record(stream)
+        torch.cuda.synchronize()
+        prof = S.profile_read()
+    secs = ta.elapsed_time(tb) / 1e3
+    margin = stop_margin(out["rel_gap"], tol)
+    return dict(form=form, seconds=round(secs, 4), iters=out["iters"], status=out["status_name"],
+                rel_gap=out["rel_gap"], objective=float(torch.dot(c, x).item()),
+                whole_solve_iters_per_s=round(out["iters"] / secs, 4) if secs > 0 else None,
+                stop_margin=round(margin, 4) if margin is not None else None,
+                near_threshold=bool(margin is not None and margin < 1e-3), gap_negative=bool(out["rel_gap"] < 0),
+                stages_s={k: round(v / 1e3, 3) for k, v in prof["ms"].items() if v},
+                gpu_launches=prof["launches"]), (x, y, s)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -336,6 +446,12 @@ def run_ours(args):
     else:
         A = torch.from_numpy(np.ascontiguousarray(lp.A_store)).cuda()
         a_dtype = A.dtype
+    peaks = load_peaks()
+    if not args.no_peak_probe:
+        probe = probe_peaks()
+        peaks.update({k: v for k, v in probe.items() if k != "how"})
+    else:
+        probe = None
     dv = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
     b, c = dv(lp.b), dv(lp.c)
     x0, y0, s0 = dv(lp.x0), dv(lp.y0), dv(lp.s0)
@@ -397,7 +513,7 @@ def run_ours(args):
         x.copy_(src[0], non_blocking=True)
         y.copy_(src[1], non_blocking=True)
         s.copy_(src[2], non_blocking=True)
-        info = one_step()
+        one_step()
         ox.copy_(x, non_blocking=True)
         oy.copy_(y, non_blocking=True)
         os_.copy_(s, non_blocking=True)
@@ -405,29 +521,27 @@ def run_ours(args):
     e2e_elapsed = time.perf_counter() - t0
     e2e_value, _ = replica_rate(e2e_elapsed, args.steps, world, device="cuda")
     vec_bytes = 8 * (2 * n + m)
-
-    ttg = None
-    # the metric's second half: one full solve from the seeded start (on by
-    # default for the mixed forms, ~9 s at 8192 x 32768; the FP64 form's
-    # ~110 s solve only with --time-to-gap)
-    if args.time_to_gap or (args.form != "fp64" and not args.no_time_to_gap):
-        restart()
-        torch.cuda.synchronize()
-        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ta.record(stream)
-        out = S.solve(A, b, c, x, y, s, alpha=ALPHA, tol=w["tol"])
-        tb.record(stream)
-        torch.cuda.synchronize()
-        secs = ta.elapsed_time(tb) / 1e3
-        ttg = dict(seconds=secs, iters=out["iters"], status=out["status_name"], rel_gap=out["rel_gap"],
-                   objective=float(torch.dot(c, x).item()))
     S.close()
+
+    # the metric's second half: full solves to the gap from the seeded start,
+    # the mixed form and the plain FP64 GPU form, each through pdas_solve
+    ttg, ttg64, comparison = None, None, None
+    if not args.no_time_to_gap:
+        ttg, _ = timed_solve(P, torch, lp, A, a_dtype, args.form, stream, w["tol"], opts)
+        if args.form != "fp64" and not args.no_fp64_arm:
+            ttg64, _ = timed_solve(P, torch, lp, A, a_dtype, "fp64", stream, w["tol"], {})
+            comparison = dict(
+                mixed_s=ttg["seconds"], fp64_s=ttg64["seconds"], speedup=round(ttg64["seconds"] / ttg["seconds"], 3),
+                iters_mixed=ttg["iters"], iters_fp64=ttg64["iters"],
+                iteration_counts_equal=ttg["iters"] == ttg64["iters"],
+                objective_rel_diff=abs(ttg["objective"] - ttg64["objective"]) / abs(ttg64["objective"]),
+                note="both stop after the first step with rel_gap < tol; iteration counts can differ by one when "
+                     "either run ends close to the threshold (see stop_margin)")
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    peaks = load_peaks()
     normal_ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
     factor_ms = prof["ms"]["factor"] / max(1, prof["calls"]["factor"])
     # the dominant kernel of the step is reported as "roofline"; both records
@@ -437,25 +551,35 @@ def run_ours(args):
     roof = max(roofs, key=lambda r: r["ms_per_launch"])
     stages = {k: round(v / max(1, args.steps), 4) for k, v in prof["ms"].items()}
     clocks = clk.summary()
+    fp64_steps = sum(i["used_fp64"] for i in infos)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=elapsed_max * 1e3 / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype=FORM_DTYPE_LABEL[args.form], data="synthetic",
-                config=dict(workload=args.workload, m=m, n=n, a_storage=lp.storage, form=args.form,
-                            splits=splits if args.form in ("bf16_ir", "tf32_ir") else None, alpha=ALPHA,
-                            steps_from="seeded interior start (restart after convergence)",
-                            l2="inputs larger than L2 (A is %d MB)" % (A.numel() * A.element_size() // 2 ** 20),
-                            parallelism="replicas" if world > 1 else "single"),
+                config=bench_config(lp, args.workload, args.form, splits, world),
+                window=dict(iterations="0..%d of the solve from the seeded start" % (args.steps - 1)
+                            if args.steps <= (ttg or {}).get("iters", args.steps) else
+                            "the solve from the seeded start, restarted after convergence",
+                            fp32_tier_steps=args.steps - fp64_steps, fp64_tier_steps=fp64_steps,
+                            note="value covers these iterations only; whole_solve_iters_per_s covers a full solve"),
                 roofline=roof, rooflines=roofs, stages_ms_per_step=stages,
                 refine_sweeps=[i["refine_sweeps"] for i in infos], used_fp64=[i["used_fp64"] for i in infos],
                 gpu_launches=prof["launches"],
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=vec_bytes, d2h_bytes_per_step=vec_bytes),
                 clocks=clocks)
+    if probe:
+        line["peaks_probe"] = probe
     if ttg:
         line["time_to_gap"] = ttg
+        line["whole_solve_iters_per_s"] = ttg["whole_solve_iters_per_s"]
+    if ttg64:
+        line["time_to_gap_fp64"] = ttg64
+        line["mixed_vs_fp64"] = comparison
     if not args.no_cpu_baseline and world == 1:
-        sec, cores, desc, parts = oracle_sample(lp)
-        line["cpu_baseline"] = dict(value=1.0 / sec, unit=UNIT, cores=cores, kind="oracle", sample=desc,
-                                    projected_seconds_per_iter=round(sec, 2), parts_s=parts)
+        secs, cores = oracle_iterations(lp, 1)
+        line["cpu_baseline"] = dict(value=1.0 / secs[0], unit=UNIT, cores=cores, kind="oracle",
+                                    sample="the first Newton iteration of the solve from the seeded start at %dx%d, "
+                                           "timed whole (direction, psi, step)" % (m, n),
+                                    seconds_per_iteration=[round(t, 3) for t in secs])
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -514,10 +638,12 @@ def main():
     ap.add_argument("--form", default="bf16_ir", choices=sorted(FORM_DTYPE_LABEL))
     ap.add_argument("--splits", type=int, default=0)
     ap.add_argument("--dspread", type=float, default=None, help="dspread_refactor option (<= 0 disables)")
-    ap.add_argument("--time-to-gap", action="store_true",
-                    help="also time one full solve to the gap tolerance (default for the mixed forms)")
-    ap.add_argument("--no-time-to-gap", action="store_true", help="skip the full solve of the mixed forms")
+    ap.add_argument("--no-time-to-gap", action="store_true", help="skip the full solves to the gap")
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 form's full solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peak-probe", action="store_true", help="skip the TF32/FP32/FP64 matmul probe")
+    ap.add_argument("--ref-budget", type=float, default=200.0,
+                    help="reference arm: seconds of oracle iterations to fit the run into")
     ap.add_argument("--kernel", choices=["step", "normal", "factor"], default="step",
                     help="normal: time only the normal-matrix stage; factor: also the Cholesky (for profiles)")
     ap.add_argument("--batch", action="store_true", help="time the 512-LP batch configuration instead")

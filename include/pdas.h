@@ -108,6 +108,11 @@ typedef struct {
                               |rel_gap|, pres and dres (pdas_iter_info) are all below tol.
                               The variant has no centring term: from starts far from
                               feasibility it can stall at the boundary (PDAS_STALLED)   (0) */
+  int fp64_tier_tc;        /* mixed forms with A stored as BF16, in the FP64 tier: 1 = the normal
+                              matrix of the kept columns (up to 16384 of them) is formed on the
+                              tensor cores from exact fixed-point BF16 digit planes of A and of
+                              D.*A (FP64-grade: products and sums exact, one FP64 rounding at
+                              the end); 0 = double-float on the FP32 pipes (normal_form 2)    (1) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */
@@ -126,7 +131,8 @@ typedef struct {
                            3 refinement did not reach its tolerance            */
   int64_t factor_columns; /* columns of A that formed the factor (n unless dropped) */
   int normal_form;      /* arithmetic of the normal matrix: 0 tcgen05 tensor cores, 1 FP32 SIMT,
-                           2 double-float (FP32 pairs, ~48-bit) on the FP32 pipes, 3 FP64        */
+                           2 double-float (FP32 pairs, ~48-bit) on the FP32 pipes, 3 FP64,
+                           4 tcgen05 tensor cores on fixed-point digit planes (FP64-grade)       */
   double pres, dres;    /* infeasible-start variant: ||b - A x||_inf / (1 + ||b||_inf) and
                            ||c - A'y - s||_inf / (1 + ||c||_inf) after the step (else 0)        */
 } pdas_iter_info;
@@ -155,7 +161,10 @@ typedef struct {
 void pdas_default_options(pdas_options* opt);
 
 /* Creates a handle for m x n problems (1 <= m < n, Section I) and allocates
- * its workspace on the current CUDA device.  opt may be NULL (defaults).
+ * its whole workspace on the current CUDA device, including the FP64 tier
+ * of a mixed form (an FP64 m x m matrix and, with drop_tol > 0, an m x n
+ * copy of the kept columns of A) and the adjoint's vectors: no later call
+ * allocates device memory.  opt may be NULL (defaults).
  * Returns PDAS_ERR_ARG for bad sizes/options, PDAS_ERR_UNSUPPORTED for a
  * form/dtype pair that is not built, PDAS_ERR_CUDA if allocation fails. */
 pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt, pdas_handle* out);
@@ -210,6 +219,16 @@ int64_t pdas_last_error_index(pdas_handle h);
 
 /* Text of the last CUDA error seen by the handle ("" if none). */
 const char* pdas_last_error_message(pdas_handle h);
+
+/* Limit of every bounded inter-block wait of the handle's later calls, in
+ * microseconds (failure detection; the paper has no counterpart): the
+ * triangular solves' hand-offs between blocks and the tile Cholesky's
+ * dependency waits give up after it, record PDAS_ERR_TIMEOUT and return,
+ * leaving the handle usable.  0 restores the default of 2 s.  The waits on
+ * the tensor-core pipelines' own barriers keep their fixed 2 s bound.
+ * Synchronises the handle's stream.  PDAS_ERR_ARG if microseconds is
+ * negative or above 2^31 - 1. */
+pdas_status pdas_set_wait_limit(pdas_handle h, int64_t microseconds);
 
 /* Starts (enable = 1) or stops (0) per-stage timing; starting clears the
  * accumulators and the launch count.  Timing adds one event record per

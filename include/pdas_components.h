@@ -104,7 +104,9 @@ int64_t pdas_chol_tile_tasks(int64_t m, int32_t nproc, int32_t* out, int64_t cap
  * calls share that array, so calls that overlap on the GPU race: serialise
  * them.  The first call on a device fetches the array's device address
  * (with that device current) and loads the kernels; make it before any
- * stream capture.  Returns PDAS_OK, PDAS_ERR_ARG or PDAS_ERR_CUDA. */
+ * stream capture.  That address is kept until the process exits, so it does
+ * not survive cudaDeviceReset: do not call this entry point on a device
+ * after resetting it.  Returns PDAS_OK, PDAS_ERR_ARG or PDAS_ERR_CUDA. */
 pdas_status pdas_gemv_t_noalloc(int64_t m, int64_t n, int a_dtype, const void* A, const double* u, double* out,
                                 void* stream);
 

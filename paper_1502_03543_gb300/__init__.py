@@ -123,6 +123,10 @@ class Solver:
     def last_error_index(self):
         return int(N.lib().pdas_last_error_index(self._h))
 
+    def set_wait_limit(self, microseconds):
+        """Limit of the handle's bounded inter-block waits (0: the 2 s default)."""
+        self._check(N.lib().pdas_set_wait_limit(self._h, int(microseconds)), "pdas_set_wait_limit")
+
     # -- argument marshalling ----------------------------------------------
     def _A(self, A):
         return _ptr(A, self.a_dtype, self.m * self.n, "A")

@@ -37,6 +37,7 @@ class Options(ctypes.Structure):
         ("drop_keep", ctypes.c_double),
         ("exact_passes", ctypes.c_int),
         ("infeasible", ctypes.c_int),
+        ("fp64_tier_tc", ctypes.c_int),
     ]
 
 
@@ -103,6 +104,7 @@ SIGNATURES = {
     "pdas_status_str": ([_I], ctypes.c_char_p),
     "pdas_last_error_index": ([_H], _I64),
     "pdas_last_error_message": ([_H], ctypes.c_char_p),
+    "pdas_set_wait_limit": ([_H, _I64], _I),
     "pdas_form_normal": ([_H, _P, _P, _P], _I),
     "pdas_copy_matrix": ([_H, _P, ctypes.POINTER(_I)], _I),
     "pdas_load_matrix": ([_H, _P, _I], _I),

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "pdas_internal.cuh"
+#include "syrk_dig.cuh"
 #include "syrk_tc.cuh"
 
 using namespace pdas;
@@ -42,15 +43,18 @@ struct pdas_ctx {
   int* flags = nullptr;
   Scalars* sc = nullptr;
   Scalars* sc_host = nullptr;  // pinned
-  double* M64 = nullptr;
+  int wait_us = 0;             // limit of the bounded inter-block waits (0: the 2 s default)
+  int* wait_pinned = nullptr;  // pinned copy of wait_us, the source of its copy into sc
+  double* M64 = nullptr;      // FP64 form; mixed forms: the FP64 tier's matrix (allocated at create)
   float* M32 = nullptr;
   double* dinv64 = nullptr;  // reciprocals of the pivots of the FP64 / FP32 factor
   float* dinv32 = nullptr;
   TcWorkspace tc{};
+  DigWorkspace dig{};  // FP64 tier on the tensor cores (BF16 A): digit planes
   int cur_f64 = 1;     // the workspace matrix in use is M64
   int refactored = 0;  // a mixed form switched to FP64 for good
   // column dropping for the FP64 factor of the mixed forms
-  void* akept = nullptr;        // m x n elements of A's dtype (lazily allocated)
+  void* akept = nullptr;        // m x n elements of A's dtype (mixed forms with drop_tol > 0)
   double* dkept = nullptr;      // n
   int* kidx = nullptr;          // n
   std::vector<double> dhost;
@@ -61,7 +65,7 @@ struct pdas_ctx {
   float2* d2 = nullptr;         // D as FP32 pairs (double-float formation)
   int last_normal_form = 3;     // pdas_iter_info.normal_form of the last formation
   bool have_factor = false;     // a factor from a previous step is in the workspace
-  double* adj = nullptr;        // adjoint vectors (5 n + m), lazily allocated
+  double* adj = nullptr;        // adjoint vectors (5 n + m)
   int4* chol_tasks = nullptr;   // task list of the tile Cholesky (FP32 factor)
   int chol_ntasks = 0;
   int* chol_state = nullptr;    // per-tile counters of the tile Cholesky
@@ -199,6 +203,8 @@ pdas_status device_status(pdas_ctx* h) {
 
 pdas_status reset_status(pdas_ctx* h) {
   CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->st));
+  if (h->wait_us > 0)  // a limit of the handle's own (pdas_set_wait_limit)
+    CK(cudaMemcpyAsync(&h->sc->wait_us, h->wait_pinned, sizeof(int), cudaMemcpyHostToDevice, h->st));
   return PDAS_OK;
 }
 
@@ -258,12 +264,6 @@ pdas_status gemv_t(pdas_ctx* h, const void* A, const double* u, int mode, const 
   return PDAS_OK;
 }
 
-pdas_status ensure_m64(pdas_ctx* h) {
-  if (!h->M64) CK(cudaMalloc(&h->M64, sizeof(double) * h->ldm * h->m));
-  if (!h->dinv64) CK(cudaMalloc(&h->dinv64, sizeof(double) * h->m));
-  return PDAS_OK;
-}
-
 bool want_fp64(const pdas_ctx* h) { return !is_mixed(h) || h->refactored; }
 
 size_t dtype_size(int dt) { return dt == PDAS_A_F64 ? 8 : dt == PDAS_A_F32 ? 4 : 2; }
@@ -295,9 +295,6 @@ pdas_status select_columns(pdas_ctx* h, int64_t* kept) {
     if (h->dhost[j] >= t) h->idx_host.push_back((int)j);
   const int64_t k = (int64_t)h->idx_host.size();
   if (k >= n) return PDAS_OK;
-  if (!h->akept) CK(cudaMalloc(&h->akept, dtype_size(h->opt.a_dtype) * h->m * n));
-  if (!h->dkept) CK(cudaMalloc(&h->dkept, sizeof(double) * n));
-  if (!h->kidx) CK(cudaMalloc(&h->kidx, sizeof(int) * n));
   CK(cudaMemcpyAsync(h->kidx, h->idx_host.data(), sizeof(int) * k, cudaMemcpyHostToDevice, h->st));
   *kept = k;
   return PDAS_OK;
@@ -306,8 +303,7 @@ pdas_status select_columns(pdas_ctx* h, int64_t* kept) {
 // a3: the normal matrix in the current precision.
 pdas_status form_normal(pdas_ctx* h, const void* A) {
   if (want_fp64(h)) {
-    pdas_status s = ensure_m64(h);
-    if (s != PDAS_OK) return s;
+    pdas_status s;
     h->cur_f64 = 1;
     int64_t kept = h->n;
     if (is_mixed(h) && (s = select_columns(h, &kept)) != PDAS_OK) return s;
@@ -315,8 +311,17 @@ pdas_status form_normal(pdas_ctx* h, const void* A) {
     // A mixed form whose A is exact in FP32 forms this matrix in double-float
     // on the FP32 pipes (FP64 remains the fallback when that factor fails).
     const bool df = is_mixed(h) && h->opt.a_dtype != PDAS_A_F64 && !h->no_df_once;
-    if (df && !h->d2) CK(cudaMalloc(&h->d2, sizeof(float2) * h->n));
-    h->last_normal_form = df ? 2 : 3;
+    // ... and, for BF16 A, on the tensor cores from exact fixed-point digit
+    // planes (FP64-grade), when the kept columns fit the digit workspace
+    const bool dig = df && h->opt.a_dtype == PDAS_A_BF16 && h->dig.planes && kept <= h->dig.kstride;
+    h->last_normal_form = dig ? 4 : df ? 2 : 3;
+    if (dig) {
+      int kl = 0;
+      CK(dig_syrk(h->st, &h->dig, (const __nv_bfloat16*)A, h->n, h->D, kept, kept < h->n ? h->kidx : nullptr,
+                  h->M64, h->ldm, h->sc, &kl));
+      h->launches += kl;
+      return PDAS_OK;
+    }
     return with_dtype(h->opt.a_dtype, [&](auto tag) -> pdas_status {
       using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
       const T* Aop = (const T*)A;
@@ -560,7 +565,7 @@ pdas_status direction(pdas_ctx* h, const void* A, const double* x, const double*
       STAGE_END(h);
       if (h->cur_f64) {
         if (h->last_factor_df) h->no_dffactor_once = true;        // the FP64 factor next
-        else if (h->last_normal_form == 2) h->no_df_once = true;  // form it in FP64 next
+        else if (h->last_normal_form == 2 || h->last_normal_form == 4) h->no_df_once = true;  // form it in FP64 next
         else if (h->last_kept < h->n) h->no_drop_once = true;      // then from every column
         else return st;                                            // the whole FP64 matrix is not SPD
       }
@@ -642,6 +647,7 @@ void pdas_default_options(pdas_options* opt) {
   opt->stall_theta = 1e-12;
   opt->stall_count = 5;
   opt->infeasible = 0;
+  opt->fp64_tier_tc = 1;
 }
 
 const char* pdas_status_str(pdas_status st) {
@@ -675,7 +681,7 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) ||
       !(opt.drop_tol >= 0) || !(opt.drop_keep >= 1.0) || opt.splits < 0 || (opt.exact_passes & ~1) ||
       opt.splits > 3 || (opt.infeasible & ~1) ||
-      opt.stall_count < 1 || !(opt.stall_theta >= 0))
+      opt.stall_count < 1 || !(opt.stall_theta >= 0) || (opt.fp64_tier_tc & ~1))
     return PDAS_ERR_ARG;
   if (opt.form == PDAS_BF16_IR && opt.a_dtype != PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
   // TF32 form: TF32 x 3 (splits 0 or 3) or one TF32 product (splits 1); FP64 or FP32 storage
@@ -721,13 +727,26 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (opt.form != PDAS_FP64 && opt.a_dtype != PDAS_A_F64) al((void**)&h->pairs, sizeof(float2) * n);  // n > m
   al((void**)&h->sc, sizeof(Scalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->sc_host, sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->wait_pinned, sizeof(int));
+  if (e == cudaSuccess) *h->wait_pinned = 0;
+  al((void**)&h->adj, sizeof(double) * (5 * n + m));  // pdas_backward
   if (e == cudaSuccess) {
-    if (opt.form == PDAS_FP64) {
-      al((void**)&h->M64, sizeof(double) * h->ldm * m);
-      al((void**)&h->dinv64, sizeof(double) * m);
-    } else {
+    // Every buffer of the FP64 tier of a mixed form is allocated here too, so
+    // that a solve allocates nothing once it runs (an out-of-memory error
+    // comes back from pdas_create, not from an iteration in mid-solve): the
+    // FP64 matrix and its pivots, D as FP32 pairs for the double-float
+    // formation, and the compact copy of the kept columns.
+    al((void**)&h->M64, sizeof(double) * h->ldm * m);
+    al((void**)&h->dinv64, sizeof(double) * m);
+    if (opt.form != PDAS_FP64) {
       al((void**)&h->M32, sizeof(float) * h->ldm * m);
       al((void**)&h->dinv32, sizeof(float) * m);
+      if (opt.a_dtype != PDAS_A_F64) al((void**)&h->d2, sizeof(float2) * n);
+      if (opt.drop_tol > 0) {
+        al((void**)&h->akept, dtype_size(opt.a_dtype) * m * n);
+        al((void**)&h->dkept, sizeof(double) * n);
+        al((void**)&h->kidx, sizeof(int) * n);
+      }
     }
   }
   if (e == cudaSuccess && opt.form != PDAS_FP64 && chol_tile_count(m) <= kTileCholMaxTiles) {
@@ -745,6 +764,8 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
     if (e == cudaSuccess)
       e = cudaMemcpy(h->chol_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess && opt.form != PDAS_FP64 && opt.a_dtype == PDAS_A_BF16 && opt.fp64_tier_tc)
+    e = dig_workspace_create(&h->dig, m, n);
   if (e == cudaSuccess && (opt.form == PDAS_BF16_IR || opt.form == PDAS_TF32_IR)) {
     e = tc_workspace_create(&h->tc, opt.form, opt.a_dtype, opt.splits, m, n);
     if (e == cudaErrorNotSupported) {
@@ -790,12 +811,22 @@ void pdas_destroy(pdas_handle h) {
   if (h->flags) cudaFree(h->flags);
   if (h->sc) cudaFree(h->sc);
   if (h->sc_host) cudaFreeHost(h->sc_host);
+  if (h->wait_pinned) cudaFreeHost(h->wait_pinned);
   tc_workspace_destroy(&h->tc);
+  dig_workspace_destroy(&h->dig);
   for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
   delete h;
 }
 
 int64_t pdas_last_error_index(pdas_handle h) { return h ? h->err_index : -1; }
+
+pdas_status pdas_set_wait_limit(pdas_handle h, int64_t microseconds) {
+  if (!h || microseconds < 0 || microseconds > 2147483647) return PDAS_ERR_ARG;
+  CK(cudaStreamSynchronize(h->st));  // no copy of the old value is still pending
+  h->wait_us = (int)microseconds;
+  *h->wait_pinned = (int)microseconds;
+  return PDAS_OK;
+}
 
 const char* pdas_last_error_message(pdas_handle h) { return h ? h->errmsg : ""; }
 
@@ -945,7 +976,6 @@ pdas_status pdas_backward(pdas_handle h, const void* A, const double* x, const d
   const int64_t m = h->m, n = h->n;
   pdas_status st = reset_status(h);
   if (st != PDAS_OK) return st;
-  if (!h->adj) CK(cudaMalloc(&h->adj, sizeof(double) * (5 * n + m)));
   double* lb = h->adj;      // dL/dc
   double* lc = lb + n;      // multiplier of X s = sigma
   double* wt = lc + n;      // A' la

@@ -21,7 +21,10 @@
 // code that name is a host-side stand-in, not a device address.  The device
 // address is fetched once per device with cudaGetSymbolAddress, with that
 // device current, on the first call made on it.  That first call also loads
-// the kernels' module, so make it before any stream capture.
+// the kernels' module, so make it before any stream capture.  The address is
+// kept for the life of the process: after cudaDeviceReset (which unloads the
+// module and frees the array) it would be stale, so a process that resets a
+// device must not call this entry point on that device again.
 #include <mutex>
 
 #include "pdas_internal.cuh"

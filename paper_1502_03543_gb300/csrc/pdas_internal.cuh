@@ -38,7 +38,7 @@ struct Scalars {
   int status;          // 0, or a pdas_status error detected on the device
   int fail_index;      // failing pivot for PDAS_ERR_NOT_SPD
   int bad_iterate;     // nonzero if some x_j <= 0 or s_j <= 0 (or not finite)
-  int pad;
+  int wait_us;         // limit of the bounded inter-block waits in microseconds (0: 2 s)
 };
 
 // Counters for the "last block finishes the reduction" pattern and the

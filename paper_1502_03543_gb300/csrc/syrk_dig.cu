@@ -1,0 +1,460 @@
+// syrk_dig.cu -- the FP64 tier's normal matrix M = A D A' (Section V) on the
+// tcgen05 tensor cores, for A stored in BF16, to FP64-grade accuracy.
+//
+// Why: once the FP32 factor of a mixed form breaks down (cond(A D A') beyond
+// FP32), the solve needs an FP64-grade M of the kept columns every
+// iteration.  On GB300 FP64 runs at 1/64 of the FP32 rate and the FP32-pipe
+// double-float SYRK does ~10 operations per term; both are far below what
+// the BF16 tensor cores give.  Here the products are made exact and the
+// accumulation exact, so the tensor cores' FP32 accumulator loses nothing.
+//
+// Fixed-point digits.  Row p of A (kept columns j < k) is scaled by 2^-ea_p,
+// ea_p the exponent of max_j |A_pj|, so a'_pj = A_pj 2^-ea_p lies in (-1, 1);
+// row q of B = D.*A (B_qj = D_j A_qj, formed in FP64) by 2^-eb_q.  Each is
+// written in balanced base-256 digits:
+//     a' = sum_{s<5} d_s 2^(-7-8s),    b' = sum_{t<8} g_t 2^(-7-8t),
+// every digit an integer in [-128, 128] (exact in BF16).  Five digits hold a
+// BF16 entry exactly down to 2^-32 of its row's largest; eight hold the FP64
+// B to 2^-63.  Then
+//     M_pq = 2^(ea_p + eb_q - 14) sum_w 2^(-8w) I_w,
+//     I_w  = sum_j sum_{s+t=w} d_s,pj g_t,qj          (integers),
+// for the 30 digit pairs with s + t <= 7 (the pairs dropped contribute at
+// most 2^-62 of 2^(ea_p + eb_q) per column).  Every product d g has
+// magnitude <= 2^14; a weight collects at most 5 pairs, so over a chunk of
+// 128 columns |I_w| <= 5 * 128 * 2^14 < 2^24: the FP32 accumulator holds
+// the chunk sum exactly, whatever its rounding.  The epilogue converts each
+// chunk's eight weight sums to integers and adds them, weighted by powers of
+// 2^8, exactly into two int64 sums per entry (weights 0-3 and 4-7); at the
+// end it combines the two in FP64 and applies the power-of-two scale.  The
+// only roundings left are the FP64 product D_j A_qj and the final FP64
+// combination.
+//
+// Kernel k_syrk_dig: one CTA per 128 x 32 lower-triangle tile (rows p of A,
+// rows q of B), 10 warps:
+//   warp 0      TMA producer: per stage of 64 columns one 3-D copy of the 5
+//               A digit planes (128 rows) and one of the 8 B digit planes
+//               (32 rows), 112 KB, into a ring of 2 stages;
+//   warp 1      allocates 512 TMEM columns (2 chunk buffers x 8 weights x 32
+//               columns); one lane issues tcgen05.mma.cta_group::1.kind::f16
+//               (M=128, N=32, K=16), 30 pairs x 4 per stage, pair (s, t)
+//               into the weight s + t accumulator of the current buffer;
+//   warps 2..9  warp w reads TMEM lanes 32 (w % 4).. and columns
+//               16 ((w - 2) / 4).. of every weight: per chunk 8 x 16 values,
+//               converted and added into int64 accumulators; then the
+//               buffer is handed back and, at the end, M_pq written in FP64.
+// Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
+// PDAS_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM, exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "syrk_dig.cuh"
+#include "tc_util.cuh"
+
+namespace pdas {
+
+namespace {
+
+using namespace tc;
+
+// 3-D tiled copy (coordinates innermost first) into shared memory; the box
+// lands as dim2 x dim1 x dim0 contiguous, completing its bytes on bar.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+constexpr int DBM = 128;                               // rows p of a tile (A digits)
+constexpr int DBN = 32;                                // rows q of a tile (B digits)
+constexpr int DBK = 64;                                // columns per stage (one 128-byte row)
+constexpr int SA = 5, SB = 8, WMAX = 7;                // digits of A and B, largest pair weight kept
+constexpr int NW = WMAX + 1;                           // weight accumulators
+constexpr int NPAIR = 30;                              // pairs (s, t), s < SA, t < SB, s + t <= WMAX
+constexpr int CHUNK_STAGES = 2;                        // 128 columns per exact chunk
+constexpr uint32_t A_PLANE = DBM * 128;                // 16 KB
+constexpr uint32_t B_PLANE = DBN * 128;                // 4 KB
+constexpr uint32_t STAGE_BYTES = SA * A_PLANE + SB * B_PLANE;  // 112 KB
+constexpr int STAGES = 2;
+constexpr uint32_t BUF_COLS = NW * DBN;                // 256 TMEM columns per chunk buffer
+constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;           // 512
+constexpr int NUM_THREADS = 320;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+constexpr uint32_t kIdesc = idesc_bf16(DBM, DBN);
+
+static_assert(NPAIR == SB + (SB - 1) + (SB - 2) + (SB - 3) + (SB - 4), "pair count");
+static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_syrk_dig(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const int2* __restrict__ tiles, int nk, int64_t m, const int* __restrict__ ea,
+               const int* __restrict__ eb, int64_t ldm, double* __restrict__ M, Scalars* sc) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars: full[STAGES] | empty[STAGES] | chunk_full[2] | chunk_free[2] | done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + STAGES + s); };
+  auto chunk_full = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
+  auto chunk_free = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
+  const uint32_t done_bar = smem_u32(bars + 2 * STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 tile = tiles[blockIdx.x];
+  const int p0 = tile.x * DBM, q0 = tile.y * DBN;
+  const int nchunks = (nk + CHUNK_STAGES - 1) / CHUNK_STAGES;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(chunk_full(b), 1);
+      mbar_init(chunk_free(b), 8);  // one arrival per epilogue warp
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t dst = sbase + s * STAGE_BYTES;
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        tma_load_3d(dst, &tmA, kb * DBK, p0, 0, full(s));
+        tma_load_3d(dst + SA * A_PLANE, &tmB, kb * DBK, q0, 0, full(s));
+        issued = kb + 1;
+      }
+      if (*abort_flag) {  // let every issued copy land before the CTA can exit
+        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+          mbar_wait(full(kb % STAGES), (uint32_t)(kb / STAGES) & 1u, nullptr);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nk && !*abort_flag; ++kb) {
+        const int c = kb / CHUNK_STAGES, buf = c & 1;
+        const bool chunk_start = (kb % CHUNK_STAGES) == 0;
+        if (chunk_start && c >= 2 &&
+            !mbar_wait(chunk_free(buf), (uint32_t)((c >> 1) - 1) & 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int s = kb % STAGES;
+        if (!mbar_wait(full(s), (uint32_t)(kb / STAGES) & 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t stage = sbase + s * STAGE_BYTES;
+        const uint32_t dbuf = tmem + (uint32_t)buf * BUF_COLS;
+#pragma unroll
+        for (int da = 0; da < SA; ++da) {
+          const uint64_t ad = sdesc_sw128(stage + da * A_PLANE);
+#pragma unroll
+          for (int dbg = 0; dbg < SB; ++dbg) {
+            if (da + dbg > WMAX) continue;
+            const uint64_t bd = sdesc_sw128(stage + SA * A_PLANE + dbg * B_PLANE);
+            const uint32_t d = dbuf + (uint32_t)((da + dbg) * DBN);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // 32 bytes (16 BF16) along K per MMA
+              // the first product of weight w in a chunk is pair (0, w) at its first K step
+              const uint32_t accum = (chunk_start && da == 0 && k == 0) ? 0u : 1u;
+              umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, accum);
+            }
+          }
+        }
+        umma_commit(empty(s));
+        if ((kb % CHUNK_STAGES) == CHUNK_STAGES - 1 || kb == nk - 1) umma_commit(chunk_full(buf));
+      }
+      umma_commit(done_bar);  // fires once every MMA issued above has completed
+      mbar_wait(done_bar, 0, nullptr);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3;         // TMEM lanes this warp may read
+    const int half = (warp - 2) >> 2;     // its 16 columns of each weight block
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 16);
+    // exact integer sums of this lane's row, 16 columns: hi = sum_{w<4} I_w 2^(8(3-w)),
+    // lo = sum_{w>=4} I_w 2^(8(7-w)) (|I_w| < 2^23.4 per chunk: int64 holds 2^15 chunks)
+    long long hi[16], lo[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+    int ok = 1;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      if (lane == 0) ok = mbar_wait(chunk_full(buf), (uint32_t)(c >> 1) & 1u, abort_flag) && !*abort_flag;
+      ok = __shfl_sync(0xffffffffu, ok, 0);  // warp-uniform for tcgen05.ld
+      if (!ok) break;
+      fence_after();
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        uint32_t r[16];
+        tmem_ld16(lane_addr + (uint32_t)buf * BUF_COLS + (uint32_t)(w * DBN), r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));  // an exact integer
+          if (w < 4) hi[j] += v * (1ll << (8 * (3 - w)));
+          else lo[j] += v * (1ll << (8 * (7 - w)));
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(chunk_free(buf));
+    }
+    if (ok) {
+      const int64_t p = p0 + quarter * 32 + lane;
+      if (p < m) {
+        const int ep = ea[p];
+        double* dst = M + p * ldm;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t q = (int64_t)q0 + half * 16 + j;
+          // sum_w 2^(-8w) I_w = 2^-24 (hi + 2^-32 lo), two FP64 roundings
+          if (q <= p) dst[q] = ldexp(fma((double)lo[j], 0x1p-32, (double)hi[j]), ep + eb[q] - 38);
+        }
+      }
+    } else if (lane == 0) {
+      *abort_flag = 1;
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// Exponents of the kept part of each row: ea_p with max_j |A_pj| < 2^ea_p and
+// eb_p with max_j |D_j A_pj| < 2^eb_p (frexp convention; 0 for a zero row).
+// One warp per row; column i of the kept set is idx[i] (idx null: i).
+__global__ void k_dig_rowexp(int64_t m, int64_t n, const __nv_bfloat16* __restrict__ A, const double* __restrict__ D,
+                             int64_t k, const int* __restrict__ idx, int* __restrict__ ea, int* __restrict__ eb) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < m;
+       p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const __nv_bfloat16* row = A + p * n;
+    double amax = 0.0, bmax = 0.0;
+    for (int64_t i = lane; i < k; i += 32) {
+      const int64_t j = idx ? idx[i] : i;
+      const double a = fabs((double)__bfloat162float(row[j]));
+      amax = fmax(amax, a);
+      bmax = fmax(bmax, a * D[j]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    }
+    if (lane == 0) {
+      int e1 = 0, e2 = 0;
+      if (amax > 0.0) frexp(amax, &e1);
+      if (bmax > 0.0) frexp(bmax, &e2);
+      ea[p] = e1;
+      eb[p] = e2;
+    }
+  }
+}
+
+// Balanced base-256 digits of the integer v (|v| < 2^(8 ND - 1) + 2^7):
+// dig[ND - 1] is the lowest; each in [-128, 128].
+template <int ND>
+__device__ __forceinline__ void balanced_digits(long long v, int (&dig)[ND]) {
+#pragma unroll
+  for (int t = ND - 1; t > 0; --t) {
+    const int low = (int)(((v + 128) & 255) - 128);
+    dig[t] = low;
+    v = (v - low) >> 8;  // exact: v - low is a multiple of 256
+  }
+  dig[0] = (int)v;
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
+  return (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(hi)) << 16);
+}
+
+// The digit planes: plane s of A (SA planes) and plane t of B (SB planes),
+// each mpad rows of stride kstride BF16, for the kept columns i < k (and
+// zeros up to the next multiple of 64).  a' 2^39 and b' 2^63 are integers
+// (up to the rounding of entries below 2^-32 and 2^-11 of the row's
+// largest), and their balanced base-256 digits are the planes' entries.
+// One thread writes 8 consecutive columns of one row to every plane.
+__global__ void k_dig_planes(int64_t m, int64_t n, const __nv_bfloat16* __restrict__ A, const double* __restrict__ D,
+                             int64_t k, int64_t kfill, const int* __restrict__ idx, const int* __restrict__ ea,
+                             const int* __restrict__ eb, int64_t mpad, int64_t kstride,
+                             __nv_bfloat16* __restrict__ planes) {
+  const int64_t groups = kfill / 8;
+  const int64_t total = m * groups;
+  const int64_t plane = mpad * kstride;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = g / groups, i0 = (g % groups) * 8;
+    const double sa = ldexp(1.0, 39 - ea[p]), sb = ldexp(1.0, 63 - eb[p]);
+    int da[8][SA], db[8][SB];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t i = i0 + e;
+      double a = 0.0, b = 0.0;
+      if (i < k) {
+        const int64_t j = idx ? idx[i] : i;
+        a = (double)__bfloat162float(A[p * n + j]);
+        b = a * D[j];
+      }
+      balanced_digits<SA>(__double2ll_rn(a * sa), da[e]);
+      balanced_digits<SB>(__double2ll_rn(b * sb), db[e]);
+    }
+    __nv_bfloat16* rowp = planes + p * kstride + i0;
+#pragma unroll
+    for (int s = 0; s < SA; ++s)
+      *reinterpret_cast<uint4*>(rowp + s * plane) = make_uint4(bf16_pair(da[0][s], da[1][s]), bf16_pair(da[2][s], da[3][s]),
+                                                               bf16_pair(da[4][s], da[5][s]), bf16_pair(da[6][s], da[7][s]));
+#pragma unroll
+    for (int t = 0; t < SB; ++t)
+      *reinterpret_cast<uint4*>(rowp + (SA + t) * plane) =
+          make_uint4(bf16_pair(db[0][t], db[1][t]), bf16_pair(db[2][t], db[3][t]), bf16_pair(db[4][t], db[5][t]),
+                     bf16_pair(db[6][t], db[7][t]));
+  }
+}
+
+// ---- host side ---------------------------------------------------------------
+struct DigHost {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  CUtensorMap mapA, mapB;
+  int2* tiles = nullptr;
+  int ntiles = 0;
+};
+
+cudaError_t get_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  *out = fn;
+  return cudaSuccess;
+}
+
+// 3-D BF16 map over `planes` consecutive digit planes: dims {kstride (K,
+// innermost), mpad, planes}, box {64 (one 128-byte row), rows, planes},
+// 128-byte swizzle.  The box lands in shared memory as planes x rows x 128 B.
+cudaError_t encode_planes(DigHost* hs, CUtensorMap* map, const void* base, int64_t mpad, int64_t kstride, int planes,
+                          int rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)kstride, (cuuint64_t)mpad, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(kstride * 2), (cuuint64_t)(mpad * kstride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)DBK, (cuuint32_t)rows, (cuuint32_t)planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = hs->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t dig_workspace_create(DigWorkspace* w, int64_t m, int64_t n) {
+  w->m = m;
+  w->mpad = (m + DBM - 1) / DBM * DBM;
+  const int64_t kmax = std::min<int64_t>(n, kDigMaxK);
+  w->kstride = (kmax + DBK - 1) / DBK * DBK;
+  DigHost* hs = new (std::nothrow) DigHost();
+  if (!hs) return cudaErrorMemoryAllocation;
+  w->host = hs;
+  cudaError_t e = get_encoder(&hs->encode);
+  if (e == cudaSuccess) e = cudaMalloc(&w->planes, sizeof(__nv_bfloat16) * (size_t)(SA + SB) * w->mpad * w->kstride);
+  // zero once: rows m..mpad of every plane are never written and must read as 0
+  if (e == cudaSuccess) e = cudaMemset(w->planes, 0, sizeof(__nv_bfloat16) * (size_t)(SA + SB) * w->mpad * w->kstride);
+  if (e == cudaSuccess) e = cudaMalloc(&w->ea, sizeof(int) * (size_t)m);
+  if (e == cudaSuccess) e = cudaMalloc(&w->eb, sizeof(int) * (size_t)w->mpad);
+  if (e == cudaSuccess) e = cudaMemset(w->eb, 0, sizeof(int) * (size_t)w->mpad);
+  // Lower-triangle tiles (I, J) of 128 x 32 (some row p >= some column q),
+  // in super-tiles of G row blocks x 4G column blocks (about one wave of
+  // 152 CTAs), so the CTAs resident together share their digit planes in L2.
+  std::vector<int2> tl;
+  const int64_t nI = w->mpad / DBM, nJ = (m + DBN - 1) / DBN;
+  const int64_t G = 6;
+  for (int64_t PI = 0; PI < nI; PI += G)
+    for (int64_t PJ = 0; PJ < nJ; PJ += 4 * G)
+      for (int64_t I = PI; I < nI && I < PI + G; ++I)
+        for (int64_t J = PJ; J < nJ && J < PJ + 4 * G && J * DBN <= I * DBM + DBM - 1; ++J)
+          tl.push_back(make_int2((int)I, (int)J));
+  hs->ntiles = (int)tl.size();
+  if (e == cudaSuccess) e = cudaMalloc(&hs->tiles, sizeof(int2) * tl.size());
+  if (e == cudaSuccess) e = cudaMemcpy(hs->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapA, w->planes, w->mpad, w->kstride, SA, DBM);
+  if (e == cudaSuccess)
+    e = encode_planes(hs, &hs->mapB, (const __nv_bfloat16*)w->planes + (size_t)SA * w->mpad * w->kstride, w->mpad,
+                      w->kstride, SB, DBN);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_dig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  return e;
+}
+
+void dig_workspace_destroy(DigWorkspace* w) {
+  if (w->planes) cudaFree(w->planes);
+  if (w->ea) cudaFree(w->ea);
+  if (w->eb) cudaFree(w->eb);
+  DigHost* hs = static_cast<DigHost*>(w->host);
+  if (hs) {
+    if (hs->tiles) cudaFree(hs->tiles);
+    delete hs;
+  }
+  *w = DigWorkspace{};
+}
+
+cudaError_t dig_syrk(cudaStream_t st, DigWorkspace* w, const __nv_bfloat16* A, int64_t n, const double* D, int64_t k,
+                     const int* idx, double* M64, int64_t ldm, Scalars* sc, int* launches) {
+  *launches = 0;
+  if (k < 1 || k > w->kstride || w->m < 1) return cudaErrorInvalidValue;
+  DigHost* hs = static_cast<DigHost*>(w->host);
+  const int64_t m = w->m;
+  const int64_t kfill = (k + DBK - 1) / DBK * DBK;  // the stages read columns < kfill
+  {
+    const int64_t warps = m, threads = warps * 32;
+    const unsigned grid = (unsigned)std::min<int64_t>((threads + 255) / 256, 4736);
+    k_dig_rowexp<<<grid, 256, 0, st>>>(m, n, A, D, k, idx, w->ea, w->eb);
+  }
+  {
+    const int64_t work = m * (kfill / 8);
+    const unsigned grid = (unsigned)std::min<int64_t>((work + 255) / 256, 4736);
+    k_dig_planes<<<grid, 256, 0, st>>>(m, n, A, D, k, kfill, idx, w->ea, w->eb, w->mpad, w->kstride,
+                                       static_cast<__nv_bfloat16*>(w->planes));
+  }
+  const int nk = (int)(kfill / DBK);
+  k_syrk_dig<<<(unsigned)hs->ntiles, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapA, hs->mapB, hs->tiles, nk, m, w->ea,
+                                                                      w->eb, ldm, M64, sc);
+  *launches = 3;
+  return cudaGetLastError();
+}
+
+}  // namespace pdas

@@ -9,8 +9,9 @@
 // diagonal tile is accurate enough; the plain FP64 form keeps substitution.
 //
 // One launch per solve.  Blocks take block rows in order from a ticket
-// counter and wait (bounded, 2 s) for the solution blocks they depend on,
-// which were handed out earlier: no deadlock.  The solution vector is filled
+// counter and wait (bounded: 2 s, or the handle's own limit) for the
+// solution blocks they depend on, which were handed out earlier: no
+// deadlock.  The solution vector is filled
 // with an all-ones bit pattern before the launch (a value the solves cannot
 // produce: each entry is an FP32 sum widened to FP64, whose low 29 bits are
 // zero), and a consumer polls the entries it needs until none holds it, so
@@ -77,7 +78,7 @@ __device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
 // waited for and read as 0.  Returns false on a timeout or a failed status.
 template <int N>
 __device__ __forceinline__ bool poll_entries(const double* p, const bool (&valid)[N], double (&out)[N], Scalars* sc) {
-  const uint64_t t0 = global_ns();
+  const uint64_t t0 = global_ns(), limit = wait_limit_ns(sc);
   for (;;) {
     bool mine = true;
 #pragma unroll
@@ -87,7 +88,7 @@ __device__ __forceinline__ bool poll_entries(const double* p, const bool (&valid
     }
     if (__all_sync(0xffffffffu, mine)) return true;
     if (dev_failed(sc)) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > limit) {
       atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
       return false;
     }

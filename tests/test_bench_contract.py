@@ -44,3 +44,28 @@ def test_form_terms():
     assert bench.form_terms("bf16_ir", 0) == 3 and bench.form_terms("bf16_ir", 2) == 2
     assert bench.form_terms("tf32_ir", 0) == 3 and bench.form_terms("tf32_ir", 1) == 1
     assert bench.form_terms("tf32_ir", 3) == 3 and bench.form_terms("fp64", 0) == 1
+
+
+def test_stop_margin_and_traffic_record():
+    assert abs(bench.stop_margin(7.66e-9, 1e-8) - 0.1158) < 1e-3
+    assert bench.stop_margin(0.0, 1e-8) is None
+    assert abs(bench.stop_margin(-9.5e-9, 1e-8) - 0.0223) < 1e-3
+    # the SYRK traffic figure is reported only for the kernel source it was captured on
+    t = bench.syrk_traffic("dense_8192x32768_bf16_colscaled", 3)
+    cap = bench.SYRK_TRAFFIC_CAPTURES[("dense_8192x32768_bf16_colscaled", 3)]
+    assert t == (cap["bytes"] if cap["digest"] == bench.syrk_source_digest() else None)
+    assert bench.syrk_traffic("dense_4096x16384_bf16_colscaled", 3) is None
+    peaks = dict(bf16_sus=1708.8, source="measured", tf32=900.0, fp32=70.0, fp64=1.1)
+    assert bench.syrk_roofline("tf32_ir", 2048, 8192, 3, 0.2, peaks)["peak"] == 900.0
+    assert bench.syrk_roofline("fp64", 2048, 8192, 1, 30.0, peaks)["peak"] == 1.1
+    assert bench.chol_roofline("fp64", 8192, 190.0, peaks)["peak"] == 1.1
+
+
+def test_both_arms_share_the_config():
+    import lpgen
+    lp = lpgen.workload("dense_64x128_f64", 0)
+    a = bench.bench_config(lp, "dense_64x128_f64", "bf16_ir", 3, 1)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "dense_64x128_f64", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         check=True, cwd=ROOT, timeout=600).stdout
+    assert json.loads(out.strip().splitlines()[-1])["config"] == a

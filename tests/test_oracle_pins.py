@@ -430,10 +430,38 @@ def pin_residuals(o, seed=3):
     return err < 1e-13, "%.1e" % err
 
 
+def pin_stop_rules(o, seed=5):
+    """The loop's other stops (the cap of 500 and the stall rule of five steps
+    shorter than 1e-12 are readings: the paper states neither).  A run capped
+    at 3 iterations returns MAX_ITER after exactly 3 steps, on the uncapped
+    run's third iterate bit for bit.  With alpha chosen so that every step has
+    theta = alpha/psi = 0.5e-12 the run stops STALLED after exactly its fifth
+    step; with theta = 2e-12 it does not stall within 8 steps (MAX_ITER).  The
+    iterate barely moves at these step lengths, so psi stays within 1e-9 of
+    its value at the start and theta within the factor 2 of the threshold.
+    (The literal zero-direction stop cannot fire from an interior point:
+    dx_j/x_j + ds_j/s_j = -1 for every j, pinned by the Newton identities.)"""
+    lp = lpgen.generate(6, 15, seed=seed)
+    full = o.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, keep_iterates=True)
+    cap = o.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, max_iter=3)
+    ok = full["iters"] > 3 and cap["status"] == oracle.MAX_ITER and cap["iters"] == 3
+    n, m = lp.n, lp.m
+    ok &= bool(np.array_equal(cap["x"], full["iterates"][2][:n]) and np.array_equal(cap["y"], full["iterates"][2][n:n + m]))
+    d = o.direction(lp.A64, lp.x0, lp.s0)
+    psi0 = o.psi(lp.x0, lp.s0, d["dx"], d["ds"])
+    ok &= psi0 > 1.0
+    lo = o.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, alpha=0.5e-12 * psi0, max_iter=50)
+    hi = o.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0, alpha=2e-12 * psi0, max_iter=8)
+    ok &= lo["status"] == oracle.STALLED and lo["iters"] == 5
+    ok &= hi["status"] == oracle.MAX_ITER and hi["iters"] == 8
+    return ok, "cap=%d/%d lo=%d/%d hi=%d/%d psi0=%.3g" % (cap["status"], cap["iters"], lo["status"], lo["iters"],
+                                                          hi["status"], hi["iters"], psi0)
+
+
 PINS = [pin_textbook_lp, pin_full_step_branch, pin_brute_force, pin_m1_closed_form, pin_newton_identities, pin_sherman_morrison,
         pin_normal_matrix, pin_cholesky, pin_triangular, pin_gemv, pin_psi_theta_step, pin_run_invariants,
         pin_backward_error, pin_not_spd, pin_infeasible_newton_system, pin_infeasible_feasible_start,
-        pin_infeasible_runs, pin_residuals]
+        pin_infeasible_runs, pin_residuals, pin_stop_rules]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -490,6 +518,11 @@ MUTANTS = [
      "rdn = fmax(rdn, fabs((c[j] - w[j]) + s[j]));"),
     ("primal residual norm uses b only", "rp = fmax(rp, fabs(b[p] - t[p]));", "rp = fmax(rp, fabs(b[p]));"),
     ("variant theta full step at psi <= 1", "psi <= alpha ? 1.0 : alpha / psi", "psi <= 1.0 ? 1.0 : alpha / psi"),
+    # the stop rules of the loop
+    ("stall count", "if (small_steps >= 5) {", "if (small_steps >= 6) {"),
+    ("stall threshold", "small_steps = theta < 1e-12 ? small_steps + 1 : 0;",
+     "small_steps = theta < 1e-11 ? small_steps + 1 : 0;"),
+    ("stall never counted", "small_steps = theta < 1e-12 ? small_steps + 1 : 0;", "small_steps = 0;"),
 ]
 
 

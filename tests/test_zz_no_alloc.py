@@ -2,7 +2,8 @@
 (code running under someone else's stream capture, memory owned by another
 framework's pool, real-time loops).  It keeps its scratch in a fixed
 file-scope device array instead of a handle's workspace; these checks call it
-through the C ABI and compare it with the handle-based pdas_gemv_t.
+through the C ABI and compare it with the handle-based pdas_gemv_t and with
+the oracle's A' u.
 
 This file is collected last on purpose, so that a failure here cannot stop
 a run of the other tests early."""
@@ -13,6 +14,7 @@ import pytest
 import torch
 
 import lpgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +55,7 @@ def test_noalloc_matches_handle_entry_point_twice(m, n, storage):
         # two FP64 summation orders of the same m-term column sums
         bound = 2 * (m * U64 / (1 - m * U64)) * (absA.T @ np.abs(u.cpu().numpy()))
         assert np.all(np.abs(got - ref) <= bound)
+        assert np.all(np.abs(got - oracle.gemv_t(lp.A64, u.cpu().numpy())) <= bound)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
