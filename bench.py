@@ -628,6 +628,73 @@ def run_batch(args):
                           slowest_lp_ms=float(out["time_us"].max() * 1e-3))))
 
 
+def run_woodbury(args):
+    """The paper's own solver of the normal equations (the Egidi-Maponi
+    rank-one recurrence from (A A')^{-1} A, pdas_woodbury.h) against the
+    library's FP64 direction on the same workload at the seeded start: one
+    JSON line with both times, their agreement and the recurrence's roofline
+    (4 m flops per column and step: a dot product and an axpy, FP64)."""
+    import torch
+
+    import paper_1502_03543_gb300 as P
+    from paper_1502_03543_gb300 import build as B
+
+    B.build()
+    lp = lpgen.workload(args.workload, seed=0)
+    if lp.storage == "bf16":
+        A = torch.from_numpy(lp.A_store.view(np.int16)).view(torch.bfloat16).cuda()
+    else:
+        A = torch.from_numpy(np.ascontiguousarray(lp.A_store)).cuda()
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    x, s = dv(lp.x0), dv(lp.s0)
+    D = x / s
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with P.Solver(lp.m, lp.n, "fp64", A.dtype) as S:
+        r = S.gemv(A, x)
+        for _ in range(max(1, args.warmup)):
+            S.direction(A, x, s)
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(args.steps):
+            _, dy_chol, _, _ = S.direction(A, x, s)
+        e1.record()
+        torch.cuda.synchronize()
+        chol_ms = e0.elapsed_time(e1) / args.steps
+    with P.WoodburySolver(lp.m, lp.n, A.dtype) as W:
+        e0, e1 = ev(), ev()
+        e0.record()
+        W.prepare(A)
+        e1.record()
+        torch.cuda.synchronize()
+        prep_ms = e0.elapsed_time(e1)
+        W.solve(A, D, r)  # warm-up
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(args.steps):
+            dy_wb, min_den = W.solve(A, D, r)
+        e1.record()
+        torch.cuda.synchronize()
+        wb_ms = e0.elapsed_time(e1) / args.steps
+    m, n = lp.m, lp.n
+    flops = 4.0 * m * n * (n + 1) / 2.0
+    peaks = load_peaks()
+    probe = probe_peaks() if not args.no_peak_probe else {}
+    peak = probe.get("fp64", 1.25)
+    achieved = flops / (wb_ms * 1e-3) / 1e12
+    diff = float((dy_wb - dy_chol).abs().max() / dy_chol.abs().max())
+    print(json.dumps(dict(metric="normal-equations solve: Woodbury recurrence vs Cholesky direction (FP64)",
+                          workload=args.workload, m=m, n=n, woodbury_solve_ms=round(wb_ms, 3),
+                          woodbury_prepare_ms=round(prep_ms, 3), cholesky_direction_ms=round(chol_ms, 3),
+                          dy_max_rel_diff=diff, min_den=min_den, steps=args.steps,
+                          roofline=dict(bound="alu", achieved=round(achieved, 4), peak=peak, unit="TFLOP/s",
+                                        frac=round(achieved / peak, 4), traffic=None,
+                                        kernel="k_wb_step (the rank-one recurrence)",
+                                        peak_note="fp64 dense, burst, of measured (matmul probe)" if probe else
+                                        "fp64 nominal", algorithmic_flops_per_solve=flops,
+                                        hbm_bytes_per_solve=16.0 * m * n * (n + 1) / 2.0,
+                                        hbm_peak=peaks["hbm"]))))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -647,11 +714,15 @@ def main():
     ap.add_argument("--kernel", choices=["step", "normal", "factor"], default="step",
                     help="normal: time only the normal-matrix stage; factor: also the Cholesky (for profiles)")
     ap.add_argument("--batch", action="store_true", help="time the 512-LP batch configuration instead")
+    ap.add_argument("--woodbury", action="store_true",
+                    help="time the paper's rank-one (Woodbury) solver against the Cholesky direction instead")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step" and not args.batch:
+    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step" and not (args.batch or args.woodbury):
         ap.error("--warmup must be >= 3")
     if args.batch:
         run_batch(args)
+    elif args.woodbury:
+        run_woodbury(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.kernel in ("normal", "factor"):

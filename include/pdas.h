@@ -113,6 +113,9 @@ typedef struct {
                               tensor cores from exact fixed-point BF16 digit planes of A and of
                               D.*A (FP64-grade: products and sums exact, one FP64 rounding at
                               the end); 0 = double-float on the FP32 pipes (normal_form 2)    (1) */
+  double df_factor_floor;  /* mixed forms in the FP64 tier: the factor is the double-float tile
+                              factor (FP32 pipes) while the relative gap of the iterate is above
+                              this, the FP64 factor below it; 0 = double-float to the end  (1e-6) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */

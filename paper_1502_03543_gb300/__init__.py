@@ -17,7 +17,7 @@ import torch
 
 from . import _native as N
 
-__all__ = ["Solver", "PdasError", "FORMS", "A_DTYPES", "solve_lp"]
+__all__ = ["Solver", "BatchSolver", "WoodburySolver", "PdasError", "FORMS", "A_DTYPES", "solve_lp"]
 
 FORMS = {"fp64": N.FP64, "tf32_ir": N.TF32_IR, "bf16_ir": N.BF16_IR, "fp32_ir": N.FP32_IR}
 A_DTYPES = {torch.float64: N.A_F64, torch.float32: N.A_F32, torch.bfloat16: N.A_BF16}
@@ -340,3 +340,55 @@ def solve_lp(A, b, c, x0, y0, s0, solver, alpha=0.95, tol=1e-8):
     """Differentiable LP solve through libpdas: returns x*; gradients with
     respect to A, b, c come from the adjoint at the final iterate."""
     return _LPSolve.apply(A, b, c, x0, y0, s0, solver, alpha, tol)
+
+
+class WoodburySolver:
+    """A libpdas Woodbury handle (pdas_woodbury.h): the paper's own solver of
+    (A D A') x = r, the Egidi-Maponi rank-one recurrence from (A A')^{-1} A,
+    for comparison with the Cholesky path.  prepare(A) once per A, then
+    solve(A, D, r) -> (x, smallest |den_l|)."""
+
+    def __init__(self, m, n, a_dtype=torch.float64, stream=None):
+        self.m, self.n, self.a_dtype = int(m), int(n), a_dtype
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = N.lib().pdas_woodbury_create(self.m, self.n, A_DTYPES[a_dtype], ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.byref(h))
+        if st != N.OK:
+            raise PdasError(st, "pdas_woodbury_create")
+        self._h = h
+
+    def _check(self, st, where):
+        if st != N.OK:
+            detail = N.lib().pdas_woodbury_last_error_message(self._h).decode() if st == N.ERR_CUDA else ""
+            raise PdasError(st, where, detail)
+
+    def prepare(self, A):
+        self._check(N.lib().pdas_woodbury_prepare(self._h, _ptr(A, self.a_dtype, self.m * self.n, "A")),
+                    "pdas_woodbury_prepare")
+
+    def solve(self, A, D, r):
+        x = torch.empty(self.m, dtype=torch.float64, device=r.device)
+        den = ctypes.c_double(0.0)
+        self._check(N.lib().pdas_woodbury_solve(self._h, _ptr(A, self.a_dtype, self.m * self.n, "A"),
+                                                _ptr(D, torch.float64, self.n, "D"),
+                                                _ptr(r, torch.float64, self.m, "r"), _ptr(x), ctypes.byref(den)),
+                    "pdas_woodbury_solve")
+        return x, den.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().pdas_woodbury_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

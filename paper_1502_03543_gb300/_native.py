@@ -1,4 +1,5 @@
-"""ctypes declarations of libpdas (include/pdas.h, include/pdas_components.h).
+"""ctypes declarations of libpdas (include/pdas.h, include/pdas_components.h,
+include/pdas_batch.h, include/pdas_woodbury.h).
 
 Loading fails loudly: there is no CPU fallback.  Build the library with
 ``python -m paper_1502_03543_gb300.build`` first.
@@ -38,6 +39,7 @@ class Options(ctypes.Structure):
         ("exact_passes", ctypes.c_int),
         ("infeasible", ctypes.c_int),
         ("fp64_tier_tc", ctypes.c_int),
+        ("df_factor_floor", ctypes.c_double),
     ]
 
 
@@ -127,6 +129,11 @@ SIGNATURES = {
     "pdas_batch_destroy": ([_H], None),
     "pdas_profile_enable": ([_H, _I], _I),
     "pdas_profile_read": ([_H, ctypes.POINTER(Profile)], _I),
+    "pdas_woodbury_create": ([_I64, _I64, _I, _P, ctypes.POINTER(_H)], _I),
+    "pdas_woodbury_prepare": ([_H, _P], _I),
+    "pdas_woodbury_solve": ([_H, _P, _P, _P, _P, ctypes.POINTER(_D)], _I),
+    "pdas_woodbury_last_error_message": ([_H], ctypes.c_char_p),
+    "pdas_woodbury_destroy": ([_H], None),
 }
 
 _lib = None

@@ -363,20 +363,18 @@ pdas_status form_normal(pdas_ctx* h, const void* A) {
 }
 
 // The FP64 tier of a mixed form factors with the double-float tile factor
-// (~5x faster than the FP64 factor on GB300's FP64 pipes) while the relative
-// gap of the iterate exceeds this floor, and with the FP64 factor below it.
-// In the last iterations the forward error of the refined direction sets the
-// gap that can be reached (the refinement accepts on a backward-error test),
-// and a slightly different preconditioner there moved the gap-1e-8 run of
-// the 8192 x 32768 problem from 54 iterations to 80.
-constexpr double kDfFactorGapFloor = 1e-6;
-
+// (~3.5x faster than the FP64 factor on GB300's FP64 pipes) while the
+// relative gap of the iterate exceeds opt.df_factor_floor, and with the FP64
+// factor below it.  In the last iterations the forward error of the refined
+// direction sets the gap that can be reached (the refinement accepts on a
+// backward-error test), and a slightly different preconditioner there moved
+// the gap-1e-8 run of the 8192 x 32768 problem from 54 iterations to 80.
 pdas_status factor(pdas_ctx* h) {
   h->last_factor_df = false;
   if (h->cur_f64 && is_mixed(h) && h->chol_ntasks > 0 && !h->no_dffactor_once &&
-      h->last_rel_gap > kDfFactorGapFloor) {
+      h->last_rel_gap > h->opt.df_factor_floor) {
     // FP64 tier of a mixed form: the double-float tile factor (FP32 pipes),
-    // while the iterate is not yet close to the optimum (see kDfFactorGapFloor)
+    // while the iterate is not yet close to the optimum
     h->last_factor_df = true;
     KL(cholesky_tiles_df(h->st, h->m, h->ldm, h->M64, h->dinv64, h->chol_tasks, h->chol_ntasks, h->chol_state,
                          h->tickets + T_CHOL, h->sc),
@@ -648,6 +646,7 @@ void pdas_default_options(pdas_options* opt) {
   opt->stall_count = 5;
   opt->infeasible = 0;
   opt->fp64_tier_tc = 1;
+  opt->df_factor_floor = 1e-6;
 }
 
 const char* pdas_status_str(pdas_status st) {
@@ -681,7 +680,8 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   if (opt.max_iter < 1 || opt.refine_max < 0 || !(opt.refine_tol > 0) || !(opt.refine_be >= 0) ||
       !(opt.drop_tol >= 0) || !(opt.drop_keep >= 1.0) || opt.splits < 0 || (opt.exact_passes & ~1) ||
       opt.splits > 3 || (opt.infeasible & ~1) ||
-      opt.stall_count < 1 || !(opt.stall_theta >= 0) || (opt.fp64_tier_tc & ~1))
+      opt.stall_count < 1 || !(opt.stall_theta >= 0) || (opt.fp64_tier_tc & ~1) ||
+      !(opt.df_factor_floor >= 0))
     return PDAS_ERR_ARG;
   if (opt.form == PDAS_BF16_IR && opt.a_dtype != PDAS_A_BF16) return PDAS_ERR_UNSUPPORTED;
   // TF32 form: TF32 x 3 (splits 0 or 3) or one TF32 product (splits 1); FP64 or FP32 storage

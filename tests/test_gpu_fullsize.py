@@ -155,18 +155,21 @@ def test_tile_cholesky_fp32_full_size(pdas, case):
 
 
 def test_double_float_tile_factor_full_size(pdas, case):
-    """The FP64 tier of a mixed form: the normal matrix formed in
-    double-float (the rule dspread_refactor = 1e-300 moves the handle to the
-    tier at once) and factored by the same tile task list in double-float
-    (hi + lo FP32 pairs: every multiply-add exact to a few units of 2^-46),
-    then solved by FP64 substitution.  g = (m + 1) 2^-43 is the Cholesky
-    bound gamma_{m+1} at a unit roundoff of 2^-43."""
+    """The FP64 tier of a mixed form (the rule dspread_refactor = 1e-300
+    moves the handle to the tier at once): the normal matrix formed by the
+    tier (on the tensor cores from digit planes when the kept columns fit
+    them, as at 4096 x 16384, else in double-float, as at 8192 x 32768 where
+    all 32768 columns are kept at the start) and factored by the same tile
+    task list in double-float (hi + lo FP32 pairs: every multiply-add exact
+    to a few units of 2^-46), then solved by FP64 substitution.
+    g = (m + 1) 2^-43 is the Cholesky bound gamma_{m+1} at a unit roundoff of
+    2^-43."""
     lp, A = case
     m, n = lp.m, lp.n
     x0, s0 = dv(lp.x0), dv(lp.s0)
     with pdas.Solver(m, n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
         _, _, _, info = S.direction(A, x0, s0)
-        assert info["used_fp64"] == 1 and info["normal_form"] == 2
+        assert info["used_fp64"] == 1 and info["normal_form"] == (4 if n <= 16384 else 2)
         S.form_normal(A, x0, s0)
         M = host64(S.copy_matrix())
         S.factor()  # no step taken yet: the gap is unknown, so the double-float factor runs
