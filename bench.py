@@ -348,7 +348,10 @@ def run_reference(args):
 
 def run_normal_only(args):
     """Times the normal-matrix stage alone (pdas_form_normal: D = x/s and
-    M = A D A' at the seeded start), for kernel profiles and the roofline."""
+    M = A D A' at the seeded start), for kernel profiles and the roofline.
+    --tier2: the FP64 tier's formation instead (the handle is moved to the
+    tier by one direction under dspread_refactor = 1e-300): the tensor-core
+    digit planes when the kept columns fit them (BF16 A), else double-float."""
     import torch
 
     import paper_1502_03543_gb300 as P
@@ -364,7 +367,12 @@ def run_normal_only(args):
     x = torch.from_numpy(lp.x0).cuda()
     s = torch.from_numpy(lp.s0).cuda()
     opts = {"splits": args.splits} if args.splits else {}
+    if args.tier2:
+        opts["dspread_refactor"] = 1e-300
     S = P.Solver(lp.m, lp.n, args.form, a_dtype, **opts)
+    if args.tier2:
+        _, _, _, info = S.direction(A, x, s)
+        normal_form = info["normal_form"]
     factor = args.kernel == "factor"
     for _ in range(args.warmup):
         S.form_normal(A, x, s)
@@ -390,7 +398,18 @@ def run_normal_only(args):
     ms = prof["ms"]["normal"] / max(1, prof["calls"]["normal"])
     splits = form_terms(args.form, args.splits)
     peaks = load_peaks()
-    roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, peaks, args.workload)
+    if args.tier2:
+        # algorithmic m(m+1)n flops; the digit planes execute 30 pair products
+        flops = float(lp.m) * (lp.m + 1) * lp.n
+        terms = 30 if normal_form == 4 else 1
+        achieved = flops / (ms * 1e-3) / 1e12
+        roof = dict(bound="tensor" if normal_form == 4 else "alu", achieved=round(achieved, 3),
+                    peak=peaks["bf16_sus"], unit="TFLOP/s", frac=round(achieved / peaks["bf16_sus"], 4),
+                    traffic=None, kernel="FP64-tier normal matrix (normal_form %d)" % normal_form,
+                    executed_frac=round(achieved * terms / peaks["bf16_sus"], 4), pair_products=terms,
+                    peak_note="bf16 dense, sustained, of %s" % peaks["source"])
+    else:
+        roof = syrk_roofline(args.form, lp.m, lp.n, splits, ms, peaks, args.workload)
     out = dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits, ms_per_launch=ms,
                launches=prof["launches"], wall_s=wall, roofline=roof)
     if factor:
@@ -713,6 +732,7 @@ def main():
                     help="reference arm: seconds of oracle iterations to fit the run into")
     ap.add_argument("--kernel", choices=["step", "normal", "factor"], default="step",
                     help="normal: time only the normal-matrix stage; factor: also the Cholesky (for profiles)")
+    ap.add_argument("--tier2", action="store_true", help="--kernel normal: the FP64 tier's formation")
     ap.add_argument("--batch", action="store_true", help="time the 512-LP batch configuration instead")
     ap.add_argument("--woodbury", action="store_true",
                     help="time the paper's rank-one (Woodbury) solver against the Cholesky direction instead")
