@@ -647,6 +647,55 @@ def run_batch(args):
                           slowest_lp_ms=float(out["time_us"].max() * 1e-3))))
 
 
+def run_batch_adjoint(args):
+    """The differentiable batch (256 LPs of 128 x 384, FP32, gap 1e-6; loss
+    sum_i w_i' x*_i, w ~ N(0,1)): the batch solve and pdas_batch_backward
+    (every LP's adjoint in one launch per bucket), K timed repetitions after
+    W warm-ups, each from the seeded starts; one JSON line."""
+    import torch
+
+    import paper_1502_03543_gb300 as P
+    from paper_1502_03543_gb300 import build as B
+
+    B.build()
+    spec = lpgen.BATCHES["adjoint_256_f32"]
+    sizes = (np.full(spec["count"], spec["m"]), np.full(spec["count"], spec["n"]))
+    lps = lpgen.batch(spec["count"], storage=spec["storage"], sizes=sizes)
+    pk = lpgen.pack(lps)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    A = torch.from_numpy(np.ascontiguousarray(pk["A"], dtype=np.float32)).cuda()
+    b, c = dv(pk["b"]), dv(pk["c"])
+    x0, y0, s0 = dv(pk["x0"]), dv(pk["y0"]), dv(pk["s0"])
+    x, y, s = x0.clone(), y0.clone(), s0.clone()
+    w = dv(np.random.default_rng(0).standard_normal(int(pk["n"].sum())))
+    S = P.BatchSolver(pk["m"], pk["n"], A, b, c, x, y, s, tol=spec["tol"])
+    fwd, bwd = [], []
+    for k in range(args.warmup + args.steps):
+        x.copy_(x0)
+        y.copy_(y0)
+        s.copy_(s0)
+        out = S.solve()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dA, db, dc, status = S.backward(w)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            fwd.append(out["ms"])
+            bwd.append((t1 - t0) * 1e3)
+    S.close()
+    print(json.dumps(dict(metric="differentiable batch: forward solve and batched adjoint (256 LPs of 128x384)",
+                          forward_ms=float(np.mean(fwd)), adjoint_ms=float(np.mean(bwd)),
+                          adjoint_lps_per_s=spec["count"] / (float(np.mean(bwd)) * 1e-3),
+                          forward_statuses={str(int(a)): int(n) for a, n in zip(*np.unique(out["status"],
+                                                                                           return_counts=True))},
+                          adjoint_statuses={str(int(a)): int(n) for a, n in zip(*np.unique(status,
+                                                                                           return_counts=True))},
+                          iterations_per_batch=int(out["iters"].sum()), steps=args.steps, warmup=args.warmup,
+                          adjoint_timing="host wall clock around pdas_batch_backward (it synchronises its stream)",
+                          config=dict(workload="adjoint_256_f32", count=spec["count"], m=spec["m"], n=spec["n"],
+                                      tol=spec["tol"], alpha=ALPHA))))
+
+
 def run_woodbury(args):
     """The paper's own solver of the normal equations (the Egidi-Maponi
     rank-one recurrence from (A A')^{-1} A, pdas_woodbury.h) against the
@@ -734,15 +783,20 @@ def main():
                     help="normal: time only the normal-matrix stage; factor: also the Cholesky (for profiles)")
     ap.add_argument("--tier2", action="store_true", help="--kernel normal: the FP64 tier's formation")
     ap.add_argument("--batch", action="store_true", help="time the 512-LP batch configuration instead")
+    ap.add_argument("--batch-adjoint", action="store_true",
+                    help="time the differentiable batch (256 LPs, forward and batched adjoint) instead")
     ap.add_argument("--woodbury", action="store_true",
                     help="time the paper's rank-one (Woodbury) solver against the Cholesky direction instead")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step" and not (args.batch or args.woodbury):
+    if args.warmup < 3 and args.impl == "ours" and args.kernel == "step" and not (args.batch or args.woodbury or
+                                                                                  args.batch_adjoint):
         ap.error("--warmup must be >= 3")
     if args.batch:
         run_batch(args)
     elif args.woodbury:
         run_woodbury(args)
+    elif args.batch_adjoint:
+        run_batch_adjoint(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.kernel in ("normal", "factor"):

@@ -92,6 +92,24 @@ double pdas_batch_last_ms(pdas_batch_handle h);
 
 const char* pdas_batch_last_error_message(pdas_batch_handle h);
 
+/* Sensitivities of a loss L(x*_1, ..., x*_count) at every LP's final
+ * iterate, after pdas_batch_solve, in one launch per bucket (one CTA per LP,
+ * as the solve): the adjoint of pdas_backward (pdas.h) for each LP --
+ * implicit differentiation of F = [A x - b; A'y + s - c; X s - sigma] = 0
+ * with sigma = x.*s held fixed, reduced to the normal equations of the
+ * Newton direction (Section V), (A D A') la = A D g, lb = D (A' la - g),
+ * and refined twice on the full adjoint system with FP64 residuals.  The
+ * normal matrix at the final D is formed and factored in the CTA (FP32, or
+ * the FP64 tier's factor where the FP32 one fails) to precondition the
+ * solves.  Device arrays, packed like the handle's buffers: dL_dx (like x,
+ * g = dL/dx), dL_db (like b) = la, dL_dc (like c) = lb, and dL_dA (FP64,
+ * packed like A; may be NULL) = -(la x' + y lb').  status_out (host, count
+ * entries, may be NULL) receives each LP's status: PDAS_OK, or
+ * PDAS_ERR_NOT_SPD if its solve broke down, PDAS_ERR_NOT_INTERIOR.  Returns
+ * PDAS_OK when the launches completed. */
+pdas_status pdas_batch_backward(pdas_batch_handle h, const double* dL_dx, double* dL_dA, double* dL_db,
+                                double* dL_dc, int* status_out);
+
 void pdas_batch_destroy(pdas_batch_handle h);
 
 #ifdef __cplusplus

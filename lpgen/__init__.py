@@ -151,4 +151,7 @@ def pack(lps):
 BATCHES = {
     # 512 LPs, m ~ U{16..256}, n = m U{2..4}, FP32 storage, instance seeds 1000 + i
     "batch_512_f32": dict(count=512, seed=0, storage="f32", tol=1e-7),
+    # the differentiable batch: 256 LPs of 128 x 384, FP32 storage, instance
+    # seeds 1000 + i, stopped at a gap of 1e-6; loss sum_i w_i' x*_i
+    "adjoint_256_f32": dict(count=256, m=128, n=384, storage="f32", tol=1e-6),
 }

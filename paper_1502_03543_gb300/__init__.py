@@ -309,6 +309,24 @@ class BatchSolver:
         return dict(status=status, iters=iters, gap=gap, fp64_iters=fp64, unrefined=unrefined, time_us=time_us,
                     ms=N.lib().pdas_batch_last_ms(self._h))
 
+    def backward(self, dL_dx, want_dA=True):
+        """Sensitivities at every LP's final iterate (pdas_batch_backward):
+        dL_dx packed like x; returns (dL_dA packed like A in FP64 or None,
+        dL_db packed like b, dL_dc packed like c, per-LP status array)."""
+        mt, nt = int(self.m.sum()), int(self.n.sum())
+        at = int((self.m.astype(np.int64) * self.n).sum())
+        dev = dL_dx.device
+        dA = torch.empty(at, dtype=torch.float64, device=dev) if want_dA else None
+        db = torch.empty(mt, dtype=torch.float64, device=dev)
+        dc = torch.empty(nt, dtype=torch.float64, device=dev)
+        status = np.zeros(self.count, dtype=np.int32)
+        st = N.lib().pdas_batch_backward(self._h, _ptr(dL_dx, torch.float64, nt, "dL_dx"),
+                                         _ptr(dA) if want_dA else None, _ptr(db), _ptr(dc),
+                                         status.ctypes.data_as(ctypes.c_void_p))
+        if st != N.OK:
+            raise PdasError(st, "pdas_batch_backward", N.lib().pdas_batch_last_error_message(self._h).decode())
+        return dA, db, dc, status
+
     def config(self):
         """The buckets: list of (m bound, CTA threads, LP count)."""
         k = 8

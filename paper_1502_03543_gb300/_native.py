@@ -127,6 +127,7 @@ SIGNATURES = {
     "pdas_batch_diagnostics": ([_H, _P, _P, _P], _I),
     "pdas_batch_last_error_message": ([_H], ctypes.c_char_p),
     "pdas_batch_destroy": ([_H], None),
+    "pdas_batch_backward": ([_H, _P, _P, _P, _P, _P], _I),
     "pdas_profile_enable": ([_H, _I], _I),
     "pdas_profile_read": ([_H, ctypes.POINTER(Profile)], _I),
     "pdas_woodbury_create": ([_I64, _I64, _I, _P, ctypes.POINTER(_H)], _I),

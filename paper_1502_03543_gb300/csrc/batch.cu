@@ -500,6 +500,136 @@ __device__ void blk_apply_m(const Ctx& c, const double* v, const double* base, d
   __syncthreads();
 }
 
+// M at the current D and its factor.  Until an FP32 factor fails (tier2
+// false) M is formed and factored in FP32 in shared memory; after that (and
+// from then on) the normal matrix of the significant columns is formed in
+// double-float and factored in FP64 in the CTA's global scratch slot, as the
+// large path does near the optimum.  mnorm receives max_p M_pp.  Returns
+// false if the FP64 factor meets a pivot that is not positive (M singular to
+// working precision).
+template <int T>
+__device__ bool factor_lp(const BatchArgs& a, Ctx& c, bool& tier2, double* M64, double* dinv64, double& mnorm) {
+  const int m = c.m, n = c.n;
+  mnorm = 0.0;
+  if (!tier2) {
+    blk_syrk<T>(c, a.m_cap);
+    double dm = 0.0;
+    for (int i = threadIdx.x; i < m; i += T) dm = fmax(dm, (double)c.L[pk(i, i)]);
+    mnorm = bmax<T>(dm, c.scal);
+    tier2 = !blk_chol<T>(c);
+  }
+  if (!tier2) return true;
+  // the significant columns: D_j >= 1e-10 max D, at least min(n, 1.25 m)
+  // of them (the threshold drops by 16x until enough pass); the factor
+  // of A_K D_K A_K' preconditions the exact M in the refinement
+  double dmx = 0.0;
+  for (int j = threadIdx.x; j < n; j += T) dmx = fmax(dmx, c.D[j]);
+  dmx = bmax<T>(dmx, c.scal);
+  const int want = min(n, (5 * m + 3) / 4);
+  double thr = dmx * 1e-10;
+  for (int guard = 0; guard < 64; ++guard) {
+    int cnt = 0;
+    for (int j = threadIdx.x; j < n; j += T) cnt += c.D[j] >= thr;
+    if ((int)bsum<T>((double)cnt, c.scal) >= want) break;
+    thr *= 0x1p-4;
+  }
+  if (threadIdx.x == 0) {  // ordered compaction
+    int k = 0;
+    for (int j = 0; j < n; ++j)
+      if (c.D[j] >= thr) c.kidx[k++] = j;
+    c.scal[31] = (double)k;
+  }
+  __syncthreads();
+  const int nk = (int)c.scal[31];
+  __syncthreads();
+  blk_syrk_df<T>(c, a.m_cap, M64, nk);
+  double dm = 0.0;
+  for (int i = threadIdx.x; i < m; i += T) dm = fmax(dm, M64[pk(i, i)]);
+  mnorm = bmax<T>(dm, c.scal);
+  return blk_chol64<T>(c, M64, dinv64);
+}
+
+// out = (A D A')^{-1} rhs: out = P^-1 rhs, then preconditioned conjugate
+// gradients on the exact M (matrix-free), accepted when ||rhs - M out||_inf
+// <= refine_tol ||rhs||_inf or <= refine_tol (mnorm ||out||_inf +
+// ||rhs||_inf).  Uses c.rho, c.z, c.p, c.q; leaves c.w = A' (last operand).
+// Returns whether the tolerance was met within refine_max steps.
+template <int T>
+__device__ bool pcg_lp(const BatchArgs& a, Ctx& c, bool tier2, const double* M64, const double* dinv64,
+                       double mnorm, const double* rhs, double* out, int refine_max) {
+  const int m = c.m;
+  double rn = 0.0;
+  for (int i = threadIdx.x; i < m; i += T) rn = fmax(rn, fabs(rhs[i]));
+  rn = bmax<T>(rn, c.scal);
+  if (!(rn > 0.0)) rn = 1.0;
+  auto precond = [&](const double* v, double* o) {
+    if (tier2) blk_precond64<T>(c, M64, dinv64, v, o);
+    else blk_precond<T>(c, v, o);
+  };
+  precond(rhs, out);
+  auto accepted = [&](double res, double dyn) {
+    return res <= a.refine_tol * rn || res <= a.refine_tol * (mnorm * dyn + rn);
+  };
+  auto true_residual = [&](double& res, double& dyn) {
+    blk_apply_m<T>(c, out, rhs, c.rho);  // rho = rhs - M out
+    double rr = 0.0, dd = 0.0;
+    for (int i = threadIdx.x; i < m; i += T) {
+      rr = fmax(rr, fabs(c.rho[i]));
+      dd = fmax(dd, fabs(out[i]));
+    }
+    res = bmax<T>(rr, c.scal);
+    dyn = bmax<T>(dd, c.scal);
+  };
+  double res, dyn;
+  true_residual(res, dyn);
+  bool done = accepted(res, dyn);
+  if (!done) {
+    double rz = 0.0;
+    auto restart = [&]() {
+      precond(c.rho, c.z);
+      double t = 0.0;
+      for (int i = threadIdx.x; i < m; i += T) {
+        c.p[i] = c.z[i];
+        t += c.rho[i] * c.z[i];
+      }
+      rz = bsum<T>(t, c.scal);
+    };
+    restart();
+    for (int k = 0; k < refine_max && rz > 0.0 && isfinite(rz); ++k) {
+      blk_apply_m<T>(c, c.p, nullptr, c.q, !tier2);
+      double t = 0.0;
+      for (int i = threadIdx.x; i < m; i += T) t += c.p[i] * c.q[i];
+      const double pq = bsum<T>(t, c.scal);
+      if (!(pq > 0.0)) break;
+      const double al = rz / pq;
+      double rr = 0.0, dd = 0.0;
+      for (int i = threadIdx.x; i < m; i += T) {
+        out[i] += al * c.p[i];
+        c.rho[i] -= al * c.q[i];
+        rr = fmax(rr, fabs(c.rho[i]));
+        dd = fmax(dd, fabs(out[i]));
+      }
+      res = bmax<T>(rr, c.scal);
+      dyn = bmax<T>(dd, c.scal);
+      if (accepted(res, dyn) || k % 10 == 9) {
+        true_residual(res, dyn);
+        if ((done = accepted(res, dyn))) break;
+        restart();
+        continue;
+      }
+      precond(c.rho, c.z);
+      t = 0.0;
+      for (int i = threadIdx.x; i < m; i += T) t += c.rho[i] * c.z[i];
+      const double rz2 = bsum<T>(t, c.scal);
+      const double beta = rz2 / rz;
+      for (int i = threadIdx.x; i < m; i += T) c.p[i] = c.z[i] + beta * c.p[i];
+      __syncthreads();
+      rz = rz2;
+    }
+  }
+  return done;
+}
+
 // The whole PDAS loop of one LP; returns its status, iterations and gap.
 template <int T>
 __device__ void solve_lp(const BatchArgs& a, const BatchLP lp, Ctx& c, int& status, int& iters, double& gap,
@@ -534,123 +664,15 @@ __device__ void solve_lp(const BatchArgs& a, const BatchLP lp, Ctx& c, int& stat
     }
     blk_gemv<T>(c, c.un2, nullptr, c.r);  // r = A x
     __syncthreads();
-    double rn = 0.0;
-    for (int i = threadIdx.x; i < m; i += T) rn = fmax(rn, fabs(c.r[i]));
-    rn = bmax<T>(rn, c.scal);
-    if (!(rn > 0.0)) rn = 1.0;
-    // M and its factor: FP32 in shared memory; once the FP32 factor fails, the
-    // LP continues with the FP64 factor of its global scratch slot
     double mnorm = 0.0;
-    if (!tier2) {
-      blk_syrk<T>(c, a.m_cap);
-      double dm = 0.0;
-      for (int i = threadIdx.x; i < m; i += T) dm = fmax(dm, (double)c.L[pk(i, i)]);
-      mnorm = bmax<T>(dm, c.scal);
-      tier2 = !blk_chol<T>(c);
+    // (a non-positive FP64 pivot means M is singular to working precision at
+    // this iterate: a nearly degenerate LP close to its optimum)
+    if (!factor_lp<T>(a, c, tier2, M64, dinv64, mnorm)) {
+      status = PDAS_ERR_NOT_SPD;
+      break;
     }
-    if (tier2) {
-      // the significant columns: D_j >= 1e-10 max D, at least min(n, 1.25 m)
-      // of them (the threshold drops by 16x until enough pass); the factor
-      // of A_K D_K A_K' preconditions the exact M in the refinement
-      double dmx = 0.0;
-      for (int j = threadIdx.x; j < n; j += T) dmx = fmax(dmx, c.D[j]);
-      dmx = bmax<T>(dmx, c.scal);
-      const int want = min(n, (5 * m + 3) / 4);
-      double thr = dmx * 1e-10;
-      for (int guard = 0; guard < 64; ++guard) {
-        int cnt = 0;
-        for (int j = threadIdx.x; j < n; j += T) cnt += c.D[j] >= thr;
-        if ((int)bsum<T>((double)cnt, c.scal) >= want) break;
-        thr *= 0x1p-4;
-      }
-      if (threadIdx.x == 0) {  // ordered compaction
-        int k = 0;
-        for (int j = 0; j < n; ++j)
-          if (c.D[j] >= thr) c.kidx[k++] = j;
-        c.scal[31] = (double)k;
-      }
-      __syncthreads();
-      const int nk = (int)c.scal[31];
-      __syncthreads();
-      blk_syrk_df<T>(c, a.m_cap, M64, nk);
-      double dm = 0.0;
-      for (int i = threadIdx.x; i < m; i += T) dm = fmax(dm, M64[pk(i, i)]);
-      mnorm = bmax<T>(dm, c.scal);
-      // (a non-positive FP64 pivot means M is singular to working precision at
-      // this iterate: a nearly degenerate LP close to its optimum)
-      if (!blk_chol64<T>(c, M64, dinv64)) {
-        status = PDAS_ERR_NOT_SPD;
-        break;
-      }
-      ++n_shift;
-    }
-    auto precond = [&](const double* v, double* out) {
-      if (tier2) blk_precond64<T>(c, M64, dinv64, v, out);
-      else blk_precond<T>(c, v, out);
-    };
-    // dy = P^-1 r, then preconditioned conjugate gradients on the exact M
-    precond(c.r, c.dy);
-    auto accepted = [&](double res, double dyn) {
-      return res <= a.refine_tol * rn || res <= a.refine_tol * (mnorm * dyn + rn);
-    };
-    auto true_residual = [&](double& res, double& dyn) {
-      blk_apply_m<T>(c, c.dy, c.r, c.rho);  // rho = r - M dy
-      double rr = 0.0, dd = 0.0;
-      for (int i = threadIdx.x; i < m; i += T) {
-        rr = fmax(rr, fabs(c.rho[i]));
-        dd = fmax(dd, fabs(c.dy[i]));
-      }
-      res = bmax<T>(rr, c.scal);
-      dyn = bmax<T>(dd, c.scal);
-    };
-    double res, dyn;
-    true_residual(res, dyn);
-    bool done = accepted(res, dyn);
-    if (!done) {
-      double rz = 0.0;
-      auto restart = [&]() {
-        precond(c.rho, c.z);
-        double t = 0.0;
-        for (int i = threadIdx.x; i < m; i += T) {
-          c.p[i] = c.z[i];
-          t += c.rho[i] * c.z[i];
-        }
-        rz = bsum<T>(t, c.scal);
-      };
-      restart();
-      for (int k = 0; k < a.refine_max && rz > 0.0 && isfinite(rz); ++k) {
-        blk_apply_m<T>(c, c.p, nullptr, c.q, !tier2);
-        double t = 0.0;
-        for (int i = threadIdx.x; i < m; i += T) t += c.p[i] * c.q[i];
-        const double pq = bsum<T>(t, c.scal);
-        if (!(pq > 0.0)) break;
-        const double al = rz / pq;
-        double rr = 0.0, dd = 0.0;
-        for (int i = threadIdx.x; i < m; i += T) {
-          c.dy[i] += al * c.p[i];
-          c.rho[i] -= al * c.q[i];
-          rr = fmax(rr, fabs(c.rho[i]));
-          dd = fmax(dd, fabs(c.dy[i]));
-        }
-        res = bmax<T>(rr, c.scal);
-        dyn = bmax<T>(dd, c.scal);
-        if (accepted(res, dyn) || k % 10 == 9) {
-          true_residual(res, dyn);
-          if ((done = accepted(res, dyn))) break;
-          restart();
-          continue;
-        }
-        precond(c.rho, c.z);
-        t = 0.0;
-        for (int i = threadIdx.x; i < m; i += T) t += c.rho[i] * c.z[i];
-        const double rz2 = bsum<T>(t, c.scal);
-        const double beta = rz2 / rz;
-        for (int i = threadIdx.x; i < m; i += T) c.p[i] = c.z[i] + beta * c.p[i];
-        __syncthreads();
-        rz = rz2;
-      }
-    }
-    if (!done) ++n_unref;
+    if (tier2) ++n_shift;
+    if (!pcg_lp<T>(a, c, tier2, M64, dinv64, mnorm, c.r, c.dy, a.refine_max)) ++n_unref;
     // w = A' dy; dx = D w - x; ds = -w
     blk_gemv_t<T>(c, c.dy, c.w);
     __syncthreads();
@@ -701,22 +723,20 @@ __device__ void solve_lp(const BatchArgs& a, const BatchLP lp, Ctx& c, int& stat
   }
 }
 
-template <int T>
-__global__ void __launch_bounds__(T) k_batch(BatchArgs a) {
-  extern __shared__ __align__(16) unsigned char batch_smem_raw[];
-  __shared__ int s_lp;
-  const BatchSmem L = batch_smem(a.m_cap, a.n_cap);
+// The per-CTA views of the dynamic shared memory for capacities (m_cap, n_cap).
+__device__ __forceinline__ Ctx make_ctx(unsigned char* batch_smem_raw, int m_cap, int n_cap) {
+  const BatchSmem L = batch_smem(m_cap, n_cap);
   Ctx c;
   c.L = reinterpret_cast<float*>(batch_smem_raw + L.L);
   c.dinv = reinterpret_cast<float*>(batch_smem_raw + L.dinv);
   c.zf = reinterpret_cast<float*>(batch_smem_raw + L.zf);
   double* vm = reinterpret_cast<double*>(batch_smem_raw + L.vm);
   c.r = vm;
-  c.dy = vm + a.m_cap;
-  c.rho = vm + 2 * a.m_cap;
-  c.z = vm + 3 * a.m_cap;
-  c.p = vm + 4 * a.m_cap;
-  c.q = vm + 5 * a.m_cap;
+  c.dy = vm + m_cap;
+  c.rho = vm + 2 * m_cap;
+  c.z = vm + 3 * m_cap;
+  c.p = vm + 4 * m_cap;
+  c.q = vm + 5 * m_cap;
   c.D = reinterpret_cast<double*>(batch_smem_raw + L.D);
   c.w = reinterpret_cast<double*>(batch_smem_raw + L.w);
   c.un2 = reinterpret_cast<float2*>(batch_smem_raw + L.un2);
@@ -725,6 +745,14 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs a) {
   c.stage = reinterpret_cast<float*>(batch_smem_raw + L.stage);
   c.dc = reinterpret_cast<float*>(batch_smem_raw + L.dc);
   c.scal = reinterpret_cast<double*>(batch_smem_raw + L.scal);
+  return c;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char batch_smem_raw[];
+  __shared__ int s_lp;
+  Ctx c = make_ctx(batch_smem_raw, a.m_cap, a.n_cap);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -756,6 +784,129 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs a) {
   }
 }
 
+// The adjoint of one LP at its final iterate (x, y, s), as pdas_backward
+// (pdas.h) computes it for one handle: implicit differentiation of
+// F = [A x - b; A'y + s - c; X s - sigma] = 0 with sigma = x.*s held fixed,
+// whose adjoint system reduces to the normal equations of the direction,
+//     (A D A') la = A D g,   lb = D (A' la - g),   lc = -lb / x,
+// then two corrections on the full system J'(la, lb, lc) = (g, 0, 0) with
+// FP64 residuals (lb alone cancels where D is large); each correction solves
+// the same normal equations with right-hand side A (D r1 - r3 - lb).  M at
+// the final D is formed and factored in the CTA (FP32 in shared memory, or
+// the FP64 tier's factor if the FP32 one fails) and preconditions the
+// conjugate gradients of every solve (at most 4 refine_max steps each).
+// Outputs: dL/db = la, dL/dc = lb, dL/dA = -(la x' + y lb') (if wanted).
+struct AdjointArgs {
+  BatchArgs a;        // the solve's buffers: (x, y, s) hold the final iterates
+  const double* g;    // dL/dx, packed like x
+  double* la;         // dL/db, packed like y
+  double* lb;         // dL/dc, packed like x
+  double* dA;         // dL/dA, packed like A (FP64), or null
+  double* lc;         // work, packed like x: multiplier of X s = sigma
+  double* wt;         // work, packed like x: A' la
+  double* r1;         // work, packed like x: residual of A' la + S lc = g
+  double* r3;         // work, packed like x: residual of lb + X lc = 0
+  int* astatus;       // per-LP status of the adjoint
+};
+
+template <int T>
+__device__ int adjoint_lp(const AdjointArgs& g, const BatchLP lp, Ctx& c) {
+  const BatchArgs& a = g.a;
+  const int m = lp.m, n = lp.n;
+  const double* x = a.x + lp.n_off;
+  const double* s = a.s + lp.n_off;
+  const double* y = a.y + lp.m_off;
+  const double* gv = g.g + lp.n_off;
+  double* la = g.la + lp.m_off;
+  double* lb = g.lb + lp.n_off;
+  double* lc = g.lc + lp.n_off;
+  double* wt = g.wt + lp.n_off;
+  double* r1 = g.r1 + lp.n_off;
+  double* r3 = g.r3 + lp.n_off;
+  double* M64 = a.scratch + (int64_t)blockIdx.x * a.slot;
+  double* dinv64 = M64 + (int64_t)a.m_cap * (a.m_cap + 1) / 2;
+  int bad = 0;
+  for (int j = threadIdx.x; j < n; j += T) {
+    const double xj = x[j], sj = s[j];
+    if (!(xj > 0.0) || !(sj > 0.0) || !isfinite(xj) || !isfinite(sj)) bad = 1;
+    c.D[j] = xj / sj;
+    c.un2[j] = df_split(c.D[j] * gv[j]);  // D g
+  }
+  if (__syncthreads_or(bad)) return PDAS_ERR_NOT_INTERIOR;
+  bool tier2 = false;
+  double mnorm = 0.0;
+  if (!factor_lp<T>(a, c, tier2, M64, dinv64, mnorm)) return PDAS_ERR_NOT_SPD;
+  blk_gemv<T>(c, c.un2, nullptr, c.r);  // r = A D g
+  __syncthreads();
+  if (!pcg_lp<T>(a, c, tier2, M64, dinv64, mnorm, c.r, c.dy, 4 * a.refine_max)) return PDAS_ERR_NOT_SPD;
+  for (int i = threadIdx.x; i < m; i += T) la[i] = c.dy[i];
+  blk_gemv_t<T>(c, c.dy, c.w);  // A' la
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += T) {
+    const double b = c.D[j] * (c.w[j] - gv[j]);
+    lb[j] = b;
+    lc[j] = -b / x[j];
+    wt[j] = c.w[j];
+  }
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    for (int j = threadIdx.x; j < n; j += T) {
+      const double e1 = gv[j] - wt[j] - s[j] * lc[j];
+      const double e3 = -lb[j] - x[j] * lc[j];
+      r1[j] = e1;
+      r3[j] = e3;
+      c.un2[j] = df_split(c.D[j] * e1 - e3 - lb[j]);
+    }
+    __syncthreads();
+    blk_gemv<T>(c, c.un2, nullptr, c.r);  // r = A (D r1 - r3 - lb)
+    __syncthreads();
+    // (no correction that meets the tolerance: it is at the rounding level; keep what we have)
+    if (!pcg_lp<T>(a, c, tier2, M64, dinv64, mnorm, c.r, c.dy, 4 * a.refine_max)) break;
+    for (int i = threadIdx.x; i < m; i += T) la[i] += c.dy[i];
+    blk_gemv_t<T>(c, c.dy, c.w);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += T) {
+      const double db = c.D[j] * (c.w[j] - r1[j]) + r3[j];
+      lb[j] += db;
+      lc[j] += (r3[j] - db) / x[j];
+      wt[j] += c.w[j];
+    }
+    __syncthreads();
+  }
+  if (g.dA) {
+    double* dA = g.dA + lp.a_off;
+    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += T) {
+      const int p = (int)(e / n), j = (int)(e - (int64_t)p * n);
+      dA[e] = -(la[p] * x[j] + y[p] * lb[j]);
+    }
+  }
+  return PDAS_OK;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_batch_adjoint(AdjointArgs g) {
+  extern __shared__ __align__(16) unsigned char batch_smem_raw[];
+  __shared__ int s_lp;
+  const BatchArgs& a = g.a;
+  Ctx c = make_ctx(batch_smem_raw, a.m_cap, a.n_cap);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned t = atomicAdd(a.ticket, 1u);
+      s_lp = t < (unsigned)a.count ? a.order[t] : -1;
+    }
+    __syncthreads();
+    const int id = s_lp;
+    if (id < 0) return;
+    const BatchLP lp = a.lps[id];
+    c.A = a.A + lp.a_off;
+    c.m = lp.m;
+    c.n = lp.n;
+    const int st = adjoint_lp<T>(g, lp, c);
+    if (threadIdx.x == 0) g.astatus[id] = st;
+  }
+}
+
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 4;  // m in [1, 64], (64, 128], (128, 192], (192, 256]
 constexpr int kCandidates[3] = {128, 256, 512};
@@ -774,6 +925,26 @@ cudaError_t launch(int threads, int grid, size_t bytes, cudaStream_t st, const B
   if (threads == 128) k_batch<128><<<grid, 128, bytes, st>>>(a);
   else if (threads == 256) k_batch<256><<<grid, 256, bytes, st>>>(a);
   else k_batch<512><<<grid, 512, bytes, st>>>(a);
+  return cudaGetLastError();
+}
+// The adjoint kernel of a bucket uses the solve kernel's shared-memory layout
+// and CTA size; its grid comes from its own occupancy.
+cudaError_t set_adjoint_smem_attr(int threads, size_t bytes) {
+  if (threads == 128)
+    return cudaFuncSetAttribute(k_batch_adjoint<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (threads == 256)
+    return cudaFuncSetAttribute(k_batch_adjoint<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(k_batch_adjoint<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+cudaError_t adjoint_occupancy(int threads, size_t bytes, int* blocks) {
+  if (threads == 128) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_batch_adjoint<128>, 128, bytes);
+  if (threads == 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_batch_adjoint<256>, 256, bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_batch_adjoint<512>, 512, bytes);
+}
+cudaError_t launch_adjoint(int threads, int grid, size_t bytes, cudaStream_t st, const AdjointArgs& g) {
+  if (threads == 128) k_batch_adjoint<128><<<grid, 128, bytes, st>>>(g);
+  else if (threads == 256) k_batch_adjoint<256><<<grid, 256, bytes, st>>>(g);
+  else k_batch_adjoint<512><<<grid, 512, bytes, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -801,6 +972,10 @@ struct pdas_batch_ctx {
   float* time_us = nullptr;
   unsigned* tickets = nullptr;  // one per bucket
   double* scratch = nullptr;    // FP64 tier slots, one per LP of each bucket
+  int64_t total_m = 0, total_n = 0;
+  double* adj_work = nullptr;   // the adjoint's four n-packed work vectors
+  int* astatus = nullptr;       // per-LP status of the last adjoint (device)
+  int* h_astatus = nullptr;     // (pinned mirror)
   int* h_status = nullptr;      // pinned mirrors
   int* h_iters = nullptr;
   double* h_gap = nullptr;
@@ -808,7 +983,7 @@ struct pdas_batch_ctx {
   int* h_unrefined = nullptr;
   float* h_time_us = nullptr;
   struct Bucket {
-    int m_bound = 0, m_cap = 0, n_cap = 0, count = 0, offset = 0, threads = 256, grid = 0;
+    int m_bound = 0, m_cap = 0, n_cap = 0, count = 0, offset = 0, threads = 256, grid = 0, adj_grid = 0;
     int64_t slot = 0, scratch_off = 0;  // doubles per FP64-tier slot; first slot of the bucket
     size_t smem = 0;
     cudaStream_t side = nullptr;
@@ -1000,6 +1175,9 @@ void pdas_batch_destroy(pdas_batch_handle h) {
   if (h->tickets) cudaFree(h->tickets);
   if (h->scratch) cudaFree(h->scratch);
   if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->adj_work) cudaFree(h->adj_work);
+  if (h->astatus) cudaFree(h->astatus);
+  if (h->h_astatus) cudaFreeHost(h->h_astatus);
   if (h->h_iters) cudaFreeHost(h->h_iters);
   if (h->h_gap) cudaFreeHost(h->h_gap);
   delete h;
@@ -1097,6 +1275,11 @@ pdas_status pdas_batch_create(int count, const int* m, const int* n, const float
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(int) * count);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_iters, sizeof(int) * count);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_gap, sizeof(double) * count);
+  h->total_m = mo;
+  h->total_n = no;
+  if (e == cudaSuccess) e = cudaMalloc(&h->adj_work, sizeof(double) * 4 * no);
+  if (e == cudaSuccess) e = cudaMalloc(&h->astatus, sizeof(int) * count);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_astatus, sizeof(int) * count);
   if (e == cudaSuccess) e = cudaMemcpy(h->lps, lps.data(), sizeof(BatchLP) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
@@ -1121,6 +1304,17 @@ pdas_status pdas_batch_create(int count, const int* m, const int* n, const float
   for (int bi = 0; bi < kBuckets; ++bi) {  // (the attribute is per function: set it for the final choice)
     auto& B = h->bk[bi];
     if (B.count && (st = grid_for_bucket(h, bi, B.threads, &B.grid)) != PDAS_OK) return fail(st);
+    if (B.count) {  // the adjoint kernel of the bucket: same CTA size and shared memory
+      int occ = 0;
+      e = set_adjoint_smem_attr(B.threads, B.smem);
+      if (e == cudaSuccess) e = adjoint_occupancy(B.threads, B.smem, &occ);
+      if (e != cudaSuccess) {
+        cuda_fail(h, e, "adjoint kernel attributes");
+        return fail(PDAS_ERR_CUDA);
+      }
+      if (occ < 1) return fail(PDAS_ERR_UNSUPPORTED);
+      B.adj_grid = std::min(B.count, occ * h->sms);
+    }
   }
   if ((st = capture(h)) != PDAS_OK) return fail(st);
   *out = h;
@@ -1167,5 +1361,33 @@ pdas_status pdas_batch_diagnostics(pdas_batch_handle h, int* fp64_out, int* unre
 }
 
 const char* pdas_batch_last_error_message(pdas_batch_handle h) { return h ? h->errmsg : ""; }
+
+pdas_status pdas_batch_backward(pdas_batch_handle h, const double* dL_dx, double* dL_dA, double* dL_db,
+                                double* dL_dc, int* status_out) {
+  if (!h || !dL_dx || !dL_db || !dL_dc) return PDAS_ERR_ARG;
+  for (const void* p : {(const void*)dL_dx, (const void*)dL_dA, (const void*)dL_db, (const void*)dL_dc})
+    if ((uintptr_t)p % 16) return PDAS_ERR_ARG;
+  BCK(cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * kBuckets, h->st));
+  for (int bi = 0; bi < kBuckets; ++bi) {
+    const auto& B = h->bk[bi];
+    if (B.count == 0) continue;
+    AdjointArgs g;
+    g.a = bucket_args(h, bi, h->x, h->y, h->s, h->opt.max_iter);
+    g.g = dL_dx;
+    g.la = dL_db;
+    g.lb = dL_dc;
+    g.dA = dL_dA;
+    g.lc = h->adj_work;
+    g.wt = h->adj_work + h->total_n;
+    g.r1 = h->adj_work + 2 * h->total_n;
+    g.r3 = h->adj_work + 3 * h->total_n;
+    g.astatus = h->astatus;
+    BCK(launch_adjoint(B.threads, B.adj_grid, B.smem, h->st, g));
+  }
+  BCK(cudaMemcpyAsync(h->h_astatus, h->astatus, sizeof(int) * h->count, cudaMemcpyDeviceToHost, h->st));
+  BCK(cudaStreamSynchronize(h->st));
+  if (status_out) memcpy(status_out, h->h_astatus, sizeof(int) * h->count);
+  return PDAS_OK;
+}
 
 }  // extern "C"
