@@ -108,14 +108,19 @@ typedef struct {
                               |rel_gap|, pres and dres (pdas_iter_info) are all below tol.
                               The variant has no centring term: from starts far from
                               feasibility it can stall at the boundary (PDAS_STALLED)   (0) */
-  int fp64_tier_tc;        /* mixed forms with A stored as BF16, in the FP64 tier: 1 = the normal
-                              matrix of the kept columns (up to 16384 of them) is formed on the
-                              tensor cores from exact fixed-point BF16 digit planes of A and of
-                              D.*A (FP64-grade: products and sums exact, one FP64 rounding at
-                              the end); 0 = double-float on the FP32 pipes (normal_form 2)    (1) */
-  double df_factor_floor;  /* mixed forms in the FP64 tier: the factor is the double-float tile
-                              factor (FP32 pipes) while the relative gap of the iterate is above
-                              this, the FP64 factor below it; 0 = double-float to the end  (1e-6) */
+  int fp64_tier_tc;        /* mixed forms in the FP64 tier: 1 = (a) with A stored as BF16, the
+                              normal matrix of the kept columns (up to 16384 of them) is formed
+                              on the tensor cores from exact fixed-point BF16 digit planes of A
+                              and of D.*A (FP64-grade: products and sums exact, one FP64
+                              rounding at the end; normal_form 4), and (b) for m > 256 the FP64
+                              factor's trailing updates run on the tensor cores from digit
+                              planes of each panel (FP64-grade at every gap);
+                              0 = double-float formation (normal_form 2) and the factors of
+                              df_factor_floor                                                 (1) */
+  double df_factor_floor;  /* mixed forms in the FP64 tier without the tensor-core factor: the
+                              factor is the double-float tile factor (FP32 pipes) while the
+                              relative gap of the iterate is above this, the FP64 SIMT factor
+                              below it; 0 = double-float to the end                        (1e-6) */
 } pdas_options;
 
 /* Per-iteration record of the last pdas_step (host memory, filled on return). */

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "pdas_internal.cuh"
+#include "chol_dig.cuh"
 #include "syrk_dig.cuh"
 #include "syrk_tc.cuh"
 
@@ -51,6 +52,7 @@ struct pdas_ctx {
   float* dinv32 = nullptr;
   TcWorkspace tc{};
   DigWorkspace dig{};  // FP64 tier on the tensor cores (BF16 A): digit planes
+  CholDigWorkspace cdig{};  // FP64 tier: the factor's trailing updates on the tensor cores
   int cur_f64 = 1;     // the workspace matrix in use is M64
   int refactored = 0;  // a mixed form switched to FP64 for good
   // column dropping for the FP64 factor of the mixed forms
@@ -73,7 +75,7 @@ struct pdas_ctx {
   unsigned char* chol_planes = nullptr;  // BF16 operand planes of the tile factor's off-diagonal tiles
   float2* pairs = nullptr;      // the vector of a double-float pass as FP32 pairs (max(m, n))
   int switch_reason = 0;  // pdas_iter_info.fp64_reason of that switch
-  bool last_factor_df = false;    // the last factor was the double-float tile factor (FP64 tier)
+  bool last_factor_df = false;    // the last factor was a fast FP64-tier factor (tensor-core or double-float)
   double last_rel_gap = HUGE_VAL;  // relative gap of the iterate after the last step
   bool no_dffactor_once = false;  // this iteration: that factor failed, use the FP64 factor
   int64_t err_index = -1;
@@ -371,6 +373,16 @@ pdas_status form_normal(pdas_ctx* h, const void* A) {
 // the gap-1e-8 run of the 8192 x 32768 problem from 54 iterations to 80.
 pdas_status factor(pdas_ctx* h) {
   h->last_factor_df = false;
+  if (h->cur_f64 && is_mixed(h) && h->cdig.planes && !h->no_dffactor_once) {
+    // FP64 tier with fp64_tier_tc: the FP64 factor whose trailing updates run
+    // on the tensor cores from exact digit planes (FP64-grade at every gap);
+    // on a failed pivot the next attempt uses the FP64 SIMT factor
+    h->last_factor_df = true;
+    int k = 0;
+    CK(cholesky_dig(h->st, &h->cdig, h->ldm, h->M64, h->dinv64, h->sc, &k));
+    h->launches += k;
+    return PDAS_OK;
+  }
   if (h->cur_f64 && is_mixed(h) && h->chol_ntasks > 0 && !h->no_dffactor_once &&
       h->last_rel_gap > h->opt.df_factor_floor) {
     // FP64 tier of a mixed form: the double-float tile factor (FP32 pipes),
@@ -766,6 +778,8 @@ pdas_status pdas_create(int64_t m, int64_t n, const pdas_options* opt_in, pdas_h
   }
   if (e == cudaSuccess && opt.form != PDAS_FP64 && opt.a_dtype == PDAS_A_BF16 && opt.fp64_tier_tc)
     e = dig_workspace_create(&h->dig, m, n);
+  if (e == cudaSuccess && opt.form != PDAS_FP64 && opt.fp64_tier_tc && m > kCholDigMinM)
+    e = chol_dig_create(&h->cdig, m);
   if (e == cudaSuccess && (opt.form == PDAS_BF16_IR || opt.form == PDAS_TF32_IR)) {
     e = tc_workspace_create(&h->tc, opt.form, opt.a_dtype, opt.splits, m, n);
     if (e == cudaErrorNotSupported) {
@@ -814,6 +828,7 @@ void pdas_destroy(pdas_handle h) {
   if (h->wait_pinned) cudaFreeHost(h->wait_pinned);
   tc_workspace_destroy(&h->tc);
   dig_workspace_destroy(&h->dig);
+  chol_dig_destroy(&h->cdig);
   for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
   delete h;
 }

@@ -16,6 +16,7 @@
 // the blocks it depends on, so a block only waits on blocks that were handed
 // out earlier and are running or done -- no deadlock.  On a timeout it sets
 // PDAS_ERR_TIMEOUT and returns.
+#include "chol_dig.cuh"
 #include "sync_util.cuh"
 #include "tile_core.cuh"
 
@@ -350,6 +351,13 @@ cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Sca
       k_chol_update<T><<<(unsigned)(tu * (tu + 1) / 2), kThreads, update_smem_bytes<T>(), st>>>(m, ldm, M, k0, kb,
                                                                                               sc);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t chol_panel64(cudaStream_t st, int64_t m, int64_t ldm, double* M, double* dinv, int64_t k0, int kb,
+                         Scalars* sc) {
+  const int64_t t = (m - k0 - kb + kTile - 1) / kTile;
+  k_chol_panel<double><<<(unsigned)(1 + t), kThreads, 0, st>>>(m, ldm, M, dinv, k0, kb, sc);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,357 @@
+// chol_dig.cu -- FP64 blocked Cholesky of the FP64 tier (Section V-A's
+// symmetric positive definite solve) whose trailing updates run on the
+// tcgen05 tensor cores, exactly, from fixed-point BF16 digit planes.
+//
+// Per 64-column panel k0 (kb = min(64, m - k0) columns):
+//   k_chol_panel<double> (chol.cu)  -- the FP64 panel: diagonal block factor,
+//                                      the panel rows solved against it;
+//   k_panel_digits                  -- row r of the panel P (trailing rows
+//                                      r >= k0 + kb, the kb panel columns) as
+//                                      7 balanced base-256 digits of
+//                                      P_rc 2^-e_r, e_r the exponent of the
+//                                      row's largest |P_rc|:
+//                                      P_rc = 2^e_r sum_s d_s 2^(-7-8s);
+//   k_dig_update                    -- C_pq -= (P P')_pq over the lower tiles
+//                                      (128 rows p x 64 columns q) of the
+//                                      trailing matrix:
+//        (P P')_pq = 2^(e_p + e_q - 14) sum_{w<=7} 2^(-8w) I_w,
+//        I_w = sum_c sum_{s+t=w} d_s,pc d_t,qc,
+//      every digit product an integer of magnitude <= 2^14, at most 7 pairs
+//      per weight and kb <= 64 columns: |I_w| < 2^23, so the tensor core's
+//      FP32 accumulator holds I_w exactly.  The epilogue combines the eight
+//      weights exactly in int64, converts once to FP64 and subtracts from C
+//      in FP64.
+// The only roundings of an update are the digits of entries below 1/8 of
+// their row's largest (to 2^-56 of 2^e_r), the digit pairs of weight 8 and
+// more left out (at most 2^-62 of 2^(e_p + e_q) per column) and the final
+// FP64 combination and subtraction: FP64-grade, where the FP64 pipes would
+// take 1/64 of the FP32 rate.
+//
+// k_dig_update: one CTA per 128 x 64 tile, 10 warps:
+//   warp 0      one TMA load of the 7 planes for rows p (128 x 64 columns)
+//               and the 7 planes for rows q (64 x 64 columns), 168 KB;
+//   warp 1      allocates 512 TMEM columns (8 weights x 64); one lane issues
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=64, K=16), 34
+//               pairs x 4 K steps, pair (s, t) into weight s + t;
+//   warps 2..9  warp w reads TMEM lanes 32 (w % 4).. and columns
+//               32 ((w - 2) / 4).. of every weight, combines the weights and
+//               stages the scaled update in shared memory; then each warp
+//               subtracts whole rows of it from C.
+// Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
+// PDAS_ERR_TIMEOUT, lets its copy land and its MMAs finish, frees TMEM, exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "chol_dig.cuh"
+#include "tc_util.cuh"
+
+namespace pdas {
+
+namespace {
+
+using namespace tc;
+
+constexpr int UBM = 128;                          // rows p of a tile
+constexpr int UBN = 64;                           // rows q (columns of C) of a tile
+constexpr int UK = 64;                            // panel width (columns of P): one 128-byte row
+constexpr int ND = 7;                             // digits per entry (55 bits)
+constexpr int WMAX = 7;                           // largest pair weight kept
+constexpr int NW = WMAX + 1;
+constexpr int NPAIR = 34;                         // pairs (s, t), s, t < 7, s + t <= 7
+constexpr uint32_t P_PLANE = UBM * 128;           // 16 KB: 128 rows of one digit
+constexpr uint32_t Q_PLANE = UBN * 128;           // 8 KB: 64 rows of one digit
+constexpr uint32_t LOAD_BYTES = ND * (P_PLANE + Q_PLANE);  // 168 KB
+static_assert(UBM * (UBN + 1) * sizeof(double) <= LOAD_BYTES, "the update's staging area");
+constexpr uint32_t TMEM_COLS = NW * UBN;          // 512
+constexpr int NUM_THREADS = 320;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)LOAD_BYTES + 256;
+constexpr uint32_t kIdesc = idesc_bf16(UBM, UBN);
+
+static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Balanced base-256 digits of the integer v: dig[ND - 1] the lowest, each in
+// [-128, 128].
+__device__ __forceinline__ void balanced_digits(long long v, int (&dig)[ND]) {
+#pragma unroll
+  for (int t = ND - 1; t > 0; --t) {
+    const int low = (int)(((v + 128) & 255) - 128);
+    dig[t] = low;
+    v = (v - low) >> 8;
+  }
+  dig[0] = (int)v;
+}
+
+// The digits of the panel rows r = k0 + kb + i (i < rows) into planes (7
+// planes of mpad rows x 64 columns, BF16), and their exponents into e[i].
+// One warp per row: the lanes hold columns 2 lane and 2 lane + 1.
+__global__ void k_panel_digits(int64_t ldm, const double* __restrict__ M, int64_t k0, int kb, int64_t rows,
+                               int64_t mpad, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < rows;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double* row = M + (k0 + kb + i) * ldm + k0;
+    const int c0 = 2 * lane, c1 = 2 * lane + 1;
+    const double v0 = c0 < kb ? row[c0] : 0.0, v1 = c1 < kb ? row[c1] : 0.0;
+    double mx = fmax(fabs(v0), fabs(v1));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int er = 0;
+    if (mx > 0.0) frexp(mx, &er);
+    if (lane == 0) e[i] = er;
+    const double sc = ldexp(1.0, 55 - er);
+    int d0[ND], d1[ND];
+    balanced_digits(__double2ll_rn(v0 * sc), d0);
+    balanced_digits(__double2ll_rn(v1 * sc), d1);
+#pragma unroll
+    for (int s = 0; s < ND; ++s) {
+      const uint32_t pair = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d0[s])) |
+                            ((uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d1[s])) << 16);
+      reinterpret_cast<uint32_t*>(planes + ((int64_t)s * mpad + i) * UK)[lane] = pair;
+    }
+  }
+}
+
+// C_pq -= (P P')_pq for the lower tiles of the trailing matrix (rows and
+// columns k0 + kb + [0, rows)); tile b is (I, J) with J <= 2 I + 1 (row
+// block I has 2 I + 2 tiles, the first I (I + 1) tiles precede it).
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_dig_update(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int64_t ldm,
+                 double* __restrict__ M, int64_t base, int64_t rows, const int* __restrict__ e, Scalars* sc) {
+  extern __shared__ uint8_t smem_raw[];
+  if (*(volatile const int*)&sc->status != 0) return;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LOAD_BYTES);  // full | mma done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t full = smem_u32(bars), mma_done = smem_u32(bars + 1);
+
+  // tile (I, J) of block b: I = the largest with I (I + 1) <= b
+  const int64_t b = blockIdx.x;
+  int64_t I = (int64_t)((sqrt(4.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) > b) --I;
+  while ((I + 1) * (I + 2) <= b) ++I;
+  const int64_t J = b - I * (I + 1);
+  const int64_t p0 = I * UBM, q0 = J * UBN;
+  if (q0 >= rows || q0 > p0 + UBM - 1) return;  // beyond the trailing matrix
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_expect_tx(full, LOAD_BYTES);
+      tma_load_3d(sbase, &tmP, 0, (int)p0, 0, full);
+      tma_load_3d(sbase + ND * P_PLANE, &tmQ, 0, (int)q0, 0, full);
+      mbar_wait(full, 0, nullptr);  // the copy has landed before this warp can leave
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (mbar_wait(full, 0, abort_flag)) {
+        fence_after();
+#pragma unroll
+        for (int s = 0; s < ND; ++s) {
+          const uint64_t ad = sdesc_sw128(sbase + s * P_PLANE);
+#pragma unroll
+          for (int t = 0; t < ND; ++t) {
+            if (s + t > WMAX) continue;
+            const uint64_t bd = sdesc_sw128(sbase + ND * P_PLANE + t * Q_PLANE);
+            const uint32_t d = tmem + (uint32_t)((s + t) * UBN);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // 32 bytes (16 BF16) along K per MMA
+              // the first product of weight w is pair (0, w) (or (w - 6, 6) past 6) at its first K step
+              const bool first = (s == (s + t > 6 ? s + t - 6 : 0)) && k == 0;
+              umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, first ? 0u : 1u);
+            }
+          }
+        }
+      } else {
+        *abort_flag = 1;
+      }
+      umma_commit(mma_done);  // fires once every MMA issued above has completed
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(mma_done, 0, abort_flag) && !*abort_flag;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    // the update, scaled, staged in shared memory (the operands are consumed
+    // once the MMAs are done), then subtracted from C by whole rows
+    double* stg = reinterpret_cast<double*>(smem);  // [128][65]
+    if (ok) {
+      fence_after();
+      const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+      const int rl = quarter * 32 + lane;
+      const int64_t p = p0 + rl;
+      const int ep = p < rows ? e[p] : 0;
+      // GB300 runs FP64 at 1/64 of the FP32 rate: the weights are combined
+      // exactly on the integer pipes, hi = I_0 2^24 + I_1 2^16 + I_2 2^8 + I_3
+      // and lo = I_4 2^24 + ... + I_7 (|I_w| < 2^23: both below 2^48), and
+      // sum_w 2^-8w I_w = 2^-24 (hi + 2^-32 lo) takes two conversions and one
+      // FP64 multiply-add; the power-of-two scale one multiply
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {  // 16 columns at a time
+        long long hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          uint32_t r[16];
+          tmem_ld16(lane_addr + (uint32_t)(w * UBN + g * 16), r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
+            if (w < 4) hi[j] += v * (1ll << (8 * (3 - w)));
+            else lo[j] += v * (1ll << (8 * (7 - w)));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = half * 32 + g * 16 + j;
+          const int64_t q = q0 + c;
+          double u = 0.0;
+          if (q < rows) {
+            const int k = ep + e[q] - 38;  // 2^(e_p + e_q - 14) times 2^-24
+            const double v = fma((double)lo[j], 0x1p-32, (double)hi[j]);
+            u = (k > -1022 && k < 1023) ? v * __longlong_as_double((long long)(1023 + k) << 52) : ldexp(v, k);
+          }
+          stg[rl * (UBN + 1) + c] = u;
+        }
+      }
+    } else if (lane == 0) {
+      *abort_flag = 1;
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
+    if (!*abort_flag) {
+      for (int rl = warp - 2; rl < UBM; rl += 8) {  // coalesced: a warp per row
+        const int64_t p = p0 + rl;
+        if (p >= rows) break;
+        double* dst = M + (base + p) * ldm + base;
+        for (int j = lane; j < UBN; j += 32) {
+          const int64_t q = q0 + j;
+          if (q <= p) dst[q] -= stg[rl * (UBN + 1) + j];
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+struct CholDigHost {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  CUtensorMap mapP, mapQ;
+};
+
+cudaError_t get_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  *out = fn;
+  return cudaSuccess;
+}
+
+// 3-D map over the 7 digit planes: dims {64, mpad, 7}, box {64, rows, 7},
+// 128-byte swizzle; the box lands as 7 x rows x 128 B.
+cudaError_t encode_planes(CholDigHost* hs, CUtensorMap* map, const void* base, int64_t mpad, int rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)UK, (cuuint64_t)mpad, (cuuint64_t)ND};
+  cuuint64_t strides[2] = {(cuuint64_t)(UK * 2), (cuuint64_t)(mpad * UK * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)UK, (cuuint32_t)rows, (cuuint32_t)ND};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = hs->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t chol_dig_create(CholDigWorkspace* w, int64_t m) {
+  w->m = m;
+  w->mpad = (m + UBM - 1) / UBM * UBM;
+  CholDigHost* hs = new (std::nothrow) CholDigHost();
+  if (!hs) return cudaErrorMemoryAllocation;
+  w->host = hs;
+  cudaError_t e = get_encoder(&hs->encode);
+  const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)ND * w->mpad * UK;
+  if (e == cudaSuccess) e = cudaMalloc(&w->planes, plane_bytes);
+  if (e == cudaSuccess) e = cudaMemset(w->planes, 0, plane_bytes);  // rows never written read as 0
+  if (e == cudaSuccess) e = cudaMalloc(&w->e, sizeof(int) * (size_t)w->mpad);
+  if (e == cudaSuccess) e = cudaMemset(w->e, 0, sizeof(int) * (size_t)w->mpad);
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapP, w->planes, w->mpad, UBM);
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapQ, w->planes, w->mpad, UBN);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dig_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  return e;
+}
+
+void chol_dig_destroy(CholDigWorkspace* w) {
+  if (w->planes) cudaFree(w->planes);
+  if (w->e) cudaFree(w->e);
+  delete static_cast<CholDigHost*>(w->host);
+  *w = CholDigWorkspace{};
+}
+
+cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, double* M, double* dinv, Scalars* sc,
+                         int* launches) {
+  *launches = 0;
+  const int64_t m = w->m;
+  CholDigHost* hs = static_cast<CholDigHost*>(w->host);
+  cudaError_t e = cudaSuccess;
+  for (int64_t k0 = 0; k0 < m && e == cudaSuccess; k0 += UK) {
+    const int kb = (int)std::min<int64_t>(UK, m - k0);
+    const int64_t rows = m - k0 - kb;  // the trailing matrix
+    e = chol_panel64(st, m, ldm, M, dinv, k0, kb, sc);
+    ++*launches;
+    if (e != cudaSuccess || rows == 0) continue;
+    const unsigned dgrid = (unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 4736);
+    k_panel_digits<<<dgrid, 256, 0, st>>>(ldm, M, k0, kb, rows, w->mpad, w->e,
+                                          static_cast<__nv_bfloat16*>(w->planes));
+    const int64_t nI = (rows + UBM - 1) / UBM;
+    k_dig_update<<<(unsigned)(nI * (nI + 1)), NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb,
+                                                                             rows, w->e, sc);
+    *launches += 2;
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace pdas

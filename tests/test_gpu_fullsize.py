@@ -155,21 +155,19 @@ def test_tile_cholesky_fp32_full_size(pdas, case):
 
 
 def test_double_float_tile_factor_full_size(pdas, case):
-    """The FP64 tier of a mixed form (the rule dspread_refactor = 1e-300
-    moves the handle to the tier at once): the normal matrix formed by the
-    tier (on the tensor cores from digit planes when the kept columns fit
-    them, as at 4096 x 16384, else in double-float, as at 8192 x 32768 where
-    all 32768 columns are kept at the start) and factored by the same tile
-    task list in double-float (hi + lo FP32 pairs: every multiply-add exact
-    to a few units of 2^-46), then solved by FP64 substitution.
-    g = (m + 1) 2^-43 is the Cholesky bound gamma_{m+1} at a unit roundoff of
-    2^-43."""
+    """The FP64 tier of a mixed form without its tensor-core parts
+    (fp64_tier_tc = 0; the rule dspread_refactor = 1e-300 moves the handle
+    to the tier at once): the normal matrix formed in double-float and
+    factored by the FP32 factor's tile task list in double-float (hi + lo
+    FP32 pairs: every multiply-add exact to a few units of 2^-46), then
+    solved by FP64 substitution.  g = (m + 1) 2^-43 is the Cholesky bound
+    gamma_{m+1} at a unit roundoff of 2^-43."""
     lp, A = case
     m, n = lp.m, lp.n
     x0, s0 = dv(lp.x0), dv(lp.s0)
-    with pdas.Solver(m, n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
+    with pdas.Solver(m, n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300, fp64_tier_tc=0) as S:
         _, _, _, info = S.direction(A, x0, s0)
-        assert info["used_fp64"] == 1 and info["normal_form"] == (4 if n <= 16384 else 2)
+        assert info["used_fp64"] == 1 and info["normal_form"] == 2
         S.form_normal(A, x0, s0)
         M = host64(S.copy_matrix())
         S.factor()  # no step taken yet: the gap is unknown, so the double-float factor runs
@@ -197,3 +195,35 @@ def test_fp64_factor_full_size(pdas, case):
         kappa, sworst = check_solves(S, L, m, U64, seed=m + 2, rhs0=lp.b)
     print("m=%d fp64 factor: |LL'-M| at %.2e of its bound, normwise %.1e; cond(L) ~ %.0f, solves at %.1e of "
           "their bound" % (m, worst, normwise, kappa, sworst))
+
+
+def test_tensor_core_fp64_factor_full_size(pdas, case):
+    """The FP64 tier's default factor: FP64 panels, trailing updates on the
+    tensor cores from 7 fixed-point BF16 digits per panel row (exact digit
+    products and sums).  Bound: gamma_{m+1}(u64) |L||L'| for the FP64
+    arithmetic, plus the digits' rounding of entries below 1/8 of their
+    panel row's largest (2^-56 of 2^e per entry) and the digit pairs left
+    out, summed over the m / 64 panels: within 2^-40 sqrt(M_pp M_qq)."""
+    lp, A = case
+    m, n = lp.m, lp.n
+    x0, s0 = dv(lp.x0), dv(lp.s0)
+    with pdas.Solver(m, n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
+        _, _, _, info = S.direction(A, x0, s0)
+        assert info["used_fp64"] == 1
+        S.form_normal(A, x0, s0)
+        M = host64(S.copy_matrix())
+        S.factor()
+        L = np.tril(host64(S.copy_matrix()))
+        d = np.sqrt(np.diag(M))
+        absL = np.abs(L)
+        worst, scaled = 0.0, 0.0
+        for p in sample_rows(m, seed=3):
+            err = np.abs(L @ L[p] - np.concatenate([M[p, : p + 1], M[p + 1:, p]]))
+            bound = gamma(m + 1, U64) * (absL @ absL[p]) + 2.0 ** -40 * d[p] * d
+            worst = max(worst, float((err / bound).max()))
+            scaled = max(scaled, float((err / (d[p] * d)).max()))
+        assert worst <= 1.0, worst
+        assert scaled <= 1e-14, scaled
+        kappa, sworst = check_solves(S, L, m, U64, seed=m + 3, rhs0=lp.b)
+    print("m=%d tensor-core FP64 factor: |LL'-M| at %.2e of its bound, scaled %.1e; cond(L) ~ %.0f, solves at "
+          "%.1e of their bound" % (m, worst, scaled, kappa, sworst))
