@@ -61,6 +61,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm, T* M, T* dinv, int64_t k0, int kb,
                                                          Scalars* sc) {
   __shared__ T Ld[kTile][kTile + 1];
+  __shared__ T rcp[kTile];  // 1 / L_cc: the row solves multiply (GB300's FP64 division is a long sequence)
   if (dev_failed(sc)) return;
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, j = e % kb;
@@ -73,12 +74,14 @@ __global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm,
       sc->fail_index = (int)(k0 + fail);
     return;
   }
+  if (threadIdx.x < kb) rcp[threadIdx.x] = T(1) / Ld[threadIdx.x][threadIdx.x];
+  __syncthreads();
   if (blockIdx.x == 0) {
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
       const int i = e / kb, j = e % kb;
       if (j <= i) M[(k0 + i) * ldm + k0 + j] = Ld[i][j];
     }
-    if (threadIdx.x < kb) dinv[k0 + threadIdx.x] = T(1) / Ld[threadIdx.x][threadIdx.x];
+    if (threadIdx.x < kb) dinv[k0 + threadIdx.x] = rcp[threadIdx.x];
     return;
   }
   // Panel rows: X L11' = B, right-looking over columns; thread (row, part)
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_chol_panel(int64_t m, int64_t ldm,
   for (int c = 0; c < kTile; ++c) {
     if (c < kb) {
       const int owner = c & 3;
-      T xc = (part == owner) ? b[c >> 2] / Ld[c][c] : T(0);
+      T xc = (part == owner) ? b[c >> 2] * rcp[c] : T(0);
       xc = __shfl_sync(0xffffffffu, xc, (threadIdx.x & 31 & ~3) | owner);
       if (part == owner) b[c >> 2] = xc;
 #pragma unroll

@@ -33,10 +33,11 @@
 //   warp 1      allocates 512 TMEM columns (8 weights x 64); one lane issues
 //               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=64, K=16), 34
 //               pairs x 4 K steps, pair (s, t) into weight s + t;
-//   warps 2..9  warp w reads TMEM lanes 32 (w % 4).. and columns
+//   warps 2..9  load their rows of C while the copies and the MMAs run;
+//               then warp w reads TMEM lanes 32 (w % 4).. and columns
 //               32 ((w - 2) / 4).. of every weight, combines the weights and
-//               stages the scaled update in shared memory; then each warp
-//               subtracts whole rows of it from C.
+//               stages the scaled update in shared memory, and each warp
+//               subtracts whole rows of it from its part of C.
 // Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
 // PDAS_ERR_TIMEOUT, lets its copy land and its MMAs finish, frees TMEM, exits.
 #include <cuda.h>
@@ -79,6 +80,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c
           "r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
+}
+
+// Whole warp: 8 consecutive columns of this warp's 32 TMEM lanes (lane = row).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Balanced base-256 digits of the integer v: dig[ND - 1] the lowest, each in
@@ -196,12 +205,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     __syncwarp();
   } else {
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int quarter = warp & 3, half = (warp - 2) >> 2, ew = warp - 2;
+    // this warp's share of C (rows ew + 8 i, columns q0 + lane and
+    // q0 + 32 + lane), loaded while the copies and the MMAs run
+    double cpre[UBM / 8][2];
+#pragma unroll
+    for (int i = 0; i < UBM / 8; ++i) {
+      const int64_t p = p0 + ew + 8 * i;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t q = q0 + lane + 32 * h;
+        cpre[i][h] = (p < rows && q <= p) ? M[(base + p) * ldm + base + q] : 0.0;
+      }
+    }
     int ok = 1;
     if (lane == 0) ok = mbar_wait(mma_done, 0, abort_flag) && !*abort_flag;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     // the update, scaled, staged in shared memory (the operands are consumed
-    // once the MMAs are done), then subtracted from C by whole rows
+    // once the MMAs are done), then subtracted from the prefetched C by whole rows
     double* stg = reinterpret_cast<double*>(smem);  // [128][65]
     if (ok) {
       fence_after();
@@ -213,32 +234,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // exactly on the integer pipes, hi = I_0 2^24 + I_1 2^16 + I_2 2^8 + I_3
       // and lo = I_4 2^24 + ... + I_7 (|I_w| < 2^23: both below 2^48), and
       // sum_w 2^-8w I_w = 2^-24 (hi + 2^-32 lo) takes two conversions and one
-      // FP64 multiply-add; the power-of-two scale one multiply
+      // FP64 multiply-add; the power-of-two scale is an integer add to the
+      // exponent field
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {  // 16 columns at a time
-        long long hi[16], lo[16];
+      for (int g = 0; g < 4; ++g) {  // 8 columns at a time
+        long long hi[8], lo[8];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+        for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-          uint32_t r[16];
-          tmem_ld16(lane_addr + (uint32_t)(w * UBN + g * 16), r);
+          uint32_t r[8];
+          tmem_ld8(lane_addr + (uint32_t)(w * UBN + g * 8), r);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 8; ++j) {
             const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
             if (w < 4) hi[j] += v * (1ll << (8 * (3 - w)));
             else lo[j] += v * (1ll << (8 * (7 - w)));
           }
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = half * 32 + g * 16 + j;
+        for (int j = 0; j < 8; ++j) {
+          const int c = half * 32 + g * 8 + j;
           const int64_t q = q0 + c;
           double u = 0.0;
           if (q < rows) {
             const int k = ep + e[q] - 38;  // 2^(e_p + e_q - 14) times 2^-24
             const double v = fma((double)lo[j], 0x1p-32, (double)hi[j]);
-            u = (k > -1022 && k < 1023) ? v * __longlong_as_double((long long)(1023 + k) << 52) : ldexp(v, k);
+            const long long bits = __double_as_longlong(v);
+            const int ev = (int)((bits >> 52) & 0x7ff);
+            u = (ev > 0 && ev + k > 0 && ev + k < 2047) ? __longlong_as_double(bits + ((long long)k << 52))
+                                                        : ldexp(v, k);  // (zero, subnormal or out of range)
           }
           stg[rl * (UBN + 1) + c] = u;
         }
@@ -248,13 +273,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
     if (!*abort_flag) {
-      for (int rl = warp - 2; rl < UBM; rl += 8) {  // coalesced: a warp per row
+#pragma unroll
+      for (int i = 0; i < UBM / 8; ++i) {
+        const int rl = ew + 8 * i;
         const int64_t p = p0 + rl;
-        if (p >= rows) break;
-        double* dst = M + (base + p) * ldm + base;
-        for (int j = lane; j < UBN; j += 32) {
-          const int64_t q = q0 + j;
-          if (q <= p) dst[q] -= stg[rl * (UBN + 1) + j];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t q = q0 + lane + 32 * h;
+          if (p < rows && q <= p) M[(base + p) * ldm + base + q] = cpre[i][h] - stg[rl * (UBN + 1) + lane + 32 * h];
         }
       }
     }
