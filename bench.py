@@ -599,16 +599,27 @@ def run_ours(args):
                                     sample="the first Newton iteration of the solve from the seeded start at %dx%d, "
                                            "timed whole (direction, psi, step)" % (m, n),
                                     seconds_per_iteration=[round(t, 3) for t in secs])
+    if not args.no_batches and world == 1:
+        # the two batch workloads, timed after the headline region (their own
+        # modes, --batch and --batch-adjoint, print the full records)
+        bt = measure_batch(3, 1)
+        line["batch_512_f32"] = dict(value=round(bt["value"], 1), unit=bt["unit"], ms_per_batch=bt["ms_per_batch"],
+                                     iterations_per_batch=bt["iterations_per_batch"], statuses=bt["statuses"],
+                                     steps=3, warmup=1)
+        ad = measure_batch_adjoint(3, 1)
+        line["adjoint_256_f32"] = dict(forward_ms=ad["forward_ms"], adjoint_ms=ad["adjoint_ms"],
+                                       adjoint_lps_per_s=round(ad["adjoint_lps_per_s"], 1),
+                                       adjoint_statuses=ad["adjoint_statuses"], steps=3, warmup=1)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_batch(args):
+def measure_batch(steps, warmup):
     """The batch configuration (512 LPs, m ~ U{16..256}, n = m U{2..4}, FP32,
     gap 1e-7) through pdas_batch: K timed graph replays after W warm-up
-    replays, each from the seeded starts; prints one JSON line (not the
-    headline metric: total Newton iterations of all LPs per second)."""
+    replays, each from the seeded starts.  Returns a record (not the headline
+    metric: total Newton iterations of all LPs per second)."""
     import torch
 
     import paper_1502_03543_gb300 as P
@@ -625,33 +636,37 @@ def run_batch(args):
     x, y, s = x0.clone(), y0.clone(), s0.clone()
     S = P.BatchSolver(pk["m"], pk["n"], A, b, c, x, y, s, tol=spec["tol"])
     times, iters, out = [], 0, None
-    for k in range(args.warmup + args.steps):
+    for k in range(warmup + steps):
         x.copy_(x0)
         y.copy_(y0)
         s.copy_(s0)
         out = S.solve()
-        if k >= args.warmup:
+        if k >= warmup:
             times.append(out["ms"])
             iters += int(out["iters"].sum())
     cfg = S.config()
     S.close()
     ms = float(np.sum(times))
     st, cnt = np.unique(out["status"], return_counts=True)
-    print(json.dumps(dict(metric="Newton iters/s (batch of 512 small LPs)", value=iters / (ms * 1e-3),
-                          unit="Newton iters/s", ms_per_batch=ms / len(times), steps=args.steps, warmup=args.warmup,
-                          iterations_per_batch=iters // len(times), higher_is_better=True,
-                          config=dict(workload="batch_512_f32", count=len(lps), tol=spec["tol"], alpha=0.95,
-                                      buckets=[dict(m_bound=m_, threads=t_, lps=n_) for m_, t_, n_ in cfg]),
-                          statuses={str(int(a)): int(b_) for a, b_ in zip(st, cnt)},
-                          fp64_tier_iterations=int(out["fp64_iters"].sum()),
-                          slowest_lp_ms=float(out["time_us"].max() * 1e-3))))
+    return dict(metric="Newton iters/s (batch of 512 small LPs)", value=iters / (ms * 1e-3),
+                unit="Newton iters/s", ms_per_batch=ms / len(times), steps=steps, warmup=warmup,
+                iterations_per_batch=iters // len(times), higher_is_better=True,
+                config=dict(workload="batch_512_f32", count=len(lps), tol=spec["tol"], alpha=0.95,
+                            buckets=[dict(m_bound=m_, threads=t_, lps=n_) for m_, t_, n_ in cfg]),
+                statuses={str(int(a)): int(b_) for a, b_ in zip(st, cnt)},
+                fp64_tier_iterations=int(out["fp64_iters"].sum()),
+                slowest_lp_ms=float(out["time_us"].max() * 1e-3))
 
 
-def run_batch_adjoint(args):
+def run_batch(args):
+    print(json.dumps(measure_batch(args.steps, args.warmup)))
+
+
+def measure_batch_adjoint(steps, warmup):
     """The differentiable batch (256 LPs of 128 x 384, FP32, gap 1e-6; loss
     sum_i w_i' x*_i, w ~ N(0,1)): the batch solve and pdas_batch_backward
     (every LP's adjoint in one launch per bucket), K timed repetitions after
-    W warm-ups, each from the seeded starts; one JSON line."""
+    W warm-ups, each from the seeded starts.  Returns a record."""
     import torch
 
     import paper_1502_03543_gb300 as P
@@ -670,7 +685,7 @@ def run_batch_adjoint(args):
     w = dv(np.random.default_rng(0).standard_normal(int(pk["n"].sum())))
     S = P.BatchSolver(pk["m"], pk["n"], A, b, c, x, y, s, tol=spec["tol"])
     fwd, bwd = [], []
-    for k in range(args.warmup + args.steps):
+    for k in range(warmup + steps):
         x.copy_(x0)
         y.copy_(y0)
         s.copy_(s0)
@@ -679,21 +694,25 @@ def run_batch_adjoint(args):
         t0 = time.perf_counter()
         dA, db, dc, status = S.backward(w)
         t1 = time.perf_counter()
-        if k >= args.warmup:
+        if k >= warmup:
             fwd.append(out["ms"])
             bwd.append((t1 - t0) * 1e3)
     S.close()
-    print(json.dumps(dict(metric="differentiable batch: forward solve and batched adjoint (256 LPs of 128x384)",
-                          forward_ms=float(np.mean(fwd)), adjoint_ms=float(np.mean(bwd)),
-                          adjoint_lps_per_s=spec["count"] / (float(np.mean(bwd)) * 1e-3),
-                          forward_statuses={str(int(a)): int(n) for a, n in zip(*np.unique(out["status"],
-                                                                                           return_counts=True))},
-                          adjoint_statuses={str(int(a)): int(n) for a, n in zip(*np.unique(status,
-                                                                                           return_counts=True))},
-                          iterations_per_batch=int(out["iters"].sum()), steps=args.steps, warmup=args.warmup,
-                          adjoint_timing="host wall clock around pdas_batch_backward (it synchronises its stream)",
-                          config=dict(workload="adjoint_256_f32", count=spec["count"], m=spec["m"], n=spec["n"],
-                                      tol=spec["tol"], alpha=ALPHA))))
+    return dict(metric="differentiable batch: forward solve and batched adjoint (256 LPs of 128x384)",
+                forward_ms=float(np.mean(fwd)), adjoint_ms=float(np.mean(bwd)),
+                adjoint_lps_per_s=spec["count"] / (float(np.mean(bwd)) * 1e-3),
+                forward_statuses={str(int(a)): int(n) for a, n in zip(*np.unique(out["status"],
+                                                                                 return_counts=True))},
+                adjoint_statuses={str(int(a)): int(n) for a, n in zip(*np.unique(status,
+                                                                                 return_counts=True))},
+                iterations_per_batch=int(out["iters"].sum()), steps=steps, warmup=warmup,
+                adjoint_timing="host wall clock around pdas_batch_backward (it synchronises its stream)",
+                config=dict(workload="adjoint_256_f32", count=spec["count"], m=spec["m"], n=spec["n"],
+                            tol=spec["tol"], alpha=ALPHA))
+
+
+def run_batch_adjoint(args):
+    print(json.dumps(measure_batch_adjoint(args.steps, args.warmup)))
 
 
 def run_woodbury(args):
@@ -777,6 +796,8 @@ def main():
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 form's full solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peak-probe", action="store_true", help="skip the TF32/FP32/FP64 matmul probe")
+    ap.add_argument("--no-batches", action="store_true",
+                    help="skip the summaries of the batch and differentiable-batch workloads")
     ap.add_argument("--ref-budget", type=float, default=200.0,
                     help="reference arm: seconds of oracle iterations to fit the run into")
     ap.add_argument("--kernel", choices=["step", "normal", "factor"], default="step",

@@ -416,10 +416,13 @@ pdas_status factor_solve(pdas_ctx* h, const double* rhs, double* out) {
 }
 
 // rho = r - A(D(A' v)); leaves w = A' v in h->w and ||rho||_inf in sc->rho_norm.
-pdas_status residual(pdas_ctx* h, const void* A, const double* v) {
-  pdas_status s = gemv_t(h, A, v, 2, nullptr, h->u, nullptr, h->w);
+// df: by the double-float passes, for a residual that only starts the
+// conjugate gradients (every residual that decides acceptance, and the w of
+// an accepted direction, come from the FP64 passes).
+pdas_status residual(pdas_ctx* h, const void* A, const double* v, bool df = false) {
+  pdas_status s = gemv_t(h, A, v, 2, nullptr, h->u, nullptr, h->w, df);
   if (s != PDAS_OK) return s;
-  return gemv(h, A, h->u, h->r, h->rho, 1);
+  return gemv(h, A, h->u, h->r, h->rho, 1, df);
 }
 
 // M v (matrix-free, FP64) -> out.
@@ -448,8 +451,13 @@ pdas_status refine(pdas_ctx* h, const void* A, int* ok) {
   const double tol = h->opt.refine_tol, be_tol = h->opt.refine_be;
   const int cap = h->opt.refine_max;
   pdas_status s;
-  auto true_residual = [&]() -> pdas_status {
-    pdas_status t = residual(h, A, h->dy);  // rho, ||rho||, w = A'dy
+  // With an FP32 factor the first residual is ~1e-7 of r and starts the
+  // conjugate gradients: the double-float passes form it (two FP64 passes
+  // saved per direction); a first residual that would be accepted is formed
+  // again by the FP64 passes.
+  const bool cheap_first = df_passes(h) && !h->cur_f64;
+  auto true_residual = [&](bool df = false) -> pdas_status {
+    pdas_status t = residual(h, A, h->dy, df);  // rho, ||rho||, w = A'dy
     if (t != PDAS_OK) return t;
     KL(launch_absmax(h->st, h->m, h->dy, h->part, h->tickets, h->sc, 2), 1);
     if ((t = read_scalars(h)) != PDAS_OK) return t;
@@ -464,11 +472,16 @@ pdas_status refine(pdas_ctx* h, const void* A, int* ok) {
     *rz = h->sc_host->dot_a;
     return device_status(h);
   };
-  if ((s = true_residual()) != PDAS_OK) return s;
+  if ((s = true_residual(cheap_first)) != PDAS_OK) return s;
   const double rn = h->sc_host->rnorm > 0 ? h->sc_host->rnorm : 1.0;
   const double mn = h->sc_host->mnorm;
   auto accepted = [&](double res, double dyn) { return res <= tol * rn || res <= be_tol * (mn * dyn + rn); };
   double res = h->sc_host->rho_norm, dyn = h->sc_host->dynorm;
+  if (cheap_first && accepted(res, dyn)) {  // acceptance is decided on the FP64 passes
+    if ((s = true_residual()) != PDAS_OK) return s;
+    res = h->sc_host->rho_norm;
+    dyn = h->sc_host->dynorm;
+  }
   int its = 0;
   if (accepted(res, dyn)) {
     *ok = 1;
