@@ -143,6 +143,9 @@ typedef struct {
                            4 tcgen05 tensor cores on fixed-point digit planes (FP64-grade)       */
   double pres, dres;    /* infeasible-start variant: ||b - A x||_inf / (1 + ||b||_inf) and
                            ||c - A'y - s||_inf / (1 + ||c||_inf) after the step (else 0)        */
+  int factor_form;      /* arithmetic of the factor of the accepted direction: 0 FP32 tile factor
+                           (tensor-core products), 1 FP32 blocked SIMT, 2 double-float tile factor,
+                           3 FP64 SIMT, 4 FP64 with tensor-core trailing updates from digit planes */
 } pdas_iter_info;
 
 /* Stages of one iteration, for pdas_profile. */

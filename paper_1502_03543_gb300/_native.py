@@ -61,6 +61,7 @@ class IterInfo(ctypes.Structure):
         ("normal_form", ctypes.c_int),
         ("pres", ctypes.c_double),
         ("dres", ctypes.c_double),
+        ("factor_form", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -66,6 +66,7 @@ struct pdas_ctx {
   bool no_df_once = false;      // the double-float factor failed: form in FP64 this time
   float2* d2 = nullptr;         // D as FP32 pairs (double-float formation)
   int last_normal_form = 3;     // pdas_iter_info.normal_form of the last formation
+  int last_factor_form = 3;     // pdas_iter_info.factor_form of the last factor
   bool have_factor = false;     // a factor from a previous step is in the workspace
   double* adj = nullptr;        // adjoint vectors (5 n + m)
   int4* chol_tasks = nullptr;   // task list of the tile Cholesky (FP32 factor)
@@ -378,6 +379,7 @@ pdas_status factor(pdas_ctx* h) {
     // on the tensor cores from exact digit planes (FP64-grade at every gap);
     // on a failed pivot the next attempt uses the FP64 SIMT factor
     h->last_factor_df = true;
+    h->last_factor_form = 4;
     int k = 0;
     CK(cholesky_dig(h->st, &h->cdig, h->ldm, h->M64, h->dinv64, h->sc, &k));
     h->launches += k;
@@ -388,15 +390,22 @@ pdas_status factor(pdas_ctx* h) {
     // FP64 tier of a mixed form: the double-float tile factor (FP32 pipes),
     // while the iterate is not yet close to the optimum
     h->last_factor_df = true;
+    h->last_factor_form = 2;
     KL(cholesky_tiles_df(h->st, h->m, h->ldm, h->M64, h->dinv64, h->chol_tasks, h->chol_ntasks, h->chol_state,
                          h->tickets + T_CHOL, h->sc),
        4);
-  } else if (h->cur_f64) KL(cholesky<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->sc), chol_launches(h->m));
-  else if (h->chol_ntasks == 0) KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->sc), chol_launches(h->m));
-  else
+  } else if (h->cur_f64) {
+    h->last_factor_form = 3;
+    KL(cholesky<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->sc), chol_launches(h->m));
+  } else if (h->chol_ntasks == 0) {
+    h->last_factor_form = 1;
+    KL(cholesky<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->sc), chol_launches(h->m));
+  } else {
+    h->last_factor_form = 0;
     KL(cholesky_tiles<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->uinv32, h->chol_tasks, h->chol_ntasks,
                              h->chol_state, h->tickets + T_CHOL, h->sc, h->chol_planes),
        1);
+  }
   return PDAS_OK;
 }
 
@@ -633,6 +642,7 @@ void fill_info(pdas_ctx* h, pdas_iter_info* info, bool stepped) {
   info->fp64_reason = (h->last_fp64 && is_mixed(h)) ? h->switch_reason : 0;
   info->factor_columns = (h->last_fp64 && is_mixed(h)) ? h->last_kept : h->n;
   info->normal_form = h->last_normal_form;
+  info->factor_form = h->last_factor_form;
   if (stepped) {
     info->psi = s.psi;
     info->theta = s.theta;

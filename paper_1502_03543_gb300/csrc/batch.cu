@@ -378,9 +378,21 @@ __device__ void blk_syrk_df(const Ctx& c, int m_cap, double* M, int nk) {
 // lower triangle is updated once per panel (16 multiply-adds per entry, one
 // read-modify-write of global memory).  dinv receives 1 / L_kk.  Returns
 // false on a pivot that is not positive and finite.
+// The pivot's square root and reciprocal are formed once, by thread 0 (which
+// updates the next diagonal entry first), and passed on in shared memory:
+// FP64 runs at a small fraction of the FP32 rate, and the same two
+// operations in every thread would cost more than the column's update.
+__device__ __forceinline__ void post_pivot(double d, double* slot) {
+  const bool ok = d > 0.0 && isfinite(d);
+  const double lkk = ok ? sqrt(d) : -1.0;
+  slot[0] = lkk;
+  slot[1] = ok ? 1.0 / lkk : 0.0;
+}
+
 template <int T>
 __device__ bool blk_chol64(const Ctx& c, double* L, double* dinv) {
   constexpr int NW = T / 32, PW = 16, PP = 17;
+  __shared__ double piv[2][2];  // (L_kk, 1 / L_kk) of the next two columns; L_kk < 0: not positive definite
   const int m = c.m, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   double* P = reinterpret_cast<double*>(c.stage);
   for (int k0 = 0; k0 < m; k0 += PW) {
@@ -391,10 +403,11 @@ __device__ bool blk_chol64(const Ctx& c, double* L, double* dinv) {
       P[r * PP + cc] = (cc < kb && cc <= r) ? L[pk(k0 + r, k0 + cc)] : 0.0;
     }
     __syncthreads();
+    if (threadIdx.x == 0) post_pivot(P[0], piv[0]);
+    __syncthreads();
     for (int cc = 0; cc < kb; ++cc) {
-      const double d = P[cc * PP + cc];
-      if (!(d > 0.0) || !isfinite(d)) return false;
-      const double lkk = sqrt(d), rs = 1.0 / lkk;
+      const double lkk = piv[cc & 1][0], rs = piv[cc & 1][1];
+      if (lkk < 0.0) return false;
       for (int r = cc + 1 + threadIdx.x; r < R; r += T) P[r * PP + cc] *= rs;
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -404,7 +417,10 @@ __device__ bool blk_chol64(const Ctx& c, double* L, double* dinv) {
       const int nc = kb - cc - 1;  // later panel columns
       for (int e = threadIdx.x; e < (R - cc - 1) * nc; e += T) {
         const int r = cc + 1 + e / nc, q = cc + 1 + e % nc;
-        if (q <= r) P[r * PP + q] = fma(-P[r * PP + cc], P[q * PP + cc], P[r * PP + q]);
+        if (q <= r) {
+          P[r * PP + q] = fma(-P[r * PP + cc], P[q * PP + cc], P[r * PP + q]);
+          if (e == 0) post_pivot(P[r * PP + q], piv[(cc + 1) & 1]);  // thread 0: entry (cc + 1, cc + 1)
+        }
       }
       __syncthreads();
     }

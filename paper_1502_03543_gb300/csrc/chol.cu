@@ -16,7 +16,6 @@
 // the blocks it depends on, so a block only waits on blocks that were handed
 // out earlier and are running or done -- no deadlock.  On a timeout it sets
 // PDAS_ERR_TIMEOUT and returns.
-#include "chol_dig.cuh"
 #include "sync_util.cuh"
 #include "tile_core.cuh"
 
@@ -29,26 +28,40 @@ __device__ __forceinline__ bool pivot_bad(T d) {
   return !(d > T(0)) || !isfinite(d);
 }
 
+// 1 / sqrt(d) of a pivot, or -1 for a pivot that is not positive and finite.
+template <typename T>
+__device__ __forceinline__ T pivot_rp(T d) {
+  return pivot_bad(d) ? T(-1) : T(1) / sqrt(d);
+}
+
 // Factor the kb x kb diagonal block held in shared memory (lower triangle).
-// Right-looking by columns with two barriers per column: every thread reads
-// the updated pivot d_c = Ld[c][c] itself (no thread writes the diagonal
-// during the loop; it is replaced by sqrt(d_c) at the end), scales column c
-// below the diagonal, then updates the trailing block.  Thread (ti, tj) =
-// (tid / 16, tid % 16) updates rows ti + 16 k and columns tj + 16 l.
+// Right-looking by columns with two barriers per column: column c is scaled
+// by rp_c = 1 / sqrt(d_c), d_c = Ld[c][c] (no thread writes the diagonal
+// during the loop; it is replaced by sqrt(d_c) at the end), then the trailing
+// block is updated.  Thread (ti, tj) = (tid / 16, tid % 16) updates rows
+// ti + 16 k and columns tj + 16 l.  rp_c is computed once, by thread 0, as
+// soon as d_c is final (thread 0 updates entry (c, c) first in the update of
+// column c - 1) and passed on in shared memory: on GPUs whose FP64 pipes run
+// at a small fraction of the FP32 rate, a square root and a division in
+// every thread would cost more than the whole update.
 // Returns -1 or the local index of the failing pivot (same in all threads).
 template <typename T>
 __device__ int factor_diag(T (*Ld)[kTile + 1], int kb) {
+  __shared__ T s_rp[2];
   const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  if (threadIdx.x == 0 && kb > 0) s_rp[0] = pivot_rp(Ld[0][0]);
   for (int c = 0; c < kb; ++c) {
-    __syncthreads();  // the trailing update of column c - 1 is complete
-    const T d = Ld[c][c];
-    if (pivot_bad(d)) return c;
-    const T rp = T(1) / sqrt(d);
+    __syncthreads();  // the trailing update of column c - 1 is complete, rp_c posted
+    const T rp = s_rp[c & 1];
+    if (rp < T(0)) return c;
     for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) Ld[r][c] *= rp;
     __syncthreads();  // column c is scaled
     for (int i = c + 1 + ti; i < kb; i += 16) {
       const T lic = Ld[i][c];
-      for (int j = c + 1 + tj; j <= i; j += 16) Ld[i][j] -= lic * Ld[j][c];
+      for (int j = c + 1 + tj; j <= i; j += 16) {
+        Ld[i][j] -= lic * Ld[j][c];
+        if (i == c + 1 && j == c + 1) s_rp[(c + 1) & 1] = pivot_rp(Ld[i][j]);  // thread 0: d_c+1 is final
+      }
     }
   }
   __syncthreads();
@@ -354,13 +367,6 @@ cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Sca
       k_chol_update<T><<<(unsigned)(tu * (tu + 1) / 2), kThreads, update_smem_bytes<T>(), st>>>(m, ldm, M, k0, kb,
                                                                                               sc);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t chol_panel64(cudaStream_t st, int64_t m, int64_t ldm, double* M, double* dinv, int64_t k0, int kb,
-                         Scalars* sc) {
-  const int64_t t = (m - k0 - kb + kTile - 1) / kTile;
-  k_chol_panel<double><<<(unsigned)(1 + t), kThreads, 0, st>>>(m, ldm, M, dinv, k0, kb, sc);
   return cudaGetLastError();
 }
 

@@ -3,13 +3,15 @@
 // tcgen05 tensor cores, exactly, from fixed-point BF16 digit planes.
 //
 // Per 64-column panel k0 (kb = min(64, m - k0) columns):
-//   k_chol_panel<double> (chol.cu)  -- the FP64 panel: diagonal block factor,
-//                                      the panel rows solved against it;
-//   k_panel_digits                  -- row r of the panel P (trailing rows
-//                                      r >= k0 + kb, the kb panel columns) as
-//                                      7 balanced base-256 digits of
-//                                      P_rc 2^-e_r, e_r the exponent of the
-//                                      row's largest |P_rc|:
+//   k_dig_diag                      -- the FP64 factor L_11 of the diagonal
+//                                      block (LDL' form) and 1 / L_cc;
+//   k_dig_panel_rows                -- the panel rows P (trailing rows
+//                                      r >= k0 + kb, the kb panel columns)
+//                                      solved in FP64, P L_11' = B, 32 rows
+//                                      per CTA over every SM; each row then
+//                                      written as 7 balanced base-256 digits
+//                                      of P_rc 2^-e_r, e_r the exponent of
+//                                      the row's largest |P_rc|:
 //                                      P_rc = 2^e_r sum_s d_s 2^(-7-8s);
 //   k_dig_update                    -- C_pq -= (P P')_pq over the lower tiles
 //                                      (128 rows p x 64 columns q) of the
@@ -19,13 +21,15 @@
 //      every digit product an integer of magnitude <= 2^14, at most 7 pairs
 //      per weight and kb <= 64 columns: |I_w| < 2^23, so the tensor core's
 //      FP32 accumulator holds I_w exactly.  The epilogue combines the eight
-//      weights exactly in int64, converts once to FP64 and subtracts from C
-//      in FP64.
+//      weights into one int64 (the last two rounded to 2^-43 of the sum),
+//      builds the double on the integer pipes and subtracts it from C in
+//      FP64.
 // The only roundings of an update are the digits of entries below 1/8 of
 // their row's largest (to 2^-56 of 2^e_r), the digit pairs of weight 8 and
-// more left out (at most 2^-62 of 2^(e_p + e_q) per column) and the final
-// FP64 combination and subtraction: FP64-grade, where the FP64 pipes would
-// take 1/64 of the FP32 rate.
+// more left out (at most 2^-62 of 2^(e_p + e_q) per column), the rounding of
+// the two lowest weights (2^-57 of 2^(e_p + e_q)), the conversion to FP64 and
+// the subtraction: FP64-grade, where the FP64 pipes would take 1/64 of the
+// FP32 rate.
 //
 // k_dig_update: one CTA per 128 x 64 tile, 10 warps:
 //   warp 0      one TMA load of the 7 planes for rows p (128 x 64 columns)
@@ -90,6 +94,27 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// z 2^k as a double, rounded to nearest (ties to even), built on the
+// integer pipes: the leading one of |z| found by a count of leading zeros,
+// the 53-bit significand shifted out and rounded, the exponent field set to
+// the position of the leading one plus k.  Subnormal and overflowing
+// results take the FP64 path.
+__device__ __forceinline__ double scaled_int_to_double(long long z, int k) {
+  if (z == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)z & 0x8000000000000000ull;
+  const unsigned long long a = z < 0 ? 0ull - (unsigned long long)z : (unsigned long long)z;
+  const int lz = __clzll((long long)a);
+  const unsigned long long nrm = a << lz;  // leading one at bit 63
+  unsigned long long mant = nrm >> 11;     // leading one at bit 52
+  const unsigned rest = (unsigned)nrm & 0x7ffu;
+  mant += (rest > 0x400u || (rest == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  const int ex = 1023 + 63 - lz + k;  // biased exponent of |z| 2^k
+  if (ex <= 0 || ex >= 2046) return ldexp((double)z, k);
+  // the leading one of mant adds 1 to the field (2 when the rounding carried
+  // into bit 53, which is then the right exponent with a zero fraction)
+  return __longlong_as_double((long long)(sgn | (((unsigned long long)(ex - 1) << 52) + mant)));
+}
+
 // Balanced base-256 digits of the integer v: dig[ND - 1] the lowest, each in
 // [-128, 128].
 __device__ __forceinline__ void balanced_digits(long long v, int (&dig)[ND]) {
@@ -102,17 +127,137 @@ __device__ __forceinline__ void balanced_digits(long long v, int (&dig)[ND]) {
   dig[0] = (int)v;
 }
 
-// The digits of the panel rows r = k0 + kb + i (i < rows) into planes (7
-// planes of mpad rows x 64 columns, BF16), and their exponents into e[i].
-// One warp per row: the lanes hold columns 2 lane and 2 lane + 1.
-__global__ void k_panel_digits(int64_t ldm, const double* __restrict__ M, int64_t k0, int kb, int64_t rows,
-                               int64_t mpad, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < rows;
-       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const double* row = M + (k0 + kb + i) * ldm + k0;
-    const int c0 = 2 * lane, c1 = 2 * lane + 1;
-    const double v0 = c0 < kb ? row[c0] : 0.0, v1 = c1 < kb ? row[c1] : 0.0;
+// 1 / d of a pivot d, or -1 when d is not positive and finite or its
+// reciprocal overflows.
+__device__ __forceinline__ double inv_pivot(double d) {
+  const double r = 1.0 / d;
+  return (d > 0.0 && isfinite(d) && isfinite(r)) ? r : -1.0;
+}
+
+// The FP64 factor of the kb x kb diagonal block of panel k0 (kb <= 64) by one
+// CTA, right-looking in the LDL' form: the update for column c subtracts
+// (M_ic / d_c) M_jc from the trailing entries, so the chain from one column
+// to the next is one reciprocal 1 / d_c (formed by thread 0 right after its
+// update of d_c) and one barrier; the square roots and the scaling
+// L_ic = M_ic / sqrt(d_c) then run for all columns at once.  (On GB300 a
+// dependent FP64 operation takes ~64 cycles, a square root ~675 and a
+// reciprocal ~430: the Cholesky form puts both on the chain.)  Writes L_11
+// (lower triangle and diagonal) to M and 1 / L_cc to dinv[k0 + c]; a pivot
+// that is not positive and finite sets PDAS_ERR_NOT_SPD with its index.
+constexpr int DG_THREADS = 256;
+__global__ void __launch_bounds__(DG_THREADS) k_dig_diag(int64_t ldm, double* __restrict__ M,
+                                                         double* __restrict__ dinv, int64_t k0, int kb, Scalars* sc) {
+  __shared__ double Ld[UK][UK + 1];
+  __shared__ double s_inv[2];  // 1 / d_c of the next column; < 0: not positive definite
+  __shared__ double s_rp[UK];
+  if (*(volatile const int*)&sc->status != 0) return;
+  for (int t = threadIdx.x; t < UK * UK; t += DG_THREADS) {
+    const int i = t / UK, j = t % UK;
+    if (j <= i && i < kb) Ld[i][j] = M[(k0 + i) * ldm + k0 + j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s_inv[0] = inv_pivot(Ld[0][0]);
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;  // rows ti + 16 a, columns tj + 16 b
+  int fail = -1;
+  for (int c = 0; c < kb; ++c) {
+    __syncthreads();  // the update for column c - 1 is complete and 1 / d_c posted
+    const double inv = s_inv[c & 1];
+    if (inv < 0.0) {
+      fail = c;
+      break;
+    }
+    for (int i = c + 1 + ti; i < kb; i += 16) {
+      const double t = Ld[i][c] * inv;
+      for (int j = c + 1 + tj; j <= i; j += 16) {
+        Ld[i][j] = fma(-t, Ld[j][c], Ld[i][j]);
+        if (i == c + 1 && j == c + 1) s_inv[(c + 1) & 1] = inv_pivot(Ld[i][j]);  // thread 0: d_c+1 is final
+      }
+    }
+  }
+  if (fail >= 0) {  // every thread read the same pivot
+    if (threadIdx.x == 0 && atomicCAS(&sc->status, 0, (int)PDAS_ERR_NOT_SPD) == 0) sc->fail_index = (int)(k0 + fail);
+    return;
+  }
+  __syncthreads();
+  if (threadIdx.x < kb) {
+    const double l = sqrt(Ld[threadIdx.x][threadIdx.x]);
+    Ld[threadIdx.x][threadIdx.x] = l;
+    s_rp[threadIdx.x] = 1.0 / l;
+    dinv[k0 + threadIdx.x] = s_rp[threadIdx.x];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < UK * UK; t += DG_THREADS) {
+    const int i = t / UK, j = t % UK;
+    if (j <= i && i < kb) M[(k0 + i) * ldm + k0 + j] = j < i ? Ld[i][j] * s_rp[j] : Ld[i][i];
+  }
+}
+
+// k_dig_panel_rows: one warp per CTA and 8 rows per warp, so that a panel
+// with few trailing rows still spreads over every SM (the solve is bound by
+// the FP64 pipes, ~2 multiply-adds per cycle per SM on GB300).
+constexpr int PR_ROWS = 8;                        // panel rows per CTA
+constexpr int PR_THREADS = 4 * PR_ROWS;           // four threads per row
+
+// The panel rows r = k0 + kb + i (i < rows): X L_11' = B in FP64 (B the kb
+// panel columns of the rows, L_11 and 1 / L_cc from the diagonal factor),
+// X written back to M; then the digits of X into planes (7 planes of mpad
+// rows x 64 columns, BF16) and the row exponents into e[i].
+// Solve: thread (row, part) holds columns part, part + 4, ... of its row in
+// registers and sweeps the columns right-looking, the owner of column c
+// passing x_c to its row's other three threads.  Digits: one warp per row,
+// the lanes holding columns 2 lane and 2 lane + 1 (16-byte-aligned rows of
+// every plane written whole by the warp).
+__global__ void __launch_bounds__(PR_THREADS) k_dig_panel_rows(int64_t ldm, double* __restrict__ M,
+                                                             const double* __restrict__ dinv, int64_t k0, int kb,
+                                                             int64_t rows, int64_t mpad, int* __restrict__ e,
+                                                             __nv_bfloat16* __restrict__ planes, const Scalars* sc) {
+  __shared__ double Lt[UK][UK + 1];  // L_11 strictly below the diagonal; then the solved rows
+  __shared__ double rcp[UK];
+  if (*(volatile const int*)&sc->status != 0) return;  // a pivot of the diagonal factor failed
+  for (int t = threadIdx.x; t < UK * UK; t += PR_THREADS) {  // the solve reads only Lt[i][j], j < i < kb
+    const int i = t / UK, j = t % UK;
+    if (j < i && i < kb) Lt[i][j] = M[(k0 + i) * ldm + k0 + j];
+  }
+  for (int t = threadIdx.x; t < UK; t += PR_THREADS) rcp[t] = t < kb ? dinv[k0 + t] : 0.0;
+  __syncthreads();
+  const int row = threadIdx.x >> 2, part = threadIdx.x & 3;
+  const int64_t r0 = (int64_t)blockIdx.x * PR_ROWS;
+  const bool live = r0 + row < rows;
+  double* mrow = M + (live ? (k0 + kb + r0 + row) * ldm + k0 : 0);
+  double x[UK / 4];
+#pragma unroll
+  for (int k = 0; k < UK / 4; ++k) {
+    const int c = part + 4 * k;
+    x[k] = (live && c < kb) ? mrow[c] : 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < UK; ++c) {
+    if (c < kb) {
+      const int owner = c & 3;
+      double xc = (part == owner) ? x[c >> 2] * rcp[c] : 0.0;
+      xc = __shfl_sync(0xffffffffu, xc, (threadIdx.x & 31 & ~3) | owner);
+      if (part == owner) x[c >> 2] = xc;
+#pragma unroll
+      for (int k = 0; k < UK / 4; ++k) {
+        const int cp = part + 4 * k;
+        if (cp > c && cp < kb) x[k] -= xc * Lt[cp][c];
+      }
+    }
+  }
+  __syncthreads();  // every thread is done with L_11
+  double (*X)[UK + 1] = Lt;
+#pragma unroll
+  for (int k = 0; k < UK / 4; ++k) {
+    const int c = part + 4 * k;
+    X[row][c] = c < kb ? x[k] : 0.0;
+    if (live && c < kb) mrow[c] = x[k];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rr = warp; rr < PR_ROWS; rr += PR_THREADS / 32) {
+    const int64_t i = r0 + rr;
+    if (i >= rows) break;
+    const double v0 = X[rr][2 * lane], v1 = X[rr][2 * lane + 1];
     double mx = fmax(fabs(v0), fabs(v1));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -149,7 +294,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   // tile (I, J) of block b: I = the largest with I (I + 1) <= b
   const int64_t b = blockIdx.x;
-  int64_t I = (int64_t)((sqrt(4.0 * (double)b + 1.0) - 1.0) * 0.5);
+  int64_t I = (int64_t)((sqrtf(4.0f * (float)b + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
   while (I * (I + 1) > b) --I;
   while ((I + 1) * (I + 2) <= b) ++I;
   const int64_t J = b - I * (I + 1);
@@ -230,26 +375,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int rl = quarter * 32 + lane;
       const int64_t p = p0 + rl;
       const int ep = p < rows ? e[p] : 0;
-      // GB300 runs FP64 at 1/64 of the FP32 rate: the weights are combined
-      // exactly on the integer pipes, hi = I_0 2^24 + I_1 2^16 + I_2 2^8 + I_3
-      // and lo = I_4 2^24 + ... + I_7 (|I_w| < 2^23: both below 2^48), and
-      // sum_w 2^-8w I_w = 2^-24 (hi + 2^-32 lo) takes two conversions and one
-      // FP64 multiply-add; the power-of-two scale is an integer add to the
-      // exponent field
+      // GB300 runs FP64 at 1/64 of the FP32 rate, so the weights are
+      // combined on the integer pipes into one integer,
+      //   Z = sum_{w<=5} I_w 2^(42-8w) + round((I_6 2^8 + I_7) 2^-14)
+      // (|I_w| <= 7 2^20 and |I_0| <= 2^20: |Z| < 2^63; the rounding is
+      // 2^-43 of sum_w 2^-8w I_w, below the digits' own truncation), and
+      // Z 2^(e_p + e_q - 56) is built as a double on the integer pipes too:
+      // the subtraction from C is the one FP64 operation of an entry
 #pragma unroll
       for (int g = 0; g < 4; ++g) {  // 8 columns at a time
-        long long hi[8], lo[8];
+        long long z[8];
+        int t[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0;
+        for (int j = 0; j < 8; ++j) {
+          z[j] = 0;
+          t[j] = 0;
+        }
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
           uint32_t r[8];
           tmem_ld8(lane_addr + (uint32_t)(w * UBN + g * 8), r);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
-            if (w < 4) hi[j] += v * (1ll << (8 * (3 - w)));
-            else lo[j] += v * (1ll << (8 * (7 - w)));
+            const int v = __float2int_rn(__uint_as_float(r[j]));
+            if (w <= 5) z[j] += (long long)v * (1ll << (42 - 8 * w));
+            else if (w == 6) t[j] = v * 256;
+            else t[j] += v;
           }
         }
 #pragma unroll
@@ -257,14 +408,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int c = half * 32 + g * 8 + j;
           const int64_t q = q0 + c;
           double u = 0.0;
-          if (q < rows) {
-            const int k = ep + e[q] - 38;  // 2^(e_p + e_q - 14) times 2^-24
-            const double v = fma((double)lo[j], 0x1p-32, (double)hi[j]);
-            const long long bits = __double_as_longlong(v);
-            const int ev = (int)((bits >> 52) & 0x7ff);
-            u = (ev > 0 && ev + k > 0 && ev + k < 2047) ? __longlong_as_double(bits + ((long long)k << 52))
-                                                        : ldexp(v, k);  // (zero, subnormal or out of range)
-          }
+          if (q < rows) u = scaled_int_to_double(z[j] + ((t[j] + 8192) >> 14), ep + e[q] - 56);
           stg[rl * (UBN + 1) + c] = u;
         }
       }
@@ -365,12 +509,12 @@ cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, doub
   for (int64_t k0 = 0; k0 < m && e == cudaSuccess; k0 += UK) {
     const int kb = (int)std::min<int64_t>(UK, m - k0);
     const int64_t rows = m - k0 - kb;  // the trailing matrix
-    e = chol_panel64(st, m, ldm, M, dinv, k0, kb, sc);
+    k_dig_diag<<<1, DG_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, sc);
     ++*launches;
+    e = cudaGetLastError();
     if (e != cudaSuccess || rows == 0) continue;
-    const unsigned dgrid = (unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 4736);
-    k_panel_digits<<<dgrid, 256, 0, st>>>(ldm, M, k0, kb, rows, w->mpad, w->e,
-                                          static_cast<__nv_bfloat16*>(w->planes));
+    k_dig_panel_rows<<<(unsigned)((rows + PR_ROWS - 1) / PR_ROWS), PR_THREADS, 0, st>>>(
+        ldm, M, dinv, k0, kb, rows, w->mpad, w->e, static_cast<__nv_bfloat16*>(w->planes), sc);
     const int64_t nI = (rows + UBM - 1) / UBM;
     k_dig_update<<<(unsigned)(nI * (nI + 1)), NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb,
                                                                              rows, w->e, sc);

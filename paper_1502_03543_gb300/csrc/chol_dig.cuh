@@ -23,16 +23,11 @@ cudaError_t chol_dig_create(CholDigWorkspace* w, int64_t m);
 void chol_dig_destroy(CholDigWorkspace* w);
 
 // In place M = L L' (lower triangle, leading dimension ldm, m = w->m) in FP64
-// by 64-column panels: the FP64 panel kernel, then the trailing update on
-// the tensor cores.  dinv (m) receives 1 / L_pp.  A pivot that is not
+// by 64-column panels: the diagonal block's FP64 factor, the panel rows'
+// FP64 solve and digits, then the trailing update on the tensor cores.  dinv (m) receives 1 / L_pp.  A pivot that is not
 // positive sets PDAS_ERR_NOT_SPD (index in sc->fail_index).  *launches
 // receives the kernels started.
 cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, double* M, double* dinv, Scalars* sc,
                          int* launches);
-
-// One FP64 panel of the blocked factor (chol.cu): columns k0 .. k0 + kb - 1,
-// kb <= 64, with the trailing matrix not yet updated by it.
-cudaError_t chol_panel64(cudaStream_t st, int64_t m, int64_t ldm, double* M, double* dinv, int64_t k0, int kb,
-                         Scalars* sc);
 
 }  // namespace pdas

@@ -48,6 +48,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <vector>
 
@@ -251,35 +252,77 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// The prepass reads BF16 A and FP64 D as bit fields, on the integer pipes
+// (GB300 runs FP64 at 1/64 of the FP32 rate): a finite value is sig 2^e with
+// an integer significand sig (the implicit one included, subnormals as they
+// are).  A_pj D_j is then the exact integer product sig_a sig_d (at most
+// 8 + 53 bits) times 2^(e_a + e_d).
+__device__ __forceinline__ void bf16_fields(uint16_t h, unsigned long long& sig, int& e) {
+  const int E = (h >> 7) & 0xff;
+  sig = (unsigned long long)((h & 0x7fu) | (E ? 0x80u : 0u));
+  e = (E ? E : 1) - 127 - 7;
+}
+__device__ __forceinline__ void f64_fields(unsigned long long bits, unsigned long long& sig, int& e) {
+  const int E = (int)((bits >> 52) & 0x7ff);
+  sig = (bits & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
+  e = (E ? E : 1) - 1023 - 52;
+}
+// frexp exponent of sig 2^e, sig > 0: the bit length of sig plus e.
+__device__ __forceinline__ int frexp_exp(unsigned long long sig, int e) { return 64 - __clzll((long long)sig) + e; }
+
 // Exponents of the kept part of each row: ea_p with max_j |A_pj| < 2^ea_p and
-// eb_p with max_j |D_j A_pj| < 2^eb_p (frexp convention; 0 for a zero row).
-// One warp per row; column i of the kept set is idx[i] (idx null: i).
+// eb_p with max_j |D_j A_pj| < 2^eb_p (frexp convention; 0 for a zero row),
+// eb_p from the exact products.  One warp per row; column i of the kept set
+// is idx[i] (idx null: i).  D > 0.
 __global__ void k_dig_rowexp(int64_t m, int64_t n, const __nv_bfloat16* __restrict__ A, const double* __restrict__ D,
                              int64_t k, const int* __restrict__ idx, int* __restrict__ ea, int* __restrict__ eb) {
   const int lane = threadIdx.x & 31;
+  const uint16_t* Ab = reinterpret_cast<const uint16_t*>(A);
+  const unsigned long long* Db = reinterpret_cast<const unsigned long long*>(D);
   for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < m;
        p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const __nv_bfloat16* row = A + p * n;
-    double amax = 0.0, bmax = 0.0;
+    const uint16_t* row = Ab + p * n;
+    unsigned amag = 0;   // largest |A_pj| as BF16 magnitude bits (ordered like the values)
+    int ebm = INT_MIN;   // largest frexp exponent of A_pj D_j
     for (int64_t i = lane; i < k; i += 32) {
       const int64_t j = idx ? idx[i] : i;
-      const double a = fabs((double)__bfloat162float(row[j]));
-      amax = fmax(amax, a);
-      bmax = fmax(bmax, a * D[j]);
+      const uint16_t h = row[j];
+      const unsigned mag = h & 0x7fffu;
+      if (mag == 0) continue;
+      amag = max(amag, mag);
+      unsigned long long sa, sd;
+      int e_a, e_d;
+      bf16_fields(h, sa, e_a);
+      f64_fields(__ldg(Db + j), sd, e_d);
+      ebm = max(ebm, frexp_exp(sa * sd, e_a + e_d));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+      amag = max(amag, __shfl_xor_sync(0xffffffffu, amag, o));
+      ebm = max(ebm, __shfl_xor_sync(0xffffffffu, ebm, o));
     }
     if (lane == 0) {
-      int e1 = 0, e2 = 0;
-      if (amax > 0.0) frexp(amax, &e1);
-      if (bmax > 0.0) frexp(bmax, &e2);
+      int e1 = 0;
+      if (amag) {
+        unsigned long long sa;
+        int e_a;
+        bf16_fields((uint16_t)amag, sa, e_a);
+        e1 = frexp_exp(sa, e_a);
+      }
       ea[p] = e1;
-      eb[p] = e2;
+      eb[p] = ebm == INT_MIN ? 0 : ebm;
     }
   }
+}
+
+// v 2^s rounded to the nearest integer (ties to even), v >= 0; for s >= 0 the
+// caller keeps v 2^s below 2^63.
+__device__ __forceinline__ unsigned long long shift_rne(unsigned long long v, int s) {
+  if (s >= 0) return v << s;
+  const int r = -s;
+  if (r >= 64) return 0ull;  // v < 2^61: below half of 2^r
+  const unsigned long long q = v >> r, rem = v & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+  return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
 }
 
 // Balanced base-256 digits of the integer v (|v| < 2^(8 ND - 1) + 2^7):
@@ -302,10 +345,12 @@ __device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
 
 // The digit planes: plane s of A (SA planes) and plane t of B (SB planes),
 // each mpad rows of stride kstride BF16, for the kept columns i < k (and
-// zeros up to the next multiple of 64).  a' 2^39 and b' 2^63 are integers
-// (up to the rounding of entries below 2^-32 and 2^-11 of the row's
-// largest), and their balanced base-256 digits are the planes' entries.
-// One thread writes 8 consecutive columns of one row to every plane.
+// zeros up to the next multiple of 64).  a' = A_pj 2^(39 - ea_p) and
+// b' = A_pj D_j 2^(63 - eb_p) rounded to integers (exact except for entries
+// below 2^-32 of the row's largest in a' and for the bits of the exact
+// product below 2^-63 of 2^eb_p in b'), both on the integer pipes; their
+// balanced base-256 digits are the planes' entries.  One thread writes 8
+// consecutive columns of one row to every plane.
 __global__ void k_dig_planes(int64_t m, int64_t n, const __nv_bfloat16* __restrict__ A, const double* __restrict__ D,
                              int64_t k, int64_t kfill, const int* __restrict__ idx, const int* __restrict__ ea,
                              const int* __restrict__ eb, int64_t mpad, int64_t kstride,
@@ -315,19 +360,28 @@ __global__ void k_dig_planes(int64_t m, int64_t n, const __nv_bfloat16* __restri
   const int64_t plane = mpad * kstride;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = g / groups, i0 = (g % groups) * 8;
-    const double sa = ldexp(1.0, 39 - ea[p]), sb = ldexp(1.0, 63 - eb[p]);
+    const int sha = 39 - ea[p], shb = 63 - eb[p];
     int da[8][SA], db[8][SB];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int64_t i = i0 + e;
-      double a = 0.0, b = 0.0;
+      long long av = 0, bv = 0;
       if (i < k) {
         const int64_t j = idx ? idx[i] : i;
-        a = (double)__bfloat162float(A[p * n + j]);
-        b = a * D[j];
+        const uint16_t h = reinterpret_cast<const uint16_t*>(A)[p * n + j];
+        unsigned long long sa, sd;
+        int e_a, e_d;
+        bf16_fields(h, sa, e_a);
+        f64_fields(__ldg(reinterpret_cast<const unsigned long long*>(D) + j), sd, e_d);
+        av = (long long)shift_rne(sa, e_a + sha);
+        bv = (long long)shift_rne(sa * sd, e_a + e_d + shb);
+        if (h & 0x8000u) {
+          av = -av;
+          bv = -bv;
+        }
       }
-      balanced_digits<SA>(__double2ll_rn(a * sa), da[e]);
-      balanced_digits<SB>(__double2ll_rn(b * sb), db[e]);
+      balanced_digits<SA>(av, da[e]);
+      balanced_digits<SB>(bv, db[e]);
     }
     __nv_bfloat16* rowp = planes + p * kstride + i0;
 #pragma unroll

@@ -129,7 +129,7 @@ __device__ void tile128_rank_k(const TIn* __restrict__ P, int64_t ldp, int64_t p
 
 // Lower-triangle tile index t -> (ti, tj) with ti >= tj.
 __device__ __forceinline__ void lower_tile(int64_t t, int64_t& ti, int64_t& tj) {
-  int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  int64_t i = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
   while (i * (i + 1) / 2 > t) --i;
   while ((i + 1) * (i + 2) / 2 <= t) ++i;
   ti = i;

@@ -210,9 +210,10 @@ def test_tensor_core_fp64_factor_full_size(pdas, case):
     with pdas.Solver(m, n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
         _, _, _, info = S.direction(A, x0, s0)
         assert info["used_fp64"] == 1
+        assert info["factor_form"] == 4, info  # the tensor-core factor, not a fallback after a failed pivot
         S.form_normal(A, x0, s0)
         M = host64(S.copy_matrix())
-        S.factor()
+        S.factor()  # raises on a failed pivot (no fallback inside pdas_factor)
         L = np.tril(host64(S.copy_matrix()))
         d = np.sqrt(np.diag(M))
         absL = np.abs(L)

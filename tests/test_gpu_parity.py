@@ -739,6 +739,26 @@ def test_fp64_tier_whole_solve(pdas, storage):
     assert np.linalg.norm(lp.A64.T @ yh + sh - lp.c) <= 1e-12 * np.linalg.norm(lp.c)
 
 
+def test_tensor_core_factor_whole_solve(pdas):
+    """BF16 A forced into the FP64 tier from the first iteration at m = 320
+    (above the size where the tier's factor moves to the tensor cores: five
+    64-column panels, ragged trailing tiles): every iteration's direction
+    comes from the digit-plane normal matrix and the tensor-core factor (no
+    fallback after a failed pivot), and the solve reaches the oracle's
+    objective in the oracle's number of iterations."""
+    lp = lpgen.generate(320, 1280, seed=23, storage="bf16", scaled=True)
+    ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
+    x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
+    A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
+    with pdas.Solver(lp.m, lp.n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
+        for k in range(ref["iters"]):
+            st, info = S.step(A, b, c, x, y, s, alpha=0.95)
+            assert info["used_fp64"] == 1 and info["normal_form"] == 4 and info["factor_form"] == 4, (k, info)
+    assert info["rel_gap"] < 1e-8
+    obj_ref = float(lp.c @ ref["x"])
+    assert abs(float(lp.c @ host(x)) - obj_ref) <= 1e-8 * abs(obj_ref)
+
+
 def test_stop_rules_match_oracle(pdas):
     """The cap and the stall rule of pdas_solve against the oracle's (both are
     readings: the paper states neither).  A run capped at 3 iterations
