@@ -67,6 +67,7 @@ constexpr int ND = 7;                             // digits per entry (55 bits)
 constexpr int WMAX = 7;                           // largest pair weight kept
 constexpr int NW = WMAX + 1;
 constexpr int NPAIR = 34;                         // pairs (s, t), s, t < 7, s + t <= 7
+static_assert(NPAIR == 7 + 7 + 6 + 5 + 4 + 3 + 2, "pair count");
 constexpr uint32_t P_PLANE = UBM * 128;           // 16 KB: 128 rows of one digit
 constexpr uint32_t Q_PLANE = UBN * 128;           // 8 KB: 64 rows of one digit
 constexpr uint32_t LOAD_BYTES = ND * (P_PLANE + Q_PLANE);  // 168 KB
@@ -127,51 +128,70 @@ __device__ __forceinline__ void balanced_digits(long long v, int (&dig)[ND]) {
   dig[0] = (int)v;
 }
 
+// GB300's FP64 pipes take ~64 cycles per warp instruction per SM
+// sub-partition, whatever the number of active lanes, and ~64 cycles of
+// latency per dependent operation (a reciprocal ~430).  The two FP64 kernels
+// of the panel are laid out for that: every FP64 instruction they issue has
+// (nearly) all its lanes busy, and the chain from one column to the next is
+// a handful of dependent operations.
+
 // 1 / d of a pivot d, or -1 when d is not positive and finite or its
 // reciprocal overflows.
 __device__ __forceinline__ double inv_pivot(double d) {
-  const double r = 1.0 / d;
+  const double r = __drcp_rn(d);
   return (d > 0.0 && isfinite(d) && isfinite(r)) ? r : -1.0;
 }
 
 // The FP64 factor of the kb x kb diagonal block of panel k0 (kb <= 64) by one
-// CTA, right-looking in the LDL' form: the update for column c subtracts
-// (M_ic / d_c) M_jc from the trailing entries, so the chain from one column
-// to the next is one reciprocal 1 / d_c (formed by thread 0 right after its
-// update of d_c) and one barrier; the square roots and the scaling
-// L_ic = M_ic / sqrt(d_c) then run for all columns at once.  (On GB300 a
-// dependent FP64 operation takes ~64 cycles, a square root ~675 and a
-// reciprocal ~430: the Cholesky form puts both on the chain.)  Writes L_11
-// (lower triangle and diagonal) to M and 1 / L_cc to dinv[k0 + c]; a pivot
-// that is not positive and finite sets PDAS_ERR_NOT_SPD with its index.
+// CTA, right-looking in the LDL' form.  Per column c, after a barrier:
+//   (a) t_i = M_ic / d_c for the rows i > c (one multiply each);
+//   (b) M_ij -= t_i M_jc over the trailing triangle c < j <= i < kb, its
+//       entries packed over all threads (entry e <-> (i, j) by a table);
+//       entry 0 is (c + 1, c + 1): thread 0 updates it first and forms
+//       1 / d_c+1 for the next column.
+// The square roots and the scaling L_ic = M_ic / sqrt(d_c) then run for all
+// columns at once.  Writes L_11 (lower triangle and diagonal) to M and
+// 1 / L_cc to dinv[k0 + c]; a pivot that is not positive and finite sets
+// PDAS_ERR_NOT_SPD with its index.
 constexpr int DG_THREADS = 256;
+constexpr int DG_TRI = (UK - 1) * UK / 2;  // entries of the largest trailing triangle
 __global__ void __launch_bounds__(DG_THREADS) k_dig_diag(int64_t ldm, double* __restrict__ M,
                                                          double* __restrict__ dinv, int64_t k0, int kb, Scalars* sc) {
   __shared__ double Ld[UK][UK + 1];
-  __shared__ double s_inv[2];  // 1 / d_c of the next column; < 0: not positive definite
+  __shared__ double tcol[UK];             // t_i of the current column
   __shared__ double s_rp[UK];
+  __shared__ unsigned short tri[DG_TRI];  // e -> (r, s), e = r (r + 1) / 2 + s, s <= r: r << 8 | s
+  __shared__ double s_inv;                // 1 / d_c of the next column; < 0: not positive definite
   if (*(volatile const int*)&sc->status != 0) return;
   for (int t = threadIdx.x; t < UK * UK; t += DG_THREADS) {
     const int i = t / UK, j = t % UK;
     if (j <= i && i < kb) Ld[i][j] = M[(k0 + i) * ldm + k0 + j];
   }
+  for (int e = threadIdx.x; e < DG_TRI; e += DG_THREADS) {
+    int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
+    while (r * (r + 1) / 2 > e) --r;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    tri[e] = (unsigned short)((r << 8) | (e - r * (r + 1) / 2));
+  }
   __syncthreads();
-  if (threadIdx.x == 0) s_inv[0] = inv_pivot(Ld[0][0]);
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;  // rows ti + 16 a, columns tj + 16 b
+  if (threadIdx.x == 0) s_inv = inv_pivot(Ld[0][0]);
   int fail = -1;
   for (int c = 0; c < kb; ++c) {
     __syncthreads();  // the update for column c - 1 is complete and 1 / d_c posted
-    const double inv = s_inv[c & 1];
+    const double inv = s_inv;
     if (inv < 0.0) {
       fail = c;
       break;
     }
-    for (int i = c + 1 + ti; i < kb; i += 16) {
-      const double t = Ld[i][c] * inv;
-      for (int j = c + 1 + tj; j <= i; j += 16) {
-        Ld[i][j] = fma(-t, Ld[j][c], Ld[i][j]);
-        if (i == c + 1 && j == c + 1) s_inv[(c + 1) & 1] = inv_pivot(Ld[i][j]);  // thread 0: d_c+1 is final
-      }
+    const int rest = kb - 1 - c;
+    if (threadIdx.x < rest) tcol[c + 1 + threadIdx.x] = Ld[c + 1 + threadIdx.x][c] * inv;
+    __syncthreads();
+    const int ne = rest * (rest + 1) / 2;
+    for (int e = threadIdx.x; e < ne; e += DG_THREADS) {
+      const int rs = tri[e], i = c + 1 + (rs >> 8), j = c + 1 + (rs & 0xff);
+      const double v = fma(-tcol[i], Ld[j][c], Ld[i][j]);
+      Ld[i][j] = v;
+      if (e == 0) s_inv = inv_pivot(v);  // thread 0: d_c+1 is final
     }
   }
   if (fail >= 0) {  // every thread read the same pivot
@@ -192,69 +212,73 @@ __global__ void __launch_bounds__(DG_THREADS) k_dig_diag(int64_t ldm, double* __
   }
 }
 
-// k_dig_panel_rows: one warp per CTA and 8 rows per warp, so that a panel
-// with few trailing rows still spreads over every SM (the solve is bound by
-// the FP64 pipes, ~2 multiply-adds per cycle per SM on GB300).
-constexpr int PR_ROWS = 8;                        // panel rows per CTA
-constexpr int PR_THREADS = 4 * PR_ROWS;           // four threads per row
-
 // The panel rows r = k0 + kb + i (i < rows): X L_11' = B in FP64 (B the kb
 // panel columns of the rows, L_11 and 1 / L_cc from the diagonal factor),
 // X written back to M; then the digits of X into planes (7 planes of mpad
 // rows x 64 columns, BF16) and the row exponents into e[i].
-// Solve: thread (row, part) holds columns part, part + 4, ... of its row in
-// registers and sweeps the columns right-looking, the owner of column c
-// passing x_c to its row's other three threads.  Digits: one warp per row,
-// the lanes holding columns 2 lane and 2 lane + 1 (16-byte-aligned rows of
-// every plane written whole by the warp).
+// Solve: T threads per row; thread `part` of a row holds columns part,
+// part + T, ... in registers.  The sweep over the columns is unrolled at
+// compile time, so at column c a thread issues multiply-adds only for its
+// slots that can still lie past c (at most one of them predicated off):
+// column c's value x_c = b_c / L_cc is formed by its owner and passed to
+// the row's other threads by a shuffle.  Small T gives the fewest FP64
+// instructions per row, large T the shortest sweep per warp; the host picks
+// T per panel from the number of rows.  Digits: one warp per row, the lanes
+// holding columns 2 lane and 2 lane + 1 (whole 128-byte plane rows).
+constexpr int PR_THREADS = 128;
+
+template <int T>
 __global__ void __launch_bounds__(PR_THREADS) k_dig_panel_rows(int64_t ldm, double* __restrict__ M,
                                                              const double* __restrict__ dinv, int64_t k0, int kb,
                                                              int64_t rows, int64_t mpad, int* __restrict__ e,
                                                              __nv_bfloat16* __restrict__ planes, const Scalars* sc) {
+  constexpr int RPB = PR_THREADS / T;  // rows per CTA
+  constexpr int NS = UK / T;           // slots per thread
   __shared__ double Lt[UK][UK + 1];  // L_11 strictly below the diagonal; then the solved rows
   __shared__ double rcp[UK];
   if (*(volatile const int*)&sc->status != 0) return;  // a pivot of the diagonal factor failed
   for (int t = threadIdx.x; t < UK * UK; t += PR_THREADS) {  // the solve reads only Lt[i][j], j < i < kb
     const int i = t / UK, j = t % UK;
-    if (j < i && i < kb) Lt[i][j] = M[(k0 + i) * ldm + k0 + j];
+    Lt[i][j] = (j < i && i < kb) ? M[(k0 + i) * ldm + k0 + j] : 0.0;
   }
   for (int t = threadIdx.x; t < UK; t += PR_THREADS) rcp[t] = t < kb ? dinv[k0 + t] : 0.0;
   __syncthreads();
-  const int row = threadIdx.x >> 2, part = threadIdx.x & 3;
-  const int64_t r0 = (int64_t)blockIdx.x * PR_ROWS;
+  const int row = threadIdx.x / T, part = threadIdx.x % T;
+  const int64_t r0 = (int64_t)blockIdx.x * RPB;
   const bool live = r0 + row < rows;
   double* mrow = M + (live ? (k0 + kb + r0 + row) * ldm + k0 : 0);
-  double x[UK / 4];
+  double x[NS];
 #pragma unroll
-  for (int k = 0; k < UK / 4; ++k) {
-    const int c = part + 4 * k;
+  for (int k = 0; k < NS; ++k) {
+    const int c = part + T * k;
     x[k] = (live && c < kb) ? mrow[c] : 0.0;
   }
+  // columns past kb hold zeros in B, L_11 and rcp: their slots stay zero
+  const int src = (threadIdx.x & 31) - part;  // lane of this row's thread 0
 #pragma unroll
   for (int c = 0; c < UK; ++c) {
-    if (c < kb) {
-      const int owner = c & 3;
-      double xc = (part == owner) ? x[c >> 2] * rcp[c] : 0.0;
-      xc = __shfl_sync(0xffffffffu, xc, (threadIdx.x & 31 & ~3) | owner);
-      if (part == owner) x[c >> 2] = xc;
+    const int kc = c / T;
+    const double own = x[kc];  // meaningful in the owner, part == c % T
+    const double xc = __shfl_sync(0xffffffffu, own, src + c % T) * rcp[c];
+    if (part == c % T) x[kc] = xc;
 #pragma unroll
-      for (int k = 0; k < UK / 4; ++k) {
-        const int cp = part + 4 * k;
-        if (cp > c && cp < kb) x[k] -= xc * Lt[cp][c];
-      }
+    for (int k = (c + 1) / T; k < NS; ++k) {
+      if (T * k + T - 1 <= c) continue;  // no thread's slot k lies past c (compile-time)
+      const int q = part + T * k;
+      if (T * k > c || q > c) x[k] = fma(-xc, Lt[q][c], x[k]);
     }
   }
   __syncthreads();  // every thread is done with L_11
   double (*X)[UK + 1] = Lt;
 #pragma unroll
-  for (int k = 0; k < UK / 4; ++k) {
-    const int c = part + 4 * k;
+  for (int k = 0; k < NS; ++k) {
+    const int c = part + T * k;
     X[row][c] = c < kb ? x[k] : 0.0;
     if (live && c < kb) mrow[c] = x[k];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int rr = warp; rr < PR_ROWS; rr += PR_THREADS / 32) {
+  for (int rr = warp; rr < RPB; rr += PR_THREADS / 32) {
     const int64_t i = r0 + rr;
     if (i >= rows) break;
     const double v0 = X[rr][2 * lane], v1 = X[rr][2 * lane + 1];
@@ -275,6 +299,33 @@ __global__ void __launch_bounds__(PR_THREADS) k_dig_panel_rows(int64_t ldm, doub
       reinterpret_cast<uint32_t*>(planes + ((int64_t)s * mpad + i) * UK)[lane] = pair;
     }
   }
+}
+
+// FP64 warp instructions of one row-solve warp with T threads per row, and
+// the warps of a panel of `rows` rows; the host takes the T with the
+// smallest (warps per SM sub-partition, rounded up) x (instructions per warp).
+constexpr int row_solve_instr(int T) {
+  int n = UK;  // the x_c multiplies
+  for (int c = 0; c < UK; ++c)
+    for (int k = (c + 1) / T; k < UK / T; ++k)
+      if (T * k + T - 1 > c) ++n;
+  return n;
+}
+
+int pick_row_threads(int64_t rows, int sub_partitions) {
+  const int Ts[4] = {4, 8, 16, 32};
+  int best = 4;
+  double best_cost = 1e300;
+  for (int T : Ts) {
+    const int64_t warps = (rows * T + 31) / 32;
+    const int64_t per = (warps + sub_partitions - 1) / sub_partitions;
+    const double cost = (double)per * row_solve_instr(T);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = T;
+    }
+  }
+  return best;
 }
 
 // C_pq -= (P P')_pq for the lower tiles of the trailing matrix (rows and
@@ -477,6 +528,11 @@ cudaError_t encode_planes(CholDigHost* hs, CUtensorMap* map, const void* base, i
 cudaError_t chol_dig_create(CholDigWorkspace* w, int64_t m) {
   w->m = m;
   w->mpad = (m + UBM - 1) / UBM * UBM;
+  int dev = 0, sms = 0;
+  cudaError_t ea = cudaGetDevice(&dev);
+  if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ea != cudaSuccess) return ea;
+  w->sub_partitions = 4 * sms;
   CholDigHost* hs = new (std::nothrow) CholDigHost();
   if (!hs) return cudaErrorMemoryAllocation;
   w->host = hs;
@@ -513,8 +569,24 @@ cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, doub
     ++*launches;
     e = cudaGetLastError();
     if (e != cudaSuccess || rows == 0) continue;
-    k_dig_panel_rows<<<(unsigned)((rows + PR_ROWS - 1) / PR_ROWS), PR_THREADS, 0, st>>>(
-        ldm, M, dinv, k0, kb, rows, w->mpad, w->e, static_cast<__nv_bfloat16*>(w->planes), sc);
+    __nv_bfloat16* planes = static_cast<__nv_bfloat16*>(w->planes);
+    switch (pick_row_threads(rows, w->sub_partitions)) {
+      case 4:
+        k_dig_panel_rows<4><<<(unsigned)((rows + 31) / 32), PR_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, rows, w->mpad,
+                                                                                 w->e, planes, sc);
+        break;
+      case 8:
+        k_dig_panel_rows<8><<<(unsigned)((rows + 15) / 16), PR_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, rows, w->mpad,
+                                                                                 w->e, planes, sc);
+        break;
+      case 16:
+        k_dig_panel_rows<16><<<(unsigned)((rows + 7) / 8), PR_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, rows, w->mpad,
+                                                                                w->e, planes, sc);
+        break;
+      default:
+        k_dig_panel_rows<32><<<(unsigned)((rows + 3) / 4), PR_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, rows, w->mpad,
+                                                                                w->e, planes, sc);
+    }
     const int64_t nI = (rows + UBM - 1) / UBM;
     k_dig_update<<<(unsigned)(nI * (nI + 1)), NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb,
                                                                              rows, w->e, sc);

@@ -14,6 +14,7 @@ constexpr int64_t kCholDigMinM = 256;
 struct CholDigWorkspace {
   int64_t m = 0;
   int64_t mpad = 0;        // m rounded up to 128
+  int sub_partitions = 0;  // SM sub-partitions of the device (4 per SM): the row solve's launch shape
   void* planes = nullptr;  // 7 BF16 digit planes of mpad rows x 64 columns (the current panel)
   int* e = nullptr;        // row exponents of the current panel (mpad)
   void* host = nullptr;    // tensor maps
