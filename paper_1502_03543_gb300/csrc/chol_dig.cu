@@ -31,17 +31,20 @@
 // the subtraction: FP64-grade, where the FP64 pipes would take 1/64 of the
 // FP32 rate.
 //
-// k_dig_update: one CTA per 128 x 64 tile, 10 warps:
-//   warp 0      one TMA load of the 7 planes for rows p (128 x 64 columns)
-//               and the 7 planes for rows q (64 x 64 columns), 168 KB;
+// k_dig_update: persistent, one CTA per SM over the 128 x 64 tiles, 10 warps:
+//   warp 0      per tile one TMA load of the 7 planes for rows p (128 x 64
+//               columns) and the 7 planes for rows q (64 x 64 columns),
+//               168 KB, as soon as the previous tile's MMAs are done;
 //   warp 1      allocates 512 TMEM columns (8 weights x 64); one lane issues
 //               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=64, K=16), 34
-//               pairs x 4 K steps, pair (s, t) into weight s + t;
-//   warps 2..9  load their rows of C while the copies and the MMAs run;
-//               then warp w reads TMEM lanes 32 (w % 4).. and columns
-//               32 ((w - 2) / 4).. of every weight, combines the weights and
-//               stages the scaled update in shared memory, and each warp
-//               subtracts whole rows of it from its part of C.
+//               pairs x 4 K steps, pair (s, t) into weight s + t, as soon as
+//               the planes have landed and the previous tile's accumulators
+//               have been read;
+//   warps 2..9  thread (warp w, lane) owns row 32 (w % 4) + lane of the tile
+//               and columns 32 ((w - 2) / 4).. of it: it loads that part of C
+//               while the copy and the MMAs run, reads its TMEM lane of every
+//               weight, combines the weights and subtracts the scaled update
+//               from C in place (16-byte accesses).
 // Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
 // PDAS_ERR_TIMEOUT, lets its copy land and its MMAs finish, frees TMEM, exits.
 #include <cuda.h>
@@ -71,7 +74,6 @@ static_assert(NPAIR == 7 + 7 + 6 + 5 + 4 + 3 + 2, "pair count");
 constexpr uint32_t P_PLANE = UBM * 128;           // 16 KB: 128 rows of one digit
 constexpr uint32_t Q_PLANE = UBN * 128;           // 8 KB: 64 rows of one digit
 constexpr uint32_t LOAD_BYTES = ND * (P_PLANE + Q_PLANE);  // 168 KB
-static_assert(UBM * (UBN + 1) * sizeof(double) <= LOAD_BYTES, "the update's staging area");
 constexpr uint32_t TMEM_COLS = NW * UBN;          // 512
 constexpr int NUM_THREADS = 320;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)LOAD_BYTES + 256;
@@ -85,14 +87,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c
           "r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
-}
-
-// Whole warp: 8 consecutive columns of this warp's 32 TMEM lanes (lane = row).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // z 2^k as a double, rounded to nearest (ties to even), built on the
@@ -328,34 +322,55 @@ int pick_row_threads(int64_t rows, int sub_partitions) {
   return best;
 }
 
+// Eight tensor-memory loads of 8 columns each (one per weight, w_stride
+// columns apart) for this warp's 32 lanes, then one wait.
+__device__ __forceinline__ void tmem_ld8x8(uint32_t taddr, uint32_t w_stride, uint32_t (&r)[NW][8]) {
+#pragma unroll
+  for (int w = 0; w < NW; ++w)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[w][0]), "=r"(r[w][1]), "=r"(r[w][2]), "=r"(r[w][3]), "=r"(r[w][4]), "=r"(r[w][5]),
+                   "=r"(r[w][6]), "=r"(r[w][7])
+                 : "r"(taddr + (uint32_t)w * w_stride));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Tile b of the update: (I, J) with J <= 2 I + 1 (row block I has 2 I + 2
+// tiles, the first I (I + 1) tiles precede it); false when the tile lies
+// outside the trailing matrix.
+__device__ __forceinline__ bool update_tile(int64_t b, int64_t rows, int64_t& p0, int64_t& q0) {
+  int64_t I = (int64_t)((sqrtf(4.0f * (float)b + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
+  while (I * (I + 1) > b) --I;
+  while ((I + 1) * (I + 2) <= b) ++I;
+  p0 = I * UBM;
+  q0 = (b - I * (I + 1)) * UBN;
+  return q0 < rows && q0 <= p0 + UBM - 1;
+}
+
 // C_pq -= (P P')_pq for the lower tiles of the trailing matrix (rows and
-// columns k0 + kb + [0, rows)); tile b is (I, J) with J <= 2 I + 1 (row
-// block I has 2 I + 2 tiles, the first I (I + 1) tiles precede it).
+// columns base + [0, rows)).  Persistent: CTA x takes tiles x, x + grid, ...
+// in order, and the stages of consecutive tiles overlap -- the copy of the
+// next tile's planes lands while this tile's epilogue runs, and the next
+// tile's MMAs start as soon as the epilogue has read the accumulators.
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_dig_update(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int64_t ldm,
-                 double* __restrict__ M, int64_t base, int64_t rows, const int* __restrict__ e, Scalars* sc) {
+                 double* __restrict__ M, int64_t base, int64_t rows, int64_t ntiles, const int* __restrict__ e,
+                 Scalars* sc) {
   extern __shared__ uint8_t smem_raw[];
   if (*(volatile const int*)&sc->status != 0) return;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LOAD_BYTES);  // full | mma done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LOAD_BYTES);  // full | free | mma done | tmem free | drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const uint32_t full = smem_u32(bars), mma_done = smem_u32(bars + 1);
-
-  // tile (I, J) of block b: I = the largest with I (I + 1) <= b
-  const int64_t b = blockIdx.x;
-  int64_t I = (int64_t)((sqrtf(4.0f * (float)b + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
-  while (I * (I + 1) > b) --I;
-  while ((I + 1) * (I + 2) <= b) ++I;
-  const int64_t J = b - I * (I + 1);
-  const int64_t p0 = I * UBM, q0 = J * UBN;
-  if (q0 >= rows || q0 > p0 + UBM - 1) return;  // beyond the trailing matrix
-
+  const uint32_t full = smem_u32(bars), pfree = smem_u32(bars + 1), mma_done = smem_u32(bars + 2),
+                 tfree = smem_u32(bars + 3), drain = smem_u32(bars + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(full, 1);
+    mbar_init(pfree, 1);
     mbar_init(mma_done, 1);
+    mbar_init(tfree, 8);  // one arrival per epilogue warp
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -365,18 +380,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
+  int64_t p0, q0;
 
   if (warp == 0) {
     if (lane == 0) {
-      mbar_expect_tx(full, LOAD_BYTES);
-      tma_load_3d(sbase, &tmP, 0, (int)p0, 0, full);
-      tma_load_3d(sbase + ND * P_PLANE, &tmQ, 0, (int)q0, 0, full);
-      mbar_wait(full, 0, nullptr);  // the copy has landed before this warp can leave
+      int it = 0;
+      for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        if (!update_tile(b, rows, p0, q0)) continue;
+        if (it > 0 && !mbar_wait(pfree, (uint32_t)(it - 1) & 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(full, LOAD_BYTES);
+        tma_load_3d(sbase, &tmP, 0, (int)p0, 0, full);
+        tma_load_3d(sbase + ND * P_PLANE, &tmQ, 0, (int)q0, 0, full);
+        ++it;
+      }
+      if (it > 0) mbar_wait(full, (uint32_t)(it - 1) & 1u, nullptr);  // the last copy has landed
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      if (mbar_wait(full, 0, abort_flag)) {
+      int it = 0;
+      for (int64_t b = blockIdx.x; b < ntiles && !*abort_flag; b += gridDim.x) {
+        if (!update_tile(b, rows, p0, q0)) continue;
+        if (!mbar_wait(full, (uint32_t)it & 1u, abort_flag) ||
+            (it > 0 && !mbar_wait(tfree, (uint32_t)(it - 1) & 1u, abort_flag))) {
+          *abort_flag = 1;
+          break;
+        }
         fence_after();
 #pragma unroll
         for (int s = 0; s < ND; ++s) {
@@ -394,38 +426,42 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
           }
         }
-      } else {
-        *abort_flag = 1;
+        umma_commit(pfree);     // the planes may be overwritten once these MMAs are done
+        umma_commit(mma_done);  // and the accumulators read
+        ++it;
       }
-      umma_commit(mma_done);  // fires once every MMA issued above has completed
+      umma_commit(drain);  // every MMA issued above has completed before the CTA leaves
+      mbar_wait(drain, 0, nullptr);
     }
     __syncwarp();
   } else {
-    const int quarter = warp & 3, half = (warp - 2) >> 2, ew = warp - 2;
-    // this warp's share of C (rows ew + 8 i, columns q0 + lane and
-    // q0 + 32 + lane), loaded while the copies and the MMAs run
-    double cpre[UBM / 8][2];
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    int it = 0;
+    for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+      if (!update_tile(b, rows, p0, q0)) continue;
+      // this thread's entries: row p (its tensor-memory lane), columns q0 + 32 half + [0, 32),
+      // those with q <= p inside the trailing matrix; C is loaded while the copy and the MMAs run
+      const int64_t p = p0 + quarter * 32 + lane;
+      const int64_t qb = q0 + half * 32;
+      const bool prow = p < rows;
+      double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
+      double2 cv[16];
 #pragma unroll
-    for (int i = 0; i < UBM / 8; ++i) {
-      const int64_t p = p0 + ew + 8 * i;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t q = q0 + lane + 32 * h;
-        cpre[i][h] = (p < rows && q <= p) ? M[(base + p) * ldm + base + q] : 0.0;
+      for (int v = 0; v < 16; ++v) {
+        const int64_t q = qb + 2 * v;
+        if (prow && q + 1 <= p) cv[v] = *reinterpret_cast<const double2*>(crow + 2 * v);
+        else cv[v] = make_double2(prow && q <= p ? crow[2 * v] : 0.0, 0.0);
       }
-    }
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait(mma_done, 0, abort_flag) && !*abort_flag;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    // the update, scaled, staged in shared memory (the operands are consumed
-    // once the MMAs are done), then subtracted from the prefetched C by whole rows
-    double* stg = reinterpret_cast<double*>(smem);  // [128][65]
-    if (ok) {
+      const int ep = prow ? e[p] : 0;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(mma_done, (uint32_t)it & 1u, abort_flag) && !*abort_flag;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *abort_flag = 1;
+        break;
+      }
       fence_after();
-      const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
-      const int rl = quarter * 32 + lane;
-      const int64_t p = p0 + rl;
-      const int ep = p < rows ? e[p] : 0;
       // GB300 runs FP64 at 1/64 of the FP32 rate, so the weights are
       // combined on the integer pipes into one integer,
       //   Z = sum_{w<=5} I_w 2^(42-8w) + round((I_6 2^8 + I_7) 2^-14)
@@ -435,49 +471,38 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // the subtraction from C is the one FP64 operation of an entry
 #pragma unroll
       for (int g = 0; g < 4; ++g) {  // 8 columns at a time
-        long long z[8];
-        int t[8];
+        uint32_t r[NW][8];
+        tmem_ld8x8(lane_addr + (uint32_t)(g * 8), UBN, r);
+        if (g == 3) {  // every accumulator of this warp is read: the next tile's MMAs may start
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tfree);
+        }
+        double u[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          z[j] = 0;
-          t[j] = 0;
-        }
+          long long z = 0;
+          int t = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          uint32_t r[8];
-          tmem_ld8(lane_addr + (uint32_t)(w * UBN + g * 8), r);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int v = __float2int_rn(__uint_as_float(r[j]));
-            if (w <= 5) z[j] += (long long)v * (1ll << (42 - 8 * w));
-            else if (w == 6) t[j] = v * 256;
-            else t[j] += v;
+          for (int w = 0; w < NW; ++w) {
+            const int v = __float2int_rn(__uint_as_float(r[w][j]));
+            if (w <= 5) z += (long long)v * (1ll << (42 - 8 * w));
+            else if (w == 6) t = v * 256;
+            else t += v;
           }
+          const int64_t q = qb + g * 8 + j;
+          u[j] = (prow && q <= p) ? scaled_int_to_double(z + ((t + 8192) >> 14), ep + e[q] - 56) : 0.0;
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = half * 32 + g * 8 + j;
-          const int64_t q = q0 + c;
-          double u = 0.0;
-          if (q < rows) u = scaled_int_to_double(z[j] + ((t[j] + 8192) >> 14), ep + e[q] - 56);
-          stg[rl * (UBN + 1) + c] = u;
-        }
-      }
-    } else if (lane == 0) {
-      *abort_flag = 1;
-    }
-    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
-    if (!*abort_flag) {
-#pragma unroll
-      for (int i = 0; i < UBM / 8; ++i) {
-        const int rl = ew + 8 * i;
-        const int64_t p = p0 + rl;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int64_t q = q0 + lane + 32 * h;
-          if (p < rows && q <= p) M[(base + p) * ldm + base + q] = cpre[i][h] - stg[rl * (UBN + 1) + lane + 32 * h];
+        for (int v = 0; v < 4; ++v) {
+          const int vi = g * 4 + v;
+          const int64_t q = qb + 2 * vi;
+          const double c0 = cv[vi].x - u[2 * v], c1 = cv[vi].y - u[2 * v + 1];
+          if (prow && q + 1 <= p) *reinterpret_cast<double2*>(crow + 2 * vi) = make_double2(c0, c1);
+          else if (prow && q <= p) crow[2 * vi] = c0;
         }
       }
+      ++it;
     }
   }
   if (threadIdx.x == 0 && *abort_flag) atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
@@ -587,9 +612,9 @@ cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, doub
         k_dig_panel_rows<32><<<(unsigned)((rows + 3) / 4), PR_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, rows, w->mpad,
                                                                                 w->e, planes, sc);
     }
-    const int64_t nI = (rows + UBM - 1) / UBM;
-    k_dig_update<<<(unsigned)(nI * (nI + 1)), NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb,
-                                                                             rows, w->e, sc);
+    const int64_t nI = (rows + UBM - 1) / UBM, ntiles = nI * (nI + 1);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, w->sub_partitions / 4);
+    k_dig_update<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb, rows, ntiles, w->e, sc);
     *launches += 2;
     e = cudaGetLastError();
   }
