@@ -413,8 +413,25 @@ def run_normal_only(args):
     out = dict(kernel="normal-matrix", workload=args.workload, form=args.form, splits=splits, ms_per_launch=ms,
                launches=prof["launches"], wall_s=wall, roofline=roof)
     if factor:
-        out["factor_ms"] = fms / args.steps
-        out["factor_roofline"] = chol_roofline(args.form, lp.m, fms / args.steps, peaks)
+        fac_ms = fms / args.steps
+        out["factor_ms"] = fac_ms
+        if args.tier2:
+            # the FP64 tier's factor: FP64 panels, trailing updates from 34 digit-pair
+            # products on the tensor cores; algorithmic m^3/3 flops, also against the FP64 peak
+            peaks["fp64"] = probe_peaks(n=4096)["fp64"]
+            alg = float(lp.m) ** 3 / 3.0
+            ach = alg / (fac_ms * 1e-3) / 1e12
+            out["factor_roofline"] = dict(
+                bound="tensor", achieved=round(ach, 3), peak=peaks["bf16_sus"], unit="TFLOP/s",
+                frac=round(ach / peaks["bf16_sus"], 4), traffic=None,
+                kernel="FP64-tier factor (k_dig_diag, k_dig_panel_rows, k_dig_update)",
+                executed_frac=round(34 * ach / peaks["bf16_sus"], 4), pair_products=34,
+                fp64_peak=peaks["fp64"], fp64_multiple=round(ach / peaks["fp64"], 3),
+                algorithmic_flops_per_launch=alg, ms_per_launch=round(fac_ms, 4),
+                peak_note="bf16 dense, sustained, of %s; fp64_peak: torch.matmul FP64 4096^3 in this run; "
+                          "fp64_multiple = achieved / fp64_peak" % peaks["source"])
+        else:
+            out["factor_roofline"] = chol_roofline(args.form, lp.m, fac_ms, peaks)
     print(json.dumps(out))
 
 

@@ -10,38 +10,46 @@
 //
 // Fixed-point digits.  Row p of A (kept columns j < k) is scaled by 2^-ea_p,
 // ea_p the exponent of max_j |A_pj|, so a'_pj = A_pj 2^-ea_p lies in (-1, 1);
-// row q of B = D.*A (B_qj = D_j A_qj, formed in FP64) by 2^-eb_q.  Each is
-// written in balanced base-256 digits:
+// row q of B = D.*A (B_qj = D_j A_qj, the exact integer product of the two
+// significands) by 2^-eb_q.  Each is written in balanced base-256 digits:
 //     a' = sum_{s<5} d_s 2^(-7-8s),    b' = sum_{t<8} g_t 2^(-7-8t),
 // every digit an integer in [-128, 128] (exact in BF16).  Five digits hold a
-// BF16 entry exactly down to 2^-32 of its row's largest; eight hold the FP64
-// B to 2^-63.  Then
+// BF16 entry exactly down to 2^-32 of its row's largest; eight hold B to
+// 2^-63.  Then
 //     M_pq = 2^(ea_p + eb_q - 14) sum_w 2^(-8w) I_w,
 //     I_w  = sum_j sum_{s+t=w} d_s,pj g_t,qj          (integers),
 // for the 30 digit pairs with s + t <= 7 (the pairs dropped contribute at
 // most 2^-62 of 2^(ea_p + eb_q) per column).  Every product d g has
 // magnitude <= 2^14; a weight collects at most 5 pairs, so over a chunk of
-// 128 columns |I_w| <= 5 * 128 * 2^14 < 2^24: the FP32 accumulator holds
+// 192 columns |I_w| <= 5 * 192 * 2^14 < 2^24: the FP32 accumulator holds
 // the chunk sum exactly, whatever its rounding.  The epilogue converts each
-// chunk's eight weight sums to integers and adds them, weighted by powers of
-// 2^8, exactly into two int64 sums per entry (weights 0-3 and 4-7); at the
-// end it combines the two in FP64 and applies the power-of-two scale.  The
-// only roundings left are the FP64 product D_j A_qj and the final FP64
-// combination.
+// chunk's weight sums to integers and adds them, weighted by powers of 2^8,
+// exactly into int64 sums: hi (weights 0-3) and lo (weights 4-7).  At the
+// end hi + 2^-32 lo is formed in FP64 and scaled by a power of two: the one
+// rounding of an entry besides the digits' own truncation.
 //
-// Kernel k_syrk_dig: one CTA per 128 x 32 lower-triangle tile (rows p of A,
-// rows q of B), 10 warps:
-//   warp 0      TMA producer: per stage of 64 columns one 3-D copy of the 5
-//               A digit planes (128 rows) and one of the 8 B digit planes
-//               (32 rows), 112 KB, into a ring of 2 stages;
-//   warp 1      allocates 512 TMEM columns (2 chunk buffers x 8 weights x 32
-//               columns); one lane issues tcgen05.mma.cta_group::1.kind::f16
-//               (M=128, N=32, K=16), 30 pairs x 4 per stage, pair (s, t)
-//               into the weight s + t accumulator of the current buffer;
+// The tensor cores read both operands of every MMA from shared memory, and
+// that operand traffic bounds the kernel (the tc pipe, not the math, was
+// 89 % busy at N = 32).  The tiles are therefore 128 rows p x 64 rows q, and
+// the product runs in two passes so that one pass's weights fit tensor
+// memory twice (2 chunk buffers x 4 weights x 64 columns = 512 columns) and
+// its int64 sums fit the epilogue's registers: pass 0 forms the 10 pairs of
+// weights 0-3 and leaves hi in M (int64 bits), pass 1 the 20 pairs of
+// weights 4-7, reads hi back and writes M_pq.
+//
+// Kernel k_syrk_dig<pass>: one CTA per 128 x 64 lower-triangle tile, 10 warps:
+//   warp 0      TMA producer: per stage of 32 columns one 3-D copy of the A
+//               digit planes the pass needs (128 rows) and one of its B
+//               planes (64 rows), 64-byte swizzle, 48 KB or 72 KB, into a
+//               ring of 3 stages;
+//   warp 1      allocates 512 TMEM columns; one lane issues
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=64, K=16), 2 per
+//               pair per stage, pair (s, t) into the accumulator of weight
+//               s + t of the current chunk buffer;
 //   warps 2..9  warp w reads TMEM lanes 32 (w % 4).. and columns
-//               16 ((w - 2) / 4).. of every weight: per chunk 8 x 16 values,
-//               converted and added into int64 accumulators; then the
-//               buffer is handed back and, at the end, M_pq written in FP64.
+//               32 ((w - 2) / 4).. of every weight: per chunk 4 x 32 values,
+//               converted and added into int64 sums; then the buffer is
+//               handed back.
 // Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
 // PDAS_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM, exits.
 #include <cuda.h>
@@ -72,33 +80,65 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int c
 }
 
 constexpr int DBM = 128;                               // rows p of a tile (A digits)
-constexpr int DBN = 32;                                // rows q of a tile (B digits)
-constexpr int DBK = 64;                                // columns per stage (one 128-byte row)
+constexpr int DBN = 64;                                // rows q of a tile (B digits)
+constexpr int DBK = 64;                                // column granule of the planes (kfill, kstride)
+constexpr int DSK = 32;                                // columns per stage (one 64-byte row)
 constexpr int SA = 5, SB = 8, WMAX = 7;                // digits of A and B, largest pair weight kept
-constexpr int NW = WMAX + 1;                           // weight accumulators
-constexpr int NPAIR = 30;                              // pairs (s, t), s < SA, t < SB, s + t <= WMAX
-constexpr int CHUNK_STAGES = 2;                        // 128 columns per exact chunk
-constexpr uint32_t A_PLANE = DBM * 128;                // 16 KB
-constexpr uint32_t B_PLANE = DBN * 128;                // 4 KB
-constexpr uint32_t STAGE_BYTES = SA * A_PLANE + SB * B_PLANE;  // 112 KB
-constexpr int STAGES = 2;
-constexpr uint32_t BUF_COLS = NW * DBN;                // 256 TMEM columns per chunk buffer
+constexpr int NWP = 4;                                 // weights per pass: 0-3, then 4-7
+constexpr int CHUNK_STAGES = 6;                        // 192 columns per exact chunk
+constexpr uint32_t A_PLANE = DBM * DSK * 2;            // 8 KB: 128 rows of one digit, one stage
+constexpr uint32_t B_PLANE = DBN * DSK * 2;            // 4 KB
+constexpr int STAGES = 3;
+constexpr uint32_t BUF_COLS = NWP * DBN;               // 256 TMEM columns per chunk buffer
 constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;           // 512
 constexpr int NUM_THREADS = 320;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
 constexpr uint32_t kIdesc = idesc_bf16(DBM, DBN);
 
-static_assert(NPAIR == SB + (SB - 1) + (SB - 2) + (SB - 3) + (SB - 4), "pair count");
-static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
+// The digit pairs (s, t) of a pass: weights W0 .. W0 + 3, s < SA, t < SB.
+// Pass 0 (weights 0-3) has 10 pairs and reads A digits 0-3 and B digits 0-3;
+// pass 1 (weights 4-7) has 20 pairs and reads all 13 planes.  A weight
+// collects at most 5 pairs, so over a chunk of 192 columns
+// |I_w| <= 5 * 192 * 2^14 < 2^24: exact in the FP32 accumulator.
+template <int PASS>
+struct DigPass {
+  static constexpr int W0 = PASS * NWP;
+  static constexpr int NA = PASS == 0 ? 4 : SA;  // A planes loaded
+  static constexpr int NB = PASS == 0 ? 4 : SB;  // B planes loaded
+  static constexpr uint32_t STAGE_BYTES = NA * A_PLANE + NB * B_PLANE;  // 48 KB or 72 KB
+  static constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  __host__ __device__ static constexpr bool kept(int s, int t) { return s + t >= W0 && s + t < W0 + NWP && s < NA && t < NB; }
+};
+static_assert(5 * DSK * CHUNK_STAGES * 16384 < (1 << 24), "exact chunk");
+static_assert(DigPass<0>::W0 + 2 * NWP - 1 == WMAX, "the two passes cover the weights 0..WMAX");
+static_assert(DigPass<1>::SMEM_BYTES <= 232448, "shared memory of one CTA");
 
+// Shared-memory matrix descriptor: K-major operand, rows of 64 bytes (32 BF16)
+// with the 64-byte swizzle; 8-row groups 512 bytes apart (version 1 at bit
+// 46, layout type 4 = 64-byte swizzle at bits 61-63).  Advancing the start
+// address by 32 bytes moves one MMA step (16 BF16) along K.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                             // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(512 >> 4) << 32;                    // stride byte offset: one 8-row group
+  d |= (uint64_t)1 << 46;                             // descriptor version
+  d |= (uint64_t)4 << 61;                             // 64-byte swizzle
+  return d;
+}
+
+// One pass of the digit product over the lower-triangle tiles (128 rows p x
+// 64 rows q): pass 0 leaves hi = sum_{w<4} I_w 2^(8(3-w)) of every entry in
+// M (its int64 bits), pass 1 forms lo = sum_{w>=4} I_w 2^(8(7-w)), reads hi
+// back and writes M_pq = 2^(ea_p + eb_q - 38) (hi + 2^-32 lo) in FP64.
+template <int PASS>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_syrk_dig(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const int2* __restrict__ tiles, int nk, int64_t m, const int* __restrict__ ea,
                const int* __restrict__ eb, int64_t ldm, double* __restrict__ M, Scalars* sc) {
+  using P = DigPass<PASS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * P::STAGE_BYTES);
   // bars: full[STAGES] | empty[STAGES] | chunk_full[2] | chunk_free[2] | done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -143,10 +183,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           *abort_flag = 1;
           break;
         }
-        const uint32_t dst = sbase + s * STAGE_BYTES;
-        mbar_expect_tx(full(s), STAGE_BYTES);
-        tma_load_3d(dst, &tmA, kb * DBK, p0, 0, full(s));
-        tma_load_3d(dst + SA * A_PLANE, &tmB, kb * DBK, q0, 0, full(s));
+        const uint32_t dst = sbase + s * P::STAGE_BYTES;
+        mbar_expect_tx(full(s), P::STAGE_BYTES);
+        tma_load_3d(dst, &tmA, kb * DSK, p0, 0, full(s));
+        tma_load_3d(dst + P::NA * A_PLANE, &tmB, kb * DSK, q0, 0, full(s));
         issued = kb + 1;
       }
       if (*abort_flag) {  // let every issued copy land before the CTA can exit
@@ -171,19 +211,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           break;
         }
         fence_after();
-        const uint32_t stage = sbase + s * STAGE_BYTES;
+        const uint32_t stage = sbase + s * P::STAGE_BYTES;
         const uint32_t dbuf = tmem + (uint32_t)buf * BUF_COLS;
 #pragma unroll
-        for (int da = 0; da < SA; ++da) {
-          const uint64_t ad = sdesc_sw128(stage + da * A_PLANE);
+        for (int da = 0; da < P::NA; ++da) {
+          const uint64_t ad = sdesc_sw64(stage + da * A_PLANE);
 #pragma unroll
-          for (int dbg = 0; dbg < SB; ++dbg) {
-            if (da + dbg > WMAX) continue;
-            const uint64_t bd = sdesc_sw128(stage + SA * A_PLANE + dbg * B_PLANE);
-            const uint32_t d = dbuf + (uint32_t)((da + dbg) * DBN);
+          for (int dbg = 0; dbg < P::NB; ++dbg) {
+            if (!P::kept(da, dbg)) continue;
+            const uint64_t bd = sdesc_sw64(stage + P::NA * A_PLANE + dbg * B_PLANE);
+            const uint32_t d = dbuf + (uint32_t)((da + dbg - P::W0) * DBN);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {  // 32 bytes (16 BF16) along K per MMA
-              // the first product of weight w in a chunk is pair (0, w) at its first K step
+            for (int k = 0; k < DSK / 16; ++k) {  // 32 bytes (16 BF16) along K per MMA
+              // the first product of a weight in a chunk is pair (0, w) at its first K step
               const uint32_t accum = (chunk_start && da == 0 && k == 0) ? 0u : 1u;
               umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, accum);
             }
@@ -198,13 +238,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     __syncwarp();
   } else {
     const int quarter = warp & 3;         // TMEM lanes this warp may read
-    const int half = (warp - 2) >> 2;     // its 16 columns of each weight block
-    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 16);
-    // exact integer sums of this lane's row, 16 columns: hi = sum_{w<4} I_w 2^(8(3-w)),
-    // lo = sum_{w>=4} I_w 2^(8(7-w)) (|I_w| < 2^23.4 per chunk: int64 holds 2^15 chunks)
-    long long hi[16], lo[16];
+    const int half = (warp - 2) >> 2;     // its 32 columns of each weight block
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    // exact integer sums of this lane's row, 32 columns: sum over the pass's
+    // weights of I_w 2^(8(3 - (w - W0))) (|I_w| < 2^24 per chunk and at most
+    // 5 2^14 k <= 5 2^28 over all columns: the int64 sums stay below 2^55)
+    long long acc[32];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+    for (int j = 0; j < 32; ++j) acc[j] = 0;
     int ok = 1;
     for (int c = 0; c < nchunks; ++c) {
       const int buf = c & 1;
@@ -213,15 +254,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (!ok) break;
       fence_after();
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        uint32_t r[16];
-        tmem_ld16(lane_addr + (uint32_t)buf * BUF_COLS + (uint32_t)(w * DBN), r);
+      for (int wl = 0; wl < NWP; ++wl) {
+        uint32_t r[32];
+        tmem_ld32(lane_addr + (uint32_t)buf * BUF_COLS + (uint32_t)(wl * DBN), r);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));  // an exact integer
-          if (w < 4) hi[j] += v * (1ll << (8 * (3 - w)));
-          else lo[j] += v * (1ll << (8 * (7 - w)));
-        }
+        for (int j = 0; j < 32; ++j)
+          acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << (8 * (NWP - 1 - wl)));
       }
       fence_before();
       __syncwarp();
@@ -230,13 +268,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (ok) {
       const int64_t p = p0 + quarter * 32 + lane;
       if (p < m) {
-        const int ep = ea[p];
-        double* dst = M + p * ldm;
+        long long* dst = reinterpret_cast<long long*>(M + p * ldm);
+        const int64_t qb = (int64_t)q0 + half * 32;
+        if (PASS == 0) {  // hi, as int64 bits, until pass 1
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int64_t q = (int64_t)q0 + half * 16 + j;
-          // sum_w 2^(-8w) I_w = 2^-24 (hi + 2^-32 lo), two FP64 roundings
-          if (q <= p) dst[q] = ldexp(fma((double)lo[j], 0x1p-32, (double)hi[j]), ep + eb[q] - 38);
+          for (int j = 0; j < 32; j += 2) {
+            const int64_t q = qb + j;
+            if (q + 1 <= p) *reinterpret_cast<longlong2*>(dst + q) = make_longlong2(acc[j], acc[j + 1]);
+            else if (q <= p) dst[q] = acc[j];
+          }
+        } else {
+          const int ep = ea[p];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t q = qb + j;
+            // sum_w 2^(-8w) I_w = 2^-24 (hi + 2^-32 lo), two FP64 roundings
+            if (q <= p) {
+              const long long hi = dst[q];
+              M[p * ldm + q] = ldexp(fma((double)acc[j], 0x1p-32, (double)hi), ep + eb[q] - 38);
+            }
+          }
         }
       }
     } else if (lane == 0) {
@@ -399,7 +450,7 @@ __global__ void k_dig_planes(int64_t m, int64_t n, const __nv_bfloat16* __restri
 // ---- host side ---------------------------------------------------------------
 struct DigHost {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  CUtensorMap mapA, mapB;
+  CUtensorMap mapA[2], mapB[2];  // per pass: A digits 0-3 / 0-4, B digits 0-3 / 0-7
   int2* tiles = nullptr;
   int ntiles = 0;
 };
@@ -421,16 +472,17 @@ cudaError_t get_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
 }
 
 // 3-D BF16 map over `planes` consecutive digit planes: dims {kstride (K,
-// innermost), mpad, planes}, box {64 (one 128-byte row), rows, planes},
-// 128-byte swizzle.  The box lands in shared memory as planes x rows x 128 B.
+// innermost), mpad, planes}, box {32 (one 64-byte row), rows, box_planes},
+// 64-byte swizzle.  The box lands in shared memory as box_planes x rows x
+// 64 B.
 cudaError_t encode_planes(DigHost* hs, CUtensorMap* map, const void* base, int64_t mpad, int64_t kstride, int planes,
-                          int rows) {
+                          int box_planes, int rows) {
   cuuint64_t dims[3] = {(cuuint64_t)kstride, (cuuint64_t)mpad, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(kstride * 2), (cuuint64_t)(mpad * kstride * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)DBK, (cuuint32_t)rows, (cuuint32_t)planes};
+  cuuint32_t box[3] = {(cuuint32_t)DSK, (cuuint32_t)rows, (cuuint32_t)box_planes};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = hs->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -452,25 +504,29 @@ cudaError_t dig_workspace_create(DigWorkspace* w, int64_t m, int64_t n) {
   if (e == cudaSuccess) e = cudaMalloc(&w->ea, sizeof(int) * (size_t)m);
   if (e == cudaSuccess) e = cudaMalloc(&w->eb, sizeof(int) * (size_t)w->mpad);
   if (e == cudaSuccess) e = cudaMemset(w->eb, 0, sizeof(int) * (size_t)w->mpad);
-  // Lower-triangle tiles (I, J) of 128 x 32 (some row p >= some column q),
-  // in super-tiles of G row blocks x 4G column blocks (about one wave of
-  // 152 CTAs), so the CTAs resident together share their digit planes in L2.
+  // Lower-triangle tiles (I, J) of 128 x 64 (some row p >= some column q),
+  // in super-tiles of G row blocks x 2G column blocks, so the CTAs resident
+  // together share their digit planes in L2.
   std::vector<int2> tl;
   const int64_t nI = w->mpad / DBM, nJ = (m + DBN - 1) / DBN;
   const int64_t G = 6;
   for (int64_t PI = 0; PI < nI; PI += G)
-    for (int64_t PJ = 0; PJ < nJ; PJ += 4 * G)
+    for (int64_t PJ = 0; PJ < nJ; PJ += 2 * G)
       for (int64_t I = PI; I < nI && I < PI + G; ++I)
-        for (int64_t J = PJ; J < nJ && J < PJ + 4 * G && J * DBN <= I * DBM + DBM - 1; ++J)
+        for (int64_t J = PJ; J < nJ && J < PJ + 2 * G && J * DBN <= I * DBM + DBM - 1; ++J)
           tl.push_back(make_int2((int)I, (int)J));
   hs->ntiles = (int)tl.size();
   if (e == cudaSuccess) e = cudaMalloc(&hs->tiles, sizeof(int2) * tl.size());
   if (e == cudaSuccess) e = cudaMemcpy(hs->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapA, w->planes, w->mpad, w->kstride, SA, DBM);
+  const void* bplanes = (const __nv_bfloat16*)w->planes + (size_t)SA * w->mpad * w->kstride;
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapA[0], w->planes, w->mpad, w->kstride, SA, DigPass<0>::NA, DBM);
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapA[1], w->planes, w->mpad, w->kstride, SA, DigPass<1>::NA, DBM);
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapB[0], bplanes, w->mpad, w->kstride, SB, DigPass<0>::NB, DBN);
+  if (e == cudaSuccess) e = encode_planes(hs, &hs->mapB[1], bplanes, w->mpad, w->kstride, SB, DigPass<1>::NB, DBN);
   if (e == cudaSuccess)
-    e = encode_planes(hs, &hs->mapB, (const __nv_bfloat16*)w->planes + (size_t)SA * w->mpad * w->kstride, w->mpad,
-                      w->kstride, SB, DBN);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syrk_dig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    e = cudaFuncSetAttribute(k_syrk_dig<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DigPass<0>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_syrk_dig<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DigPass<1>::SMEM_BYTES);
   return e;
 }
 
@@ -504,10 +560,12 @@ cudaError_t dig_syrk(cudaStream_t st, DigWorkspace* w, const __nv_bfloat16* A, i
     k_dig_planes<<<grid, 256, 0, st>>>(m, n, A, D, k, kfill, idx, w->ea, w->eb, w->mpad, w->kstride,
                                        static_cast<__nv_bfloat16*>(w->planes));
   }
-  const int nk = (int)(kfill / DBK);
-  k_syrk_dig<<<(unsigned)hs->ntiles, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapA, hs->mapB, hs->tiles, nk, m, w->ea,
-                                                                      w->eb, ldm, M64, sc);
-  *launches = 3;
+  const int nk = (int)(kfill / DSK);
+  k_syrk_dig<0><<<(unsigned)hs->ntiles, NUM_THREADS, DigPass<0>::SMEM_BYTES, st>>>(
+      hs->mapA[0], hs->mapB[0], hs->tiles, nk, m, w->ea, w->eb, ldm, M64, sc);
+  k_syrk_dig<1><<<(unsigned)hs->ntiles, NUM_THREADS, DigPass<1>::SMEM_BYTES, st>>>(
+      hs->mapA[1], hs->mapB[1], hs->tiles, nk, m, w->ea, w->eb, ldm, M64, sc);
+  *launches = 4;
   return cudaGetLastError();
 }
 
