@@ -194,12 +194,40 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k_chol_updat
   }
 }
 
+// Reduce-scatter of eight per-lane partial sums v[0..7] over the warp: every
+// lane returns the whole sum of row red_row(lane) = 4 b4 + 2 b3 + b2 (b_k bit
+// k of the lane), with 9 additions (5 levels) where summing the eight rows
+// one by one takes 40: on GPUs whose FP64 pipes are charged per warp
+// instruction the difference is ~2000 cycles per block.
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter8(const T (&v)[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  T a[4], b[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {  // lanes 0-15 keep rows 0-3, lanes 16-31 rows 4-7
+    const T keep = h16 ? v[i + 4] : v[i], give = h16 ? v[i] : v[i + 4];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const T keep = h8 ? a[i + 2] : a[i], give = h8 ? a[i] : a[i + 2];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+  T c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+__device__ __forceinline__ int red_row(int lane) { return 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1); }
+
 // ---------------------------------------------------------------------------
 // L z = v.  Block row b (64 rows): z_b = L_bb^{-1} (v_b - sum_{j<b} L_bj z_j).
 // Arithmetic in T (the factor's precision; the FP32 factor of the mixed forms
 // is a preconditioner, refined in FP64 afterwards); v, z in FP64.  Warp w
 // owns rows 8w..8w+7 of the block, lane l owns columns l, l+32; the diagonal
-// block is solved by warp 0 with the reciprocals of the pivots.
+// block is solved by warp 0 on its rows divided by their pivots,
+// z_r = v_r / L_rr - sum_{c<r} (L_rc / L_rr) z_c, so a step of its chain is
+// one shuffle and one multiply-add (no multiply by 1 / L_cc on the chain).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm, const T* __restrict__ L,
                                                          const T* __restrict__ dinv, const double* __restrict__ v,
@@ -217,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int i = e / kTile, j = e % kTile;
-    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] : T(0);
+    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] * dinv[r0 + i] : T(0);  // row i over L_ii
   }
   if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
   T part[8];
@@ -241,24 +269,25 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
 #pragma unroll
     for (int i = 0; i < 8; ++i) part[i] = fma(l0[i], z0, fma(l1[i], z1, part[i]));
   }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    T t = part[i];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    const int r = 8 * w + i;
-    if (lane == 0) acc[r] = r < rb ? (T)v[r0 + r] - t : T(0);
+  {
+    const T t = warp_reduce_scatter8(part, lane);
+    const int r = 8 * w + red_row(lane);
+    if ((lane & 3) == 0) acc[r] = r < rb ? (T)v[r0 + r] - t : T(0);
   }
   if (__syncthreads_or(!ok)) return;  // a wait gave up: the status says why
   if (w == 0) {
-    T a0 = acc[lane], a1 = acc[lane + 32];
-    for (int c = 0; c < rb; ++c) {
-      const T own = c < 32 ? a0 : a1;
-      const T zc = __shfl_sync(0xffffffffu, own, c & 31) * rcp[c];
-      if (lane == (c & 31)) {
-        if (c < 32) a0 = zc; else a1 = zc;
-      }
-      if (lane > c) a0 -= Ld[lane][c] * zc;
-      if (lane + 32 > c) a1 -= Ld[lane + 32][c] * zc;
+    // the scaled right-hand side; rows 0..31 finish at column 31, so the
+    // second half of the sweep updates a1 only
+    T a0 = acc[lane] * rcp[lane], a1 = acc[lane + 32] * rcp[lane + 32];
+    const int c1 = rb < 32 ? rb : 32;
+    for (int c = 0; c < c1; ++c) {
+      const T zc = __shfl_sync(0xffffffffu, a0, c);
+      if (lane > c) a0 = fma(-Ld[lane][c], zc, a0);
+      a1 = fma(-Ld[lane + 32][c], zc, a1);
+    }
+    for (int c = 32; c < rb; ++c) {
+      const T zc = __shfl_sync(0xffffffffu, a1, c - 32);
+      if (lane + 32 > c) a1 = fma(-Ld[lane + 32][c], zc, a1);
     }
     if (lane < rb) z[r0 + lane] = (double)a0;
     if (lane + 32 < rb) z[r0 + lane + 32] = (double)a1;
@@ -290,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int i = e / kTile, j = e % kTile;
-    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] : T(0);
+    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] * dinv[r0 + j] : T(0);  // column j over L_jj
   }
   if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
   T p0 = T(0), p1 = T(0);
@@ -327,16 +356,18 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
       a0 += red[i][lane];
       a1 += red[i][lane + 32];
     }
-    a0 = lane < rb ? (T)zin[r0 + lane] - a0 : T(0);
-    a1 = lane + 32 < rb ? (T)zin[r0 + lane + 32] - a1 : T(0);
-    for (int c = rb - 1; c >= 0; --c) {
-      const T own = c < 32 ? a0 : a1;
-      const T yc = __shfl_sync(0xffffffffu, own, c & 31) * rcp[c];
-      if (lane == (c & 31)) {
-        if (c < 32) a0 = yc; else a1 = yc;
-      }
-      if (lane < c) a0 -= Ld[c][lane] * yc;
-      if (lane + 32 < c) a1 -= Ld[c][lane + 32] * yc;
+    // rows divided by their pivots (the coefficients were scaled at the
+    // load): a step of the chain is one shuffle and one multiply-add
+    a0 = (lane < rb ? (T)zin[r0 + lane] - a0 : T(0)) * rcp[lane];
+    a1 = (lane + 32 < rb ? (T)zin[r0 + lane + 32] - a1 : T(0)) * rcp[lane + 32];
+    for (int c = rb - 1; c >= 32; --c) {
+      const T yc = __shfl_sync(0xffffffffu, a1, c - 32);
+      if (lane + 32 < c) a1 = fma(-Ld[c][lane + 32], yc, a1);
+      a0 = fma(-Ld[c][lane], yc, a0);
+    }
+    for (int c = (rb < 32 ? rb : 32) - 1; c >= 0; --c) {
+      const T yc = __shfl_sync(0xffffffffu, a0, c);
+      if (lane < c) a0 = fma(-Ld[c][lane], yc, a0);
     }
     if (lane < rb) y[r0 + lane] = (double)a0;
     if (lane + 32 < rb) y[r0 + lane + 32] = (double)a1;

@@ -441,19 +441,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
       if (!update_tile(b, rows, p0, q0)) continue;
       // this thread's entries: row p (its tensor-memory lane), columns q0 + 32 half + [0, 32),
-      // those with q <= p inside the trailing matrix; C is loaded while the copy and the MMAs run
+      // those with q <= p inside the trailing matrix
       const int64_t p = p0 + quarter * 32 + lane;
       const int64_t qb = q0 + half * 32;
       const bool prow = p < rows;
-      double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
-      double2 cv[16];
-#pragma unroll
-      for (int v = 0; v < 16; ++v) {
-        const int64_t q = qb + 2 * v;
-        if (prow && q + 1 <= p) cv[v] = *reinterpret_cast<const double2*>(crow + 2 * v);
-        else cv[v] = make_double2(prow && q <= p ? crow[2 * v] : 0.0, 0.0);
-      }
       const int ep = prow ? e[p] : 0;
+      const int eq_lane = qb + lane < rows ? e[qb + lane] : 0;  // e_q of column qb + lane, passed by shuffles
       int ok = 1;
       if (lane == 0) ok = mbar_wait(mma_done, (uint32_t)it & 1u, abort_flag) && !*abort_flag;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -463,22 +456,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       fence_after();
       // GB300 runs FP64 at 1/64 of the FP32 rate, so the weights are
-      // combined on the integer pipes into one integer,
+      // combined on the integer pipes into one integer per entry,
       //   Z = sum_{w<=5} I_w 2^(42-8w) + round((I_6 2^8 + I_7) 2^-14)
       // (|I_w| <= 7 2^20 and |I_0| <= 2^20: |Z| < 2^63; the rounding is
-      // 2^-43 of sum_w 2^-8w I_w, below the digits' own truncation), and
-      // Z 2^(e_p + e_q - 56) is built as a double on the integer pipes too:
-      // the subtraction from C is the one FP64 operation of an entry
+      // 2^-43 of sum_w 2^-8w I_w, below the digits' own truncation).  All
+      // of the tile's accumulators are read first, so the next tile's MMAs
+      // can start; Z 2^(e_p + e_q - 56) is then built as a double on the
+      // integer pipes and subtracted from C (the one FP64 operation of an
+      // entry) while those MMAs run.
+      long long Z[32];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {  // 8 columns at a time
         uint32_t r[NW][8];
         tmem_ld8x8(lane_addr + (uint32_t)(g * 8), UBN, r);
-        if (g == 3) {  // every accumulator of this warp is read: the next tile's MMAs may start
-          fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(tfree);
-        }
-        double u[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           long long z = 0;
@@ -490,16 +480,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             else if (w == 6) t = v * 256;
             else t += v;
           }
-          const int64_t q = qb + g * 8 + j;
-          u[j] = (prow && q <= p) ? scaled_int_to_double(z + ((t + 8192) >> 14), ep + e[q] - 56) : 0.0;
+          Z[g * 8 + j] = z + ((t + 8192) >> 14);
         }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tfree);  // the accumulators may be overwritten
+      double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int vi = g * 4 + v;
-          const int64_t q = qb + 2 * vi;
-          const double c0 = cv[vi].x - u[2 * v], c1 = cv[vi].y - u[2 * v + 1];
-          if (prow && q + 1 <= p) *reinterpret_cast<double2*>(crow + 2 * vi) = make_double2(c0, c1);
-          else if (prow && q <= p) crow[2 * vi] = c0;
+      for (int v = 0; v < 16; ++v) {
+        if ((v & 3) == 0) asm volatile("" ::: "memory");  // C in batches of 4 loads (registers)
+        const int e0 = __shfl_sync(0xffffffffu, eq_lane, 2 * v), e1 = __shfl_sync(0xffffffffu, eq_lane, 2 * v + 1);
+        const int64_t q = qb + 2 * v;
+        if (prow && q <= p) {
+          const double u0 = scaled_int_to_double(Z[2 * v], ep + e0 - 56);
+          if (q + 1 <= p) {
+            const double u1 = scaled_int_to_double(Z[2 * v + 1], ep + e1 - 56);
+            double2 cv = *reinterpret_cast<const double2*>(crow + 2 * v);
+            cv.x -= u0;
+            cv.y -= u1;
+            *reinterpret_cast<double2*>(crow + 2 * v) = cv;
+          } else {
+            crow[2 * v] -= u0;
+          }
         }
       }
       ++it;
