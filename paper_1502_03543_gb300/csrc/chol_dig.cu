@@ -31,7 +31,7 @@
 // the subtraction: FP64-grade, where the FP64 pipes would take 1/64 of the
 // FP32 rate.
 //
-// k_dig_update: persistent, one CTA per SM over the 128 x 64 tiles, 10 warps:
+// k_dig_update: persistent, one CTA per SM over the 128 x 64 tiles, 18 warps:
 //   warp 0      per tile one TMA load of the 7 planes for rows p (128 x 64
 //               columns) and the 7 planes for rows q (64 x 64 columns),
 //               168 KB, as soon as the previous tile's MMAs are done;
@@ -40,11 +40,14 @@
 //               pairs x 4 K steps, pair (s, t) into weight s + t, as soon as
 //               the planes have landed and the previous tile's accumulators
 //               have been read;
-//   warps 2..9  thread (warp w, lane) owns row 32 (w % 4) + lane of the tile
-//               and columns 32 ((w - 2) / 4).. of it: it loads that part of C
-//               while the copy and the MMAs run, reads its TMEM lane of every
-//               weight, combines the weights and subtracts the scaled update
-//               from C in place (16-byte accesses).
+//   warps 2..17 thread (warp w, lane) owns row 32 (w % 4) + lane of the tile
+//               and columns 16 ((w - 2) / 4).. of it: it reads its TMEM lane
+//               of every weight and combines the weights into one integer
+//               per entry; once all of them have read, the next tile's MMAs
+//               may start, and the thread subtracts the scaled update from
+//               C in place (16-byte accesses).  The epilogue is the longest
+//               stage of a tile (integer work per entry and C's latency), so
+//               it has 16 warps to hide that latency.
 // Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
 // PDAS_ERR_TIMEOUT, lets its copy land and its MMAs finish, frees TMEM, exits.
 #include <cuda.h>
@@ -75,7 +78,8 @@ constexpr uint32_t P_PLANE = UBM * 128;           // 16 KB: 128 rows of one digi
 constexpr uint32_t Q_PLANE = UBN * 128;           // 8 KB: 64 rows of one digit
 constexpr uint32_t LOAD_BYTES = ND * (P_PLANE + Q_PLANE);  // 168 KB
 constexpr uint32_t TMEM_COLS = NW * UBN;          // 512
-constexpr int NUM_THREADS = 320;
+constexpr int NUM_THREADS = 576;                  // 2 role warps + 16 epilogue warps
+constexpr int EPI_WARPS = NUM_THREADS / 32 - 2;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)LOAD_BYTES + 256;
 constexpr uint32_t kIdesc = idesc_bf16(UBM, UBN);
 
@@ -322,14 +326,13 @@ int pick_row_threads(int64_t rows, int sub_partitions) {
   return best;
 }
 
-// Eight tensor-memory loads of 8 columns each (one per weight, w_stride
+// Eight tensor-memory loads of 4 columns each (one per weight, w_stride
 // columns apart) for this warp's 32 lanes, then one wait.
-__device__ __forceinline__ void tmem_ld8x8(uint32_t taddr, uint32_t w_stride, uint32_t (&r)[NW][8]) {
+__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, uint32_t w_stride, uint32_t (&r)[NW][4]) {
 #pragma unroll
   for (int w = 0; w < NW; ++w)
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[w][0]), "=r"(r[w][1]), "=r"(r[w][2]), "=r"(r[w][3]), "=r"(r[w][4]), "=r"(r[w][5]),
-                   "=r"(r[w][6]), "=r"(r[w][7])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[w][0]), "=r"(r[w][1]), "=r"(r[w][2]), "=r"(r[w][3])
                  : "r"(taddr + (uint32_t)w * w_stride));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     mbar_init(full, 1);
     mbar_init(pfree, 1);
     mbar_init(mma_done, 1);
-    mbar_init(tfree, 8);  // one arrival per epilogue warp
+    mbar_init(tfree, EPI_WARPS);  // one arrival per epilogue warp
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -435,18 +438,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     __syncwarp();
   } else {
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
-    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    constexpr int EC = UBN / (EPI_WARPS / 4);  // columns per epilogue thread: 16
+    const int quarter = warp & 3, cg = (warp - 2) >> 2;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cg * EC);
     int it = 0;
     for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
       if (!update_tile(b, rows, p0, q0)) continue;
-      // this thread's entries: row p (its tensor-memory lane), columns q0 + 32 half + [0, 32),
+      // this thread's entries: row p (its tensor-memory lane), columns q0 + 16 cg + [0, 16),
       // those with q <= p inside the trailing matrix
       const int64_t p = p0 + quarter * 32 + lane;
-      const int64_t qb = q0 + half * 32;
+      const int64_t qb = q0 + cg * EC;
       const bool prow = p < rows;
       const int ep = prow ? e[p] : 0;
-      const int eq_lane = qb + lane < rows ? e[qb + lane] : 0;  // e_q of column qb + lane, passed by shuffles
+      const int eq_lane = lane < EC && qb + lane < rows ? e[qb + lane] : 0;  // e_q of column qb + lane, by shuffles
       int ok = 1;
       if (lane == 0) ok = mbar_wait(mma_done, (uint32_t)it & 1u, abort_flag) && !*abort_flag;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -458,29 +462,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // GB300 runs FP64 at 1/64 of the FP32 rate, so the weights are
       // combined on the integer pipes into one integer per entry,
       //   Z = sum_{w<=5} I_w 2^(42-8w) + round((I_6 2^8 + I_7) 2^-14)
-      // (|I_w| <= 7 2^20 and |I_0| <= 2^20: |Z| < 2^63; the rounding is
-      // 2^-43 of sum_w 2^-8w I_w, below the digits' own truncation).  All
-      // of the tile's accumulators are read first, so the next tile's MMAs
-      // can start; Z 2^(e_p + e_q - 56) is then built as a double on the
-      // integer pipes and subtracted from C (the one FP64 operation of an
-      // entry) while those MMAs run.
-      long long Z[32];
+      //     = t_01 2^34 + t_23 2^18 + t_45 2^2 + round(t_67 2^-14),
+      //   t_ab = I_a 2^8 + I_b, exact in int32 (|I_w| <= 7 2^20)
+      // (|I_0| <= 2^20: |Z| < 2^63; the rounding is 2^-43 of
+      // sum_w 2^-8w I_w, below the digits' own truncation).  All of the
+      // tile's accumulators are read first, so the next tile's MMAs can
+      // start; Z 2^(e_p + e_q - 56) is then built as a double on the integer
+      // pipes and subtracted from C (the one FP64 operation of an entry)
+      // while those MMAs run.
+      long long Z[EC];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {  // 8 columns at a time
-        uint32_t r[NW][8];
-        tmem_ld8x8(lane_addr + (uint32_t)(g * 8), UBN, r);
+      for (int g = 0; g < EC / 4; ++g) {  // 4 columns at a time
+        uint32_t r[NW][4];
+        tmem_ld8x4(lane_addr + (uint32_t)(g * 4), UBN, r);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          long long z = 0;
-          int t = 0;
+        for (int j = 0; j < 4; ++j) {
+          int iw[NW];
 #pragma unroll
-          for (int w = 0; w < NW; ++w) {
-            const int v = __float2int_rn(__uint_as_float(r[w][j]));
-            if (w <= 5) z += (long long)v * (1ll << (42 - 8 * w));
-            else if (w == 6) t = v * 256;
-            else t += v;
-          }
-          Z[g * 8 + j] = z + ((t + 8192) >> 14);
+          for (int w = 0; w < NW; ++w) iw[w] = __float2int_rn(__uint_as_float(r[w][j]));
+          const int t01 = iw[0] * 256 + iw[1], t23 = iw[2] * 256 + iw[3], t45 = iw[4] * 256 + iw[5];
+          const int t67 = iw[6] * 256 + iw[7];
+          Z[g * 4 + j] = (long long)t01 * (1ll << 34) + (long long)t23 * (1ll << 18) + (long long)t45 * 4 +
+                         ((t67 + 8192) >> 14);
         }
       }
       fence_before();
@@ -488,8 +491,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (lane == 0) mbar_arrive(tfree);  // the accumulators may be overwritten
       double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
 #pragma unroll
-      for (int v = 0; v < 16; ++v) {
-        if ((v & 3) == 0) asm volatile("" ::: "memory");  // C in batches of 4 loads (registers)
+      for (int v = 0; v < EC / 2; ++v) {
         const int e0 = __shfl_sync(0xffffffffu, eq_lane, 2 * v), e1 = __shfl_sync(0xffffffffu, eq_lane, 2 * v + 1);
         const int64_t q = qb + 2 * v;
         if (prow && q <= p) {
