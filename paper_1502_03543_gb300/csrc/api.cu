@@ -412,14 +412,19 @@ pdas_status factor(pdas_ctx* h) {
 // out = (L L')^{-1} rhs with the current factor (via h->z).
 pdas_status factor_solve(pdas_ctx* h, const double* rhs, double* out) {
   if (h->cur_f64) {
-    KL(trsv_lower<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, rhs, h->z, h->flags, h->tickets, h->sc), 1);
-    KL(trsv_upper_t<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->z, out, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_lower<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, rhs, h->z, h->flags, h->tickets, h->sc,
+                          is_mixed(h)),
+       1);
+    KL(trsv_upper_t<double>(h->st, h->m, h->ldm, h->M64, h->dinv64, h->z, out, h->flags, h->tickets, h->sc,
+                            is_mixed(h)),
+       1);
   } else if (h->chol_ntasks > 0) {  // the tile factor, with the inverses of its diagonal tiles
     KL(trsv_lower_blk(h->st, h->m, h->ldm, h->M32, h->uinv32, rhs, h->z, h->tickets + T_TRSV, h->sc), 1);
     KL(trsv_upper_blk(h->st, h->m, h->ldm, h->M32, h->uinv32, h->z, out, h->tickets + T_TRSV, h->sc), 1);
   } else {
-    KL(trsv_lower<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, rhs, h->z, h->flags, h->tickets, h->sc), 1);
-    KL(trsv_upper_t<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->z, out, h->flags, h->tickets, h->sc), 1);
+    KL(trsv_lower<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, rhs, h->z, h->flags, h->tickets, h->sc, true), 1);
+    KL(trsv_upper_t<float>(h->st, h->m, h->ldm, h->M32, h->dinv32, h->z, out, h->flags, h->tickets, h->sc, true),
+       1);
   }
   return PDAS_OK;
 }

@@ -225,10 +225,14 @@ __device__ __forceinline__ int red_row(int lane) { return 4 * ((lane >> 4) & 1) 
 // Arithmetic in T (the factor's precision; the FP32 factor of the mixed forms
 // is a preconditioner, refined in FP64 afterwards); v, z in FP64.  Warp w
 // owns rows 8w..8w+7 of the block, lane l owns columns l, l+32; the diagonal
-// block is solved by warp 0 on its rows divided by their pivots,
-// z_r = v_r / L_rr - sum_{c<r} (L_rc / L_rr) z_c, so a step of its chain is
-// one shuffle and one multiply-add (no multiply by 1 / L_cc on the chain).
-template <typename T>
+// block is solved by warp 0.  SCALED (the FP64 tier of the mixed forms,
+// whose refinement takes the solve as a preconditioner): on its rows divided
+// by their pivots, z_r = v_r / L_rr - sum_{c<r} (L_rc / L_rr) z_c, so a step
+// of its chain is one shuffle and one multiply-add, and the eight row sums
+// of a warp are combined by a reduce-scatter.  Otherwise (the plain FP64
+// form's direct solve, Section V-A) by substitution with the pivot
+// reciprocals and a butterfly per row.
+template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm, const T* __restrict__ L,
                                                          const T* __restrict__ dinv, const double* __restrict__ v,
                                                          double* z, int* flags, unsigned* ticket, Scalars* sc) {
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int i = e / kTile, j = e % kTile;
-    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] * dinv[r0 + i] : T(0);  // row i over L_ii
+    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] * (SCALED ? dinv[r0 + i] : T(1)) : T(0);  // row i over L_ii
   }
   if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
   T part[8];
@@ -269,25 +273,50 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
 #pragma unroll
     for (int i = 0; i < 8; ++i) part[i] = fma(l0[i], z0, fma(l1[i], z1, part[i]));
   }
-  {
+  if constexpr (SCALED) {
     const T t = warp_reduce_scatter8(part, lane);
     const int r = 8 * w + red_row(lane);
     if ((lane & 3) == 0) acc[r] = r < rb ? (T)v[r0 + r] - t : T(0);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      T t = part[i];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const int r = 8 * w + i;
+      if (lane == 0) acc[r] = r < rb ? (T)v[r0 + r] - t : T(0);
+    }
   }
   if (__syncthreads_or(!ok)) return;  // a wait gave up: the status says why
   if (w == 0) {
-    // the scaled right-hand side; rows 0..31 finish at column 31, so the
-    // second half of the sweep updates a1 only
-    T a0 = acc[lane] * rcp[lane], a1 = acc[lane + 32] * rcp[lane + 32];
-    const int c1 = rb < 32 ? rb : 32;
-    for (int c = 0; c < c1; ++c) {
-      const T zc = __shfl_sync(0xffffffffu, a0, c);
-      if (lane > c) a0 = fma(-Ld[lane][c], zc, a0);
-      a1 = fma(-Ld[lane + 32][c], zc, a1);
-    }
-    for (int c = 32; c < rb; ++c) {
-      const T zc = __shfl_sync(0xffffffffu, a1, c - 32);
-      if (lane + 32 > c) a1 = fma(-Ld[lane + 32][c], zc, a1);
+    T a0, a1;
+    if constexpr (SCALED) {
+      // the scaled right-hand side; rows 0..31 finish at column 31, so the
+      // second half of the sweep updates a1 only
+      a0 = acc[lane] * rcp[lane];
+      a1 = acc[lane + 32] * rcp[lane + 32];
+      const int c1 = rb < 32 ? rb : 32;
+      for (int c = 0; c < c1; ++c) {
+        const T zc = __shfl_sync(0xffffffffu, a0, c);
+        if (lane > c) a0 = fma(-Ld[lane][c], zc, a0);
+        a1 = fma(-Ld[lane + 32][c], zc, a1);
+      }
+      for (int c = 32; c < rb; ++c) {
+        const T zc = __shfl_sync(0xffffffffu, a1, c - 32);
+        if (lane + 32 > c) a1 = fma(-Ld[lane + 32][c], zc, a1);
+      }
+    } else {
+      a0 = acc[lane];
+      a1 = acc[lane + 32];
+      for (int c = 0; c < rb; ++c) {
+        const T own = c < 32 ? a0 : a1;
+        const T zc = __shfl_sync(0xffffffffu, own, c & 31) * rcp[c];
+        if (lane == (c & 31)) {
+          if (c < 32) a0 = zc;
+          else a1 = zc;
+        }
+        if (lane > c) a0 -= Ld[lane][c] * zc;
+        if (lane + 32 > c) a1 -= Ld[lane + 32][c] * zc;
+      }
     }
     if (lane < rb) z[r0 + lane] = (double)a0;
     if (lane + 32 < rb) z[r0 + lane + 32] = (double)a1;
@@ -300,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_lower(int64_t m, int64_t ldm,
 // L' y = z.  Row block b of L' is column block b of L; blocks go from the
 // last to the first.  For each later block kb, thread (w, lane) adds
 // L[k][r] y_k for rows k = 8w..8w+7 of that block and columns r = lane, lane+32.
-template <typename T>
+template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ldm, const T* __restrict__ L,
                                                            const T* __restrict__ dinv,
                                                            const double* __restrict__ zin, double* y, int* flags,
@@ -319,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int i = e / kTile, j = e % kTile;
-    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] * dinv[r0 + j] : T(0);  // column j over L_jj
+    Ld[i][j] = (i < rb && j < i) ? L[(r0 + i) * ldm + r0 + j] * (SCALED ? dinv[r0 + j] : T(1)) : T(0);  // column j over L_jj
   }
   if (threadIdx.x < kTile) rcp[threadIdx.x] = threadIdx.x < rb ? dinv[r0 + threadIdx.x] : T(0);
   T p0 = T(0), p1 = T(0);
@@ -356,18 +385,33 @@ __global__ void __launch_bounds__(kThreads) k_trsv_upper_t(int64_t m, int64_t ld
       a0 += red[i][lane];
       a1 += red[i][lane + 32];
     }
-    // rows divided by their pivots (the coefficients were scaled at the
-    // load): a step of the chain is one shuffle and one multiply-add
-    a0 = (lane < rb ? (T)zin[r0 + lane] - a0 : T(0)) * rcp[lane];
-    a1 = (lane + 32 < rb ? (T)zin[r0 + lane + 32] - a1 : T(0)) * rcp[lane + 32];
-    for (int c = rb - 1; c >= 32; --c) {
-      const T yc = __shfl_sync(0xffffffffu, a1, c - 32);
-      if (lane + 32 < c) a1 = fma(-Ld[c][lane + 32], yc, a1);
-      a0 = fma(-Ld[c][lane], yc, a0);
-    }
-    for (int c = (rb < 32 ? rb : 32) - 1; c >= 0; --c) {
-      const T yc = __shfl_sync(0xffffffffu, a0, c);
-      if (lane < c) a0 = fma(-Ld[c][lane], yc, a0);
+    a0 = lane < rb ? (T)zin[r0 + lane] - a0 : T(0);
+    a1 = lane + 32 < rb ? (T)zin[r0 + lane + 32] - a1 : T(0);
+    if constexpr (SCALED) {
+      // rows divided by their pivots (the coefficients were scaled at the
+      // load): a step of the chain is one shuffle and one multiply-add
+      a0 *= rcp[lane];
+      a1 *= rcp[lane + 32];
+      for (int c = rb - 1; c >= 32; --c) {
+        const T yc = __shfl_sync(0xffffffffu, a1, c - 32);
+        if (lane + 32 < c) a1 = fma(-Ld[c][lane + 32], yc, a1);
+        a0 = fma(-Ld[c][lane], yc, a0);
+      }
+      for (int c = (rb < 32 ? rb : 32) - 1; c >= 0; --c) {
+        const T yc = __shfl_sync(0xffffffffu, a0, c);
+        if (lane < c) a0 = fma(-Ld[c][lane], yc, a0);
+      }
+    } else {
+      for (int c = rb - 1; c >= 0; --c) {
+        const T own = c < 32 ? a0 : a1;
+        const T yc = __shfl_sync(0xffffffffu, own, c & 31) * rcp[c];
+        if (lane == (c & 31)) {
+          if (c < 32) a0 = yc;
+          else a1 = yc;
+        }
+        if (lane < c) a0 -= Ld[c][lane] * yc;
+        if (lane + 32 < c) a1 -= Ld[c][lane + 32] * yc;
+      }
     }
     if (lane < rb) y[r0 + lane] = (double)a0;
     if (lane + 32 < rb) y[r0 + lane + 32] = (double)a1;
@@ -403,35 +447,41 @@ cudaError_t cholesky(cudaStream_t st, int64_t m, int64_t ldm, T* M, T* dinv, Sca
 
 template <typename T>
 cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* v, double* z,
-                       int* flags, unsigned* tickets, Scalars* sc) {
+                       int* flags, unsigned* tickets, Scalars* sc, bool scaled) {
   const int64_t nblk = (m + kTile - 1) / kTile;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets + T_TRSV, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_trsv_lower<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, v, z, flags, tickets + T_TRSV, sc);
+  if (scaled)
+    k_trsv_lower<T, true><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, v, z, flags, tickets + T_TRSV, sc);
+  else
+    k_trsv_lower<T, false><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, v, z, flags, tickets + T_TRSV, sc);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* z,
-                         double* y, int* flags, unsigned* tickets, Scalars* sc) {
+                         double* y, int* flags, unsigned* tickets, Scalars* sc, bool scaled) {
   const int64_t nblk = (m + kTile - 1) / kTile;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * nblk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets + T_TRSV, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_trsv_upper_t<T><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, z, y, flags, tickets + T_TRSV, sc);
+  if (scaled)
+    k_trsv_upper_t<T, true><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, z, y, flags, tickets + T_TRSV, sc);
+  else
+    k_trsv_upper_t<T, false><<<(unsigned)nblk, kThreads, 0, st>>>(m, ldm, L, dinv, z, y, flags, tickets + T_TRSV, sc);
   return cudaGetLastError();
 }
 
 template cudaError_t cholesky<double>(cudaStream_t, int64_t, int64_t, double*, double*, Scalars*);
 template cudaError_t cholesky<float>(cudaStream_t, int64_t, int64_t, float*, float*, Scalars*);
 template cudaError_t trsv_lower<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, const double*,
-                                        double*, int*, unsigned*, Scalars*);
+                                        double*, int*, unsigned*, Scalars*, bool);
 template cudaError_t trsv_lower<float>(cudaStream_t, int64_t, int64_t, const float*, const float*, const double*,
-                                       double*, int*, unsigned*, Scalars*);
+                                       double*, int*, unsigned*, Scalars*, bool);
 template cudaError_t trsv_upper_t<double>(cudaStream_t, int64_t, int64_t, const double*, const double*, const double*,
-                                          double*, int*, unsigned*, Scalars*);
+                                          double*, int*, unsigned*, Scalars*, bool);
 template cudaError_t trsv_upper_t<float>(cudaStream_t, int64_t, int64_t, const float*, const float*, const double*,
-                                         double*, int*, unsigned*, Scalars*);
+                                         double*, int*, unsigned*, Scalars*, bool);
 
 }  // namespace pdas

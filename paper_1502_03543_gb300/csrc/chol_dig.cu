@@ -4,7 +4,12 @@
 //
 // Per 64-column panel k0 (kb = min(64, m - k0) columns):
 //   k_dig_diag                      -- the FP64 factor L_11 of the diagonal
-//                                      block (LDL' form) and 1 / L_cc;
+//                                      block (LDL' form) and 1 / L_cc: a
+//                                      launch of its own for the first panel;
+//                                      for the others CTA 0 of the previous
+//                                      panel's update factors the block right
+//                                      after writing tile 0, which holds it,
+//                                      while the other CTAs update the rest;
 //   k_dig_panel_rows                -- the panel rows P (trailing rows
 //                                      r >= k0 + kb, the kb panel columns)
 //                                      solved in FP64, P L_11' = B, 32 rows
@@ -153,61 +158,74 @@ __device__ __forceinline__ double inv_pivot(double d) {
 // PDAS_ERR_NOT_SPD with its index.
 constexpr int DG_THREADS = 256;
 constexpr int DG_TRI = (UK - 1) * UK / 2;  // entries of the largest trailing triangle
-__global__ void __launch_bounds__(DG_THREADS) k_dig_diag(int64_t ldm, double* __restrict__ M,
-                                                         double* __restrict__ dinv, int64_t k0, int kb, Scalars* sc) {
-  __shared__ double Ld[UK][UK + 1];
-  __shared__ double tcol[UK];             // t_i of the current column
-  __shared__ double s_rp[UK];
-  __shared__ unsigned short tri[DG_TRI];  // e -> (r, s), e = r (r + 1) / 2 + s, s <= r: r << 8 | s
-  __shared__ double s_inv;                // 1 / d_c of the next column; < 0: not positive definite
-  if (*(volatile const int*)&sc->status != 0) return;
-  for (int t = threadIdx.x; t < UK * UK; t += DG_THREADS) {
+struct DiagSmem {
+  double Ld[UK][UK + 1];
+  double tcol[UK];             // t_i of the current column
+  double s_rp[UK];
+  double s_inv;                // 1 / d_c of the next column; < 0: not positive definite
+  unsigned short tri[DG_TRI];  // e -> (r, s), e = r (r + 1) / 2 + s, s <= r: r << 8 | s
+};
+
+// The factor itself, by NT threads (tid) that meet at bar().
+template <int NT, class Bar>
+__device__ __forceinline__ void diag_factor(int64_t ldm, double* __restrict__ M, double* __restrict__ dinv,
+                                            int64_t k0, int kb, Scalars* sc, DiagSmem& S, int tid, Bar bar) {
+  for (int t = tid; t < UK * UK; t += NT) {
     const int i = t / UK, j = t % UK;
-    if (j <= i && i < kb) Ld[i][j] = M[(k0 + i) * ldm + k0 + j];
+    if (j <= i && i < kb) S.Ld[i][j] = M[(k0 + i) * ldm + k0 + j];
   }
-  for (int e = threadIdx.x; e < DG_TRI; e += DG_THREADS) {
+  for (int e = tid; e < DG_TRI; e += NT) {
     int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
     while (r * (r + 1) / 2 > e) --r;
     while ((r + 1) * (r + 2) / 2 <= e) ++r;
-    tri[e] = (unsigned short)((r << 8) | (e - r * (r + 1) / 2));
+    S.tri[e] = (unsigned short)((r << 8) | (e - r * (r + 1) / 2));
   }
-  __syncthreads();
-  if (threadIdx.x == 0) s_inv = inv_pivot(Ld[0][0]);
+  bar();
+  if (tid == 0) S.s_inv = inv_pivot(S.Ld[0][0]);
   int fail = -1;
   for (int c = 0; c < kb; ++c) {
-    __syncthreads();  // the update for column c - 1 is complete and 1 / d_c posted
-    const double inv = s_inv;
+    bar();  // the update for column c - 1 is complete and 1 / d_c posted
+    const double inv = S.s_inv;
     if (inv < 0.0) {
       fail = c;
       break;
     }
     const int rest = kb - 1 - c;
-    if (threadIdx.x < rest) tcol[c + 1 + threadIdx.x] = Ld[c + 1 + threadIdx.x][c] * inv;
-    __syncthreads();
+    if (tid < rest) S.tcol[c + 1 + tid] = S.Ld[c + 1 + tid][c] * inv;
+    bar();
     const int ne = rest * (rest + 1) / 2;
-    for (int e = threadIdx.x; e < ne; e += DG_THREADS) {
-      const int rs = tri[e], i = c + 1 + (rs >> 8), j = c + 1 + (rs & 0xff);
-      const double v = fma(-tcol[i], Ld[j][c], Ld[i][j]);
-      Ld[i][j] = v;
-      if (e == 0) s_inv = inv_pivot(v);  // thread 0: d_c+1 is final
+    for (int e = tid; e < ne; e += NT) {
+      const int rs = S.tri[e], i = c + 1 + (rs >> 8), j = c + 1 + (rs & 0xff);
+      const double v = fma(-S.tcol[i], S.Ld[j][c], S.Ld[i][j]);
+      S.Ld[i][j] = v;
+      if (e == 0) S.s_inv = inv_pivot(v);  // thread 0: d_c+1 is final
     }
   }
   if (fail >= 0) {  // every thread read the same pivot
-    if (threadIdx.x == 0 && atomicCAS(&sc->status, 0, (int)PDAS_ERR_NOT_SPD) == 0) sc->fail_index = (int)(k0 + fail);
+    if (tid == 0 && atomicCAS(&sc->status, 0, (int)PDAS_ERR_NOT_SPD) == 0) sc->fail_index = (int)(k0 + fail);
     return;
   }
-  __syncthreads();
-  if (threadIdx.x < kb) {
-    const double l = sqrt(Ld[threadIdx.x][threadIdx.x]);
-    Ld[threadIdx.x][threadIdx.x] = l;
-    s_rp[threadIdx.x] = 1.0 / l;
-    dinv[k0 + threadIdx.x] = s_rp[threadIdx.x];
+  bar();
+  if (tid < kb) {
+    const double l = sqrt(S.Ld[tid][tid]);
+    S.Ld[tid][tid] = l;
+    S.s_rp[tid] = 1.0 / l;
+    dinv[k0 + tid] = S.s_rp[tid];
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < UK * UK; t += DG_THREADS) {
+  bar();
+  for (int t = tid; t < UK * UK; t += NT) {
     const int i = t / UK, j = t % UK;
-    if (j <= i && i < kb) M[(k0 + i) * ldm + k0 + j] = j < i ? Ld[i][j] * s_rp[j] : Ld[i][i];
+    if (j <= i && i < kb) M[(k0 + i) * ldm + k0 + j] = j < i ? S.Ld[i][j] * S.s_rp[j] : S.Ld[i][i];
   }
+}
+
+// The first panel's diagonal block (the others are factored inside the
+// previous panel's update, k_dig_update).
+__global__ void __launch_bounds__(DG_THREADS) k_dig_diag(int64_t ldm, double* __restrict__ M,
+                                                         double* __restrict__ dinv, int64_t k0, int kb, Scalars* sc) {
+  __shared__ DiagSmem S;
+  if (*(volatile const int*)&sc->status != 0) return;
+  diag_factor<DG_THREADS>(ldm, M, dinv, k0, kb, sc, S, (int)threadIdx.x, [] { __syncthreads(); });
 }
 
 // The panel rows r = k0 + kb + i (i < rows): X L_11' = B in FP64 (B the kb
@@ -357,7 +375,7 @@ __device__ __forceinline__ bool update_tile(int64_t b, int64_t rows, int64_t& p0
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_dig_update(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int64_t ldm,
                  double* __restrict__ M, int64_t base, int64_t rows, int64_t ntiles, const int* __restrict__ e,
-                 Scalars* sc) {
+                 double* __restrict__ dinv, int kbn, Scalars* sc) {
   extern __shared__ uint8_t smem_raw[];
   if (*(volatile const int*)&sc->status != 0) return;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -365,6 +383,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LOAD_BYTES);  // full | free | mma done | tmem free | drain
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* diag_go = reinterpret_cast<volatile int*>(tmem_slot + 2);
   const uint32_t full = smem_u32(bars), pfree = smem_u32(bars + 1), mma_done = smem_u32(bars + 2),
                  tfree = smem_u32(bars + 3), drain = smem_u32(bars + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -384,11 +403,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   fence_after();
   const uint32_t tmem = *tmem_slot;
   int64_t p0, q0;
+  // with the next panel's diagonal block folded in (kbn > 0), CTA 0 takes
+  // tile 0 alone (the tile that holds that block) and factors the block
+  // once the tile is written; the other CTAs share the rest of the tiles
+  const bool fold = kbn > 0;
+  const int64_t b_step = !fold ? (int64_t)gridDim.x : (blockIdx.x == 0 ? ntiles : (int64_t)gridDim.x - 1);
 
   if (warp == 0) {
     if (lane == 0) {
       int it = 0;
-      for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+      for (int64_t b = blockIdx.x; b < ntiles; b += b_step) {
         if (!update_tile(b, rows, p0, q0)) continue;
         if (it > 0 && !mbar_wait(pfree, (uint32_t)(it - 1) & 1u, abort_flag)) {
           *abort_flag = 1;
@@ -405,7 +429,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       int it = 0;
-      for (int64_t b = blockIdx.x; b < ntiles && !*abort_flag; b += gridDim.x) {
+      for (int64_t b = blockIdx.x; b < ntiles && !*abort_flag; b += b_step) {
         if (!update_tile(b, rows, p0, q0)) continue;
         if (!mbar_wait(full, (uint32_t)it & 1u, abort_flag) ||
             (it > 0 && !mbar_wait(tfree, (uint32_t)(it - 1) & 1u, abort_flag))) {
@@ -442,7 +466,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int quarter = warp & 3, cg = (warp - 2) >> 2;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cg * EC);
     int it = 0;
-    for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+    for (int64_t b = blockIdx.x; b < ntiles; b += b_step) {
       if (!update_tile(b, rows, p0, q0)) continue;
       // this thread's entries: row p (its tensor-memory lane), columns q0 + 16 cg + [0, 16),
       // those with q <= p inside the trailing matrix
@@ -509,6 +533,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       ++it;
     }
+    if (fold && blockIdx.x == 0) {
+      // tile 0 is written (the barrier orders every epilogue thread's stores
+      // before the reads below) and its MMAs are done, so the plane buffer is
+      // free: the epilogue warps factor the next panel's diagonal block there,
+      // if no wait of this CTA gave up (one thread decides, all follow)
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+      if (threadIdx.x == 64) *diag_go = !*abort_flag;
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+      if (*diag_go)
+        diag_factor<EPI_WARPS * 32>(ldm, M, dinv, base, kbn, sc, *reinterpret_cast<DiagSmem*>(smem),
+                                    (int)threadIdx.x - 64,
+                                    [] { asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory"); });
+    }
   }
   if (threadIdx.x == 0 && *abort_flag) atomicCAS(&sc->status, 0, (int)PDAS_ERR_TIMEOUT);
   fence_before();
@@ -518,6 +555,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tmem_dealloc(tmem, TMEM_COLS);
   }
 }
+static_assert(sizeof(DiagSmem) <= LOAD_BYTES, "the folded diagonal factor fits the plane buffer");
 
 struct CholDigHost {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -595,9 +633,11 @@ cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, doub
   for (int64_t k0 = 0; k0 < m && e == cudaSuccess; k0 += UK) {
     const int kb = (int)std::min<int64_t>(UK, m - k0);
     const int64_t rows = m - k0 - kb;  // the trailing matrix
-    k_dig_diag<<<1, DG_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, sc);
-    ++*launches;
-    e = cudaGetLastError();
+    if (k0 == 0) {  // later diagonal blocks are factored inside the previous panel's update
+      k_dig_diag<<<1, DG_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, sc);
+      ++*launches;
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess || rows == 0) continue;
     __nv_bfloat16* planes = static_cast<__nv_bfloat16*>(w->planes);
     switch (pick_row_threads(rows, w->sub_partitions)) {
@@ -619,7 +659,9 @@ cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, doub
     }
     const int64_t nI = (rows + UBM - 1) / UBM, ntiles = nI * (nI + 1);
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, w->sub_partitions / 4);
-    k_dig_update<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb, rows, ntiles, w->e, sc);
+    const int kbn = (int)std::min<int64_t>(UK, rows);  // the next panel's width: its diagonal block is folded in
+    k_dig_update<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb, rows, ntiles, w->e,
+                                                        dinv, kbn, sc);
     *launches += 2;
     e = cudaGetLastError();
   }

@@ -167,12 +167,15 @@ cudaError_t trsv_lower_blk(cudaStream_t st, int64_t m, int64_t ldm, const float*
                            const double* v, double* z, unsigned* ticket, Scalars* sc);
 cudaError_t trsv_upper_blk(cudaStream_t st, int64_t m, int64_t ldm, const float* L, const float* Uinv,
                            const double* z, double* y, unsigned* ticket, Scalars* sc);
+// scaled: the diagonal blocks are solved on pivot-scaled rows (the FP64 tier
+// of the mixed forms, a preconditioner: shorter chains); else by plain
+// substitution (the plain FP64 form's direct solve).
 template <typename T>
 cudaError_t trsv_lower(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* v,
-                       double* z, int* flags, unsigned* tickets, Scalars* sc);
+                       double* z, int* flags, unsigned* tickets, Scalars* sc, bool scaled);
 template <typename T>
 cudaError_t trsv_upper_t(cudaStream_t st, int64_t m, int64_t ldm, const T* L, const T* dinv, const double* z,
-                         double* y, int* flags, unsigned* tickets, Scalars* sc);
+                         double* y, int* flags, unsigned* tickets, Scalars* sc, bool scaled);
 
 // sc->mnorm = max_p M[p][p] (before the factorization overwrites it).
 template <typename T>
