@@ -739,14 +739,17 @@ def test_fp64_tier_whole_solve(pdas, storage):
     assert np.linalg.norm(lp.A64.T @ yh + sh - lp.c) <= 1e-12 * np.linalg.norm(lp.c)
 
 
-def test_tensor_core_factor_whole_solve(pdas):
+@pytest.mark.parametrize("m", [320, 300])
+def test_tensor_core_factor_whole_solve(pdas, m):
     """BF16 A forced into the FP64 tier from the first iteration at m = 320
-    (above the size where the tier's factor moves to the tensor cores: five
-    64-column panels, ragged trailing tiles): every iteration's direction
-    comes from the digit-plane normal matrix and the tensor-core factor (no
-    fallback after a failed pivot), and the solve reaches the oracle's
-    objective in the oracle's number of iterations."""
-    lp = lpgen.generate(320, 1280, seed=23, storage="bf16", scaled=True)
+    and 300 (above the size where the tier's factor moves to the tensor
+    cores: five 64-column panels, ragged trailing tiles; at 300 the last
+    panel is 44 columns wide, so the diagonal block factored inside the last
+    update is narrower than a panel): every iteration's direction comes from
+    the digit-plane normal matrix and the tensor-core factor (no fallback
+    after a failed pivot), and the solve reaches the oracle's objective in
+    the oracle's number of iterations."""
+    lp = lpgen.generate(m, 4 * m, seed=23, storage="bf16", scaled=True)
     ref = oracle.solve(lp.A64, lp.b, lp.c, lp.x0, lp.y0, lp.s0)
     x, y, s = dv(lp.x0), dv(lp.y0), dv(lp.s0)
     A, b, c = dev_A(lp), dv(lp.b), dv(lp.c)
@@ -757,6 +760,32 @@ def test_tensor_core_factor_whole_solve(pdas):
     assert info["rel_gap"] < 1e-8
     obj_ref = float(lp.c @ ref["x"])
     assert abs(float(lp.c @ host(x)) - obj_ref) <= 1e-8 * abs(obj_ref)
+
+
+@pytest.mark.parametrize("m", [300, 700, 1000])
+def test_tensor_core_factor_ragged(pdas, m):
+    """The FP64 tier's tensor-core factor (FP64 diagonal blocks, the next
+    panel's block factored inside the update, FP64 panel rows, trailing
+    updates from exact digit planes) at sizes that are not multiples of the
+    64-column panel or the 128-row tile.  Every row of |LL' - M| within
+    gamma_{m+1}(u64) |L||L'| plus the digits' truncation (2^-40 of
+    sqrt(M_pp M_qq), as at full size)."""
+    lp = lpgen.generate(m, 4 * m, seed=m, storage="bf16", scaled=True)
+    A = dev_A(lp)
+    x0, s0 = dv(lp.x0), dv(lp.s0)
+    with pdas.Solver(m, lp.n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
+        _, _, _, info = S.direction(A, x0, s0)
+        assert info["used_fp64"] == 1 and info["factor_form"] == 4, info
+        S.form_normal(A, x0, s0)
+        M = host(S.copy_matrix()).astype(np.float64)
+        S.factor()
+        L = np.tril(host(S.copy_matrix()).astype(np.float64))
+    Ml = np.tril(M) + np.tril(M, -1).T
+    d = np.sqrt(np.diag(Ml))
+    err = np.abs(L @ L.T - Ml)
+    bound = gamma(m + 1, U64) * (np.abs(L) @ np.abs(L).T) + 2.0 ** -40 * np.outer(d, d)
+    assert np.all(err <= bound), float((err / bound).max())
+    assert float((err / np.outer(d, d)).max()) <= 1e-14
 
 
 def test_stop_rules_match_oracle(pdas):
