@@ -182,6 +182,25 @@ def test_not_spd_reports_pivot(pdas, form, dt, m, bad):
         assert st == -3 and S.last_error_index() == bad
 
 
+@pytest.mark.parametrize("bad", [10, 97, 290])
+def test_not_spd_reports_pivot_tensor_core_factor(pdas, bad):
+    """The FP64 tier's tensor-core factor at m = 300 (five 64-column panels,
+    the last 44 wide) reports a pivot that is not positive with its index:
+    in the first panel (the diagonal block's own launch), in a later panel
+    (the block factored inside the previous panel's update) and in the last,
+    narrower panel."""
+    m = 300
+    lp = lpgen.generate(m, 4 * m, seed=5, storage="bf16", scaled=True)
+    M = np.eye(m)
+    M[bad, bad] = -1.0
+    with pdas.Solver(m, lp.n, "bf16_ir", torch.bfloat16, dspread_refactor=1e-300) as S:
+        _, _, _, info = S.direction(dev_A(lp), dv(lp.x0), dv(lp.s0))
+        assert info["factor_form"] == 4
+        S.load_matrix(dv(M))
+        st = S.factor(raise_on_error=False)
+        assert st == -3 and S.last_error_index() == bad
+
+
 def lapack_direction(A, x, s):
     D = x / s
     M = (A * D) @ A.T
