@@ -86,7 +86,44 @@ constexpr uint32_t TMEM_COLS = NW * UBN;          // 512
 constexpr int NUM_THREADS = 576;                  // 2 role warps + 16 epilogue warps
 constexpr int EPI_WARPS = NUM_THREADS / 32 - 2;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)LOAD_BYTES + 256;
-constexpr uint32_t kIdesc = idesc_bf16(UBM, UBN);
+
+// The pairs (s, t) with a fixed s have consecutive t; the Q planes t lie one
+// after another in shared memory (64 rows each, the same 8-row group stride)
+// and the accumulators of the weights s + t one after another in tensor
+// memory, so one MMA with N = 64 x (pairs) covers up to 4 of them.  A group
+// starts its weights' accumulators (no accumulation at its first K step)
+// when it holds the first product of each of them: pair (0, w), or (1, 6)
+// for w = 7, which therefore gets a group of its own.
+struct MmaGroup {
+  int s, t0, nt;
+  bool first;
+};
+constexpr int NGROUP = 12;
+__host__ __device__ constexpr MmaGroup mma_group(int g) {
+  constexpr MmaGroup G[NGROUP] = {{0, 0, 4, true},  {0, 4, 3, true},  {1, 0, 4, false}, {1, 4, 2, false},
+                                  {1, 6, 1, true},  {2, 0, 4, false}, {2, 4, 2, false}, {3, 0, 4, false},
+                                  {3, 4, 1, false}, {4, 0, 4, false}, {5, 0, 3, false}, {6, 0, 2, false}};
+  return G[g];
+}
+// the groups cover each pair (s, t), s + t <= WMAX, once; a group's first
+// flag holds exactly when each of its weights first appears in it
+constexpr bool groups_ok() {
+  int seen[ND][ND] = {};
+  bool started[NW] = {};
+  int pairs = 0;
+  for (int g = 0; g < NGROUP; ++g) {
+    const MmaGroup G = mma_group(g);
+    if (G.nt < 1 || G.nt > 4 || G.t0 + G.nt > ND) return false;
+    for (int t = G.t0; t < G.t0 + G.nt; ++t) {
+      if (G.s + t > WMAX || seen[G.s][t]++) return false;
+      if (started[G.s + t] == G.first) return false;
+      ++pairs;
+    }
+    for (int t = G.t0; t < G.t0 + G.nt; ++t) started[G.s + t] = true;
+  }
+  return pairs == NPAIR;
+}
+static_assert(groups_ok(), "MMA groups of the digit pairs");
 
 static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
 
@@ -344,13 +381,13 @@ int pick_row_threads(int64_t rows, int sub_partitions) {
   return best;
 }
 
-// Eight tensor-memory loads of 4 columns each (one per weight, w_stride
+// Eight tensor-memory loads of 2 columns each (one per weight, w_stride
 // columns apart) for this warp's 32 lanes, then one wait.
-__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, uint32_t w_stride, uint32_t (&r)[NW][4]) {
+__device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t w_stride, uint32_t (&r)[NW][2]) {
 #pragma unroll
   for (int w = 0; w < NW; ++w)
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[w][0]), "=r"(r[w][1]), "=r"(r[w][2]), "=r"(r[w][3])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(r[w][0]), "=r"(r[w][1])
                  : "r"(taddr + (uint32_t)w * w_stride));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -438,20 +475,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
 #pragma unroll
-        for (int s = 0; s < ND; ++s) {
-          const uint64_t ad = sdesc_sw128(sbase + s * P_PLANE);
+        for (int g = 0; g < NGROUP; ++g) {
+          const MmaGroup G = mma_group(g);
+          const uint64_t ad = sdesc_sw128(sbase + G.s * P_PLANE);
+          const uint64_t bd = sdesc_sw128(sbase + ND * P_PLANE + G.t0 * Q_PLANE);
+          const uint32_t d = tmem + (uint32_t)((G.s + G.t0) * UBN);
+          const uint32_t idesc = idesc_bf16(UBM, UBN * G.nt);
 #pragma unroll
-          for (int t = 0; t < ND; ++t) {
-            if (s + t > WMAX) continue;
-            const uint64_t bd = sdesc_sw128(sbase + ND * P_PLANE + t * Q_PLANE);
-            const uint32_t d = tmem + (uint32_t)((s + t) * UBN);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {  // 32 bytes (16 BF16) along K per MMA
-              // the first product of weight w is pair (0, w) (or (w - 6, 6) past 6) at its first K step
-              const bool first = (s == (s + t > 6 ? s + t - 6 : 0)) && k == 0;
-              umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, first ? 0u : 1u);
-            }
-          }
+          for (int k = 0; k < 4; ++k)  // 32 bytes (16 BF16) along K per MMA
+            umma_f16(d, ad + 2 * k, bd + 2 * k, idesc, G.first && k == 0 ? 0u : 1u);
         }
         umma_commit(pfree);     // the planes may be overwritten once these MMAs are done
         umma_commit(mma_done);  // and the accumulators read
@@ -475,6 +507,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const bool prow = p < rows;
       const int ep = prow ? e[p] : 0;
       const int eq_lane = lane < EC && qb + lane < rows ? e[qb + lane] : 0;  // e_q of column qb + lane, by shuffles
+      // this thread's entries of C, loaded before the wait: the loads are in
+      // flight while the tile's MMAs run (C does not depend on them)
+      double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
+      double2 cv[EC / 2];
+#pragma unroll
+      for (int v = 0; v < EC / 2; ++v) {
+        const int64_t q = qb + 2 * v;
+        if (prow && q + 1 <= p)
+          cv[v] = *reinterpret_cast<const double2*>(crow + 2 * v);
+        else
+          cv[v] = make_double2(prow && q <= p ? crow[2 * v] : 0.0, 0.0);
+      }
       int ok = 1;
       if (lane == 0) ok = mbar_wait(mma_done, (uint32_t)it & 1u, abort_flag) && !*abort_flag;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -496,24 +540,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // while those MMAs run.
       long long Z[EC];
 #pragma unroll
-      for (int g = 0; g < EC / 4; ++g) {  // 4 columns at a time
-        uint32_t r[NW][4];
-        tmem_ld8x4(lane_addr + (uint32_t)(g * 4), UBN, r);
+      for (int g = 0; g < EC / 2; ++g) {  // 2 columns at a time
+        uint32_t r[NW][2];
+        tmem_ld8x2(lane_addr + (uint32_t)(g * 2), UBN, r);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 2; ++j) {
           int iw[NW];
 #pragma unroll
           for (int w = 0; w < NW; ++w) iw[w] = __float2int_rn(__uint_as_float(r[w][j]));
           const int t01 = iw[0] * 256 + iw[1], t23 = iw[2] * 256 + iw[3], t45 = iw[4] * 256 + iw[5];
           const int t67 = iw[6] * 256 + iw[7];
-          Z[g * 4 + j] = (long long)t01 * (1ll << 34) + (long long)t23 * (1ll << 18) + (long long)t45 * 4 +
+          Z[g * 2 + j] = (long long)t01 * (1ll << 34) + (long long)t23 * (1ll << 18) + (long long)t45 * 4 +
                          ((t67 + 8192) >> 14);
         }
       }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tfree);  // the accumulators may be overwritten
-      double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
 #pragma unroll
       for (int v = 0; v < EC / 2; ++v) {
         const int e0 = __shfl_sync(0xffffffffu, eq_lane, 2 * v), e1 = __shfl_sync(0xffffffffu, eq_lane, 2 * v + 1);
@@ -522,12 +565,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const double u0 = scaled_int_to_double(Z[2 * v], ep + e0 - 56);
           if (q + 1 <= p) {
             const double u1 = scaled_int_to_double(Z[2 * v + 1], ep + e1 - 56);
-            double2 cv = *reinterpret_cast<const double2*>(crow + 2 * v);
-            cv.x -= u0;
-            cv.y -= u1;
-            *reinterpret_cast<double2*>(crow + 2 * v) = cv;
+            cv[v].x -= u0;
+            cv[v].y -= u1;
+            *reinterpret_cast<double2*>(crow + 2 * v) = cv[v];
           } else {
-            crow[2 * v] -= u0;
+            crow[2 * v] = cv[v].x - u0;
           }
         }
       }

@@ -92,7 +92,6 @@ constexpr int STAGES = 3;
 constexpr uint32_t BUF_COLS = NWP * DBN;               // 256 TMEM columns per chunk buffer
 constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;           // 512
 constexpr int NUM_THREADS = 320;
-constexpr uint32_t kIdesc = idesc_bf16(DBM, DBN);
 
 // The digit pairs (s, t) of a pass: weights W0 .. W0 + 3, s < SA, t < SB.
 // Pass 0 (weights 0-3) has 10 pairs and reads A digits 0-3 and B digits 0-3;
@@ -107,7 +106,24 @@ struct DigPass {
   static constexpr uint32_t STAGE_BYTES = NA * A_PLANE + NB * B_PLANE;  // 48 KB or 72 KB
   static constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
   __host__ __device__ static constexpr bool kept(int s, int t) { return s + t >= W0 && s + t < W0 + NWP && s < NA && t < NB; }
+  // the B digits t paired with A digit s in this pass: first_t(s) .. last_t(s)
+  __host__ __device__ static constexpr int first_t(int s) { return W0 - s > 0 ? W0 - s : 0; }
+  __host__ __device__ static constexpr int last_t(int s) { return W0 + NWP - 1 - s < NB - 1 ? W0 + NWP - 1 - s : NB - 1; }
 };
+// first_t .. last_t is exactly the pairs kept, at most 4 of them (N <= 256),
+// and A digit 0 meets every weight of the pass
+template <int PASS>
+constexpr bool pass_groups_ok() {
+  using P = DigPass<PASS>;
+  if (P::first_t(0) != P::W0 || P::last_t(0) != P::W0 + NWP - 1) return false;
+  for (int s = 0; s < P::NA; ++s) {
+    if (P::last_t(s) - P::first_t(s) + 1 > 4) return false;
+    for (int t = 0; t < P::NB; ++t)
+      if (P::kept(s, t) != (t >= P::first_t(s) && t <= P::last_t(s))) return false;
+  }
+  return true;
+}
+static_assert(pass_groups_ok<0>() && pass_groups_ok<1>(), "one MMA per A digit covers the pass's pairs");
 static_assert(5 * DSK * CHUNK_STAGES * 16384 < (1 << 24), "exact chunk");
 static_assert(DigPass<0>::W0 + 2 * NWP - 1 == WMAX, "the two passes cover the weights 0..WMAX");
 static_assert(DigPass<1>::SMEM_BYTES <= 232448, "shared memory of one CTA");
@@ -215,18 +231,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const uint32_t dbuf = tmem + (uint32_t)buf * BUF_COLS;
 #pragma unroll
         for (int da = 0; da < P::NA; ++da) {
+          // the pairs (da, t) of the pass have consecutive t; their B planes
+          // lie one after another in the stage (64 rows each, the same 8-row
+          // group stride) and their weights' accumulators one after another
+          // in tensor memory, so one MMA with N = 64 x (pairs) covers them
+          const int t0 = P::first_t(da), t1 = P::last_t(da);
+          if (t1 < t0) continue;
           const uint64_t ad = sdesc_sw64(stage + da * A_PLANE);
+          const uint64_t bd = sdesc_sw64(stage + P::NA * A_PLANE + t0 * B_PLANE);
+          const uint32_t d = dbuf + (uint32_t)((da + t0 - P::W0) * DBN);
+          const uint32_t idesc = idesc_bf16(DBM, DBN * (t1 - t0 + 1));
 #pragma unroll
-          for (int dbg = 0; dbg < P::NB; ++dbg) {
-            if (!P::kept(da, dbg)) continue;
-            const uint64_t bd = sdesc_sw64(stage + P::NA * A_PLANE + dbg * B_PLANE);
-            const uint32_t d = dbuf + (uint32_t)((da + dbg - P::W0) * DBN);
-#pragma unroll
-            for (int k = 0; k < DSK / 16; ++k) {  // 32 bytes (16 BF16) along K per MMA
-              // the first product of a weight in a chunk is pair (0, w) at its first K step
-              const uint32_t accum = (chunk_start && da == 0 && k == 0) ? 0u : 1u;
-              umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, accum);
-            }
+          for (int k = 0; k < DSK / 16; ++k) {  // 32 bytes (16 BF16) along K per MMA
+            // the MMA of A digit 0 covers every weight of the pass: at the
+            // chunk's first K step it starts all of their accumulators
+            const uint32_t accum = (chunk_start && da == 0 && k == 0) ? 0u : 1u;
+            umma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
           }
         }
         umma_commit(empty(s));
