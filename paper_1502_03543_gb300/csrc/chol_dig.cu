@@ -183,68 +183,145 @@ __device__ __forceinline__ double inv_pivot(double d) {
 }
 
 // The FP64 factor of the kb x kb diagonal block of panel k0 (kb <= 64) by one
-// CTA, right-looking in the LDL' form.  Per column c, after a barrier:
-//   (a) t_i = M_ic / d_c for the rows i > c (one multiply each);
-//   (b) M_ij -= t_i M_jc over the trailing triangle c < j <= i < kb, its
-//       entries packed over all threads (entry e <-> (i, j) by a table);
-//       entry 0 is (c + 1, c + 1): thread 0 updates it first and forms
-//       1 / d_c+1 for the next column.
-// The square roots and the scaling L_ic = M_ic / sqrt(d_c) then run for all
-// columns at once.  Writes L_11 (lower triangle and diagonal) to M and
-// 1 / L_cc to dinv[k0 + c]; a pivot that is not positive and finite sets
-// PDAS_ERR_NOT_SPD with its index.
+// CTA, right-looking in the LDL' form (an identity past kb), one barrier per
+// column.  At step c the first warp (the "pivot warp", lane l holding rows l
+// and l + 32) finishes column c + 1: M_i,c+1 -= t_ic M_c+1,c for its rows,
+// the pivot d_c+1 (row c + 1), 1 / d_c+1, and t_i,c+1 = M_i,c+1 / d_c+1, and
+// posts t and M of column c + 1.  Meanwhile the "bulk" warps apply column c
+// to the columns past c + 1, M_ij -= t_ic M_jc, and post column c + 2.
+// GB300's FP64 pipe runs one warp instruction per ~64 cycles per SM
+// sub-partition, whatever the number of active lanes, so:
+//   - the bulk's entries are ordered by column from the last to the first
+//     (rows ascending inside a column) and dealt to its threads in turn,
+//     entry (i, j), i >= j, at e = P(j) + i - j, P(j) = (63 - j)(64 - j) / 2:
+//     the entries of the columns past c + 1 are the first P(c + 1), so every
+//     FP64 instruction has all lanes busy but the last, and column c + 2,
+//     posted next, comes last in the order (a thread updates its slots from
+//     the highest down);
+//   - the warps on the pivot warp's sub-partition take no bulk entries, so
+//     the dependent chain of the pivot (a multiply-add, the reciprocal, a
+//     multiply per column) never queues behind the bulk.
+// Each entry receives the same operations in the same order as in a sweep
+// over the trailing triangle.  The square roots and the scaling
+// L_ic = M_ic / sqrt(d_c) then run for all columns at once.  Writes L_11
+// (lower triangle and diagonal) to M and 1 / L_cc to dinv[k0 + c]; a pivot
+// that is not positive and finite sets PDAS_ERR_NOT_SPD with its index.
 constexpr int DG_THREADS = 256;
-constexpr int DG_TRI = (UK - 1) * UK / 2;  // entries of the largest trailing triangle
 struct DiagSmem {
-  double Ld[UK][UK + 1];
-  double tcol[UK];             // t_i of the current column
-  double s_rp[UK];
-  double s_inv;                // 1 / d_c of the next column; < 0: not positive definite
-  unsigned short tri[DG_TRI];  // e -> (r, s), e = r (r + 1) / 2 + s, s <= r: r << 8 | s
+  double Ld[UK][UK + 1];  // the block, staged (coalesced loads and stores); then M_ic of finished columns
+  double w[2][UK];        // column c + 2 from the bulk (alternating halves)
+  double t[2][UK];        // t_ic of column c (alternating halves)
+  double u[2][UK];        // M_ic of column c (alternating halves)
+  double dg[UK];          // the pivots d_c
+  double s_rp[UK];        // 1 / L_cc
+  int fail;               // first column whose pivot failed, or -1
 };
+__host__ __device__ constexpr int diag_col_start(int j) { return (UK - 1 - j) * (UK - j) / 2; }
 
-// The factor itself, by NT threads (tid) that meet at bar().
+// The factor itself, by NT threads (tid; warp w = tid / 32 runs on SM
+// sub-partition w mod 4 up to a common offset) that meet at bar().
 template <int NT, class Bar>
 __device__ __forceinline__ void diag_factor(int64_t ldm, double* __restrict__ M, double* __restrict__ dinv,
                                             int64_t k0, int kb, Scalars* sc, DiagSmem& S, int tid, Bar bar) {
+  constexpr int NBULK = NT / 4 * 3;                     // threads of the bulk warps
+  constexpr int NS = (diag_col_start(1) + NBULK - 1) / NBULK;  // slots: the columns past 1 at most
+  const int wq = tid >> 5, lane = tid & 31;
+  const bool pivot_warp = wq == 0, bulk = (wq & 3) != 0;
+  const int b = (wq - (wq >> 2) - 1) * 32 + lane;       // bulk index
   for (int t = tid; t < UK * UK; t += NT) {
     const int i = t / UK, j = t % UK;
-    if (j <= i && i < kb) S.Ld[i][j] = M[(k0 + i) * ldm + k0 + j];
+    if (j <= i) S.Ld[i][j] = i < kb ? M[(k0 + i) * ldm + k0 + j] : (i == j ? 1.0 : 0.0);
   }
-  for (int e = tid; e < DG_TRI; e += NT) {
-    int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
-    while (r * (r + 1) / 2 > e) --r;
-    while ((r + 1) * (r + 2) / 2 <= e) ++r;
-    S.tri[e] = (unsigned short)((r << 8) | (e - r * (r + 1) / 2));
+  if (tid == 0) S.fail = -1;
+  bar();
+  double v[NS];
+  int ij[NS];  // i << 8 | j of the slot's entry
+  if (bulk) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int e = b + s * NBULK;
+      int i = UK - 1, j = UK - 1;  // (a slot past the columns it serves: never updated, never posted)
+      if (e < diag_col_start(1)) {
+        int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
+        while (r * (r + 1) / 2 > e) --r;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        j = UK - 1 - r;  // diag_col_start(j) = r (r + 1) / 2
+        i = j + (e - r * (r + 1) / 2);
+      }
+      ij[s] = (i << 8) | j;
+      v[s] = S.Ld[i][j];
+    }
+  }
+  if (tid < UK) S.w[1][tid] = S.Ld[tid][1];  // column 1 before any update
+  // pivot warp: column 0 (t and M of its rows lane, lane + 32 in registers)
+  double t0 = 0.0, t1 = 0.0, u0 = 0.0, u1 = 0.0;
+  if (pivot_warp) {
+    u0 = S.Ld[lane][0];
+    u1 = S.Ld[lane + 32][0];
+    const double d = S.Ld[0][0], inv = inv_pivot(d);
+    t0 = u0 * inv;
+    t1 = u1 * inv;
+    S.t[0][lane] = t0;
+    S.t[0][lane + 32] = t1;
+    S.u[0][lane] = u0;
+    S.u[0][lane + 32] = u1;
+    if (lane == 0) {
+      S.dg[0] = d;
+      if (inv < 0.0) S.fail = 0;
+    }
   }
   bar();
-  if (tid == 0) S.s_inv = inv_pivot(S.Ld[0][0]);
-  int fail = -1;
-  for (int c = 0; c < kb; ++c) {
-    bar();  // the update for column c - 1 is complete and 1 / d_c posted
-    const double inv = S.s_inv;
-    if (inv < 0.0) {
-      fail = c;
-      break;
+  int fail = S.fail;
+  for (int c = 0; c + 1 < kb && fail < 0; ++c) {
+    if (pivot_warp) {
+      const double* wb = S.w[(c + 1) & 1];
+      const double w0 = wb[lane], w1 = wb[lane + 32];
+      const int pr = (c + 1) & 31;
+      const bool hi = c + 1 >= 32;
+      const double up = __shfl_sync(0xffffffffu, hi ? u1 : u0, pr);  // M_c+1,c
+      const double n0 = fma(-t0, up, w0), n1 = fma(-t1, up, w1);     // M_i,c+1
+      const double d = __shfl_sync(0xffffffffu, hi ? n1 : n0, pr);   // d_c+1
+      const double inv = inv_pivot(d);
+      t0 = n0 * inv;
+      t1 = n1 * inv;
+      u0 = n0;
+      u1 = n1;
+      double* tb = S.t[(c + 1) & 1];
+      double* ub = S.u[(c + 1) & 1];
+      tb[lane] = t0;
+      tb[lane + 32] = t1;
+      ub[lane] = u0;
+      ub[lane + 32] = u1;
+      if (lane > c + 1) S.Ld[lane][c + 1] = u0;
+      if (lane + 32 > c + 1) S.Ld[lane + 32][c + 1] = u1;
+      if (lane == 0) {
+        S.dg[c + 1] = d;
+        if (inv < 0.0) S.fail = c + 1;
+      }
+    } else if (bulk) {
+      const double* tc = S.t[c & 1];
+      const double* uc = S.u[c & 1];
+      double* wn = S.w[c & 1];  // column c + 2 (buffer (c + 2) & 1)
+      const int ne = diag_col_start(c + 1), ne2 = diag_col_start(c + 2);
+#pragma unroll
+      for (int s = NS - 1; s >= 0; --s) {
+        const int e = b + s * NBULK;
+        if (e < ne) {
+          const int i = ij[s] >> 8, j = ij[s] & 0xff;
+          v[s] = fma(-tc[i], uc[j], v[s]);
+          if (e >= ne2) wn[i] = v[s];  // column c + 2, all of its updates up to column c applied
+        }
+      }
     }
-    const int rest = kb - 1 - c;
-    if (tid < rest) S.tcol[c + 1 + tid] = S.Ld[c + 1 + tid][c] * inv;
     bar();
-    const int ne = rest * (rest + 1) / 2;
-    for (int e = tid; e < ne; e += NT) {
-      const int rs = S.tri[e], i = c + 1 + (rs >> 8), j = c + 1 + (rs & 0xff);
-      const double v = fma(-S.tcol[i], S.Ld[j][c], S.Ld[i][j]);
-      S.Ld[i][j] = v;
-      if (e == 0) S.s_inv = inv_pivot(v);  // thread 0: d_c+1 is final
-    }
+    fail = S.fail;
   }
-  if (fail >= 0) {  // every thread read the same pivot
+  if (fail >= 0) {  // every thread read the same index
     if (tid == 0 && atomicCAS(&sc->status, 0, (int)PDAS_ERR_NOT_SPD) == 0) sc->fail_index = (int)(k0 + fail);
     return;
   }
-  bar();
   if (tid < kb) {
-    const double l = sqrt(S.Ld[tid][tid]);
+    const double l = sqrt(S.dg[tid]);
     S.Ld[tid][tid] = l;
     S.s_rp[tid] = 1.0 / l;
     dinv[k0 + tid] = S.s_rp[tid];
