@@ -19,7 +19,7 @@
 //                                      the row's largest |P_rc|:
 //                                      P_rc = 2^e_r sum_s d_s 2^(-7-8s);
 //   k_dig_update                    -- C_pq -= (P P')_pq over the lower tiles
-//                                      (128 rows p x 64 columns q) of the
+//                                      (128 rows p x 32 columns q) of the
 //                                      trailing matrix:
 //        (P P')_pq = 2^(e_p + e_q - 14) sum_{w<=7} 2^(-8w) I_w,
 //        I_w = sum_c sum_{s+t=w} d_s,pc d_t,qc,
@@ -72,7 +72,7 @@ namespace {
 using namespace tc;
 
 constexpr int UBM = 128;                          // rows p of a tile
-constexpr int UBN = 64;                           // rows q (columns of C) of a tile
+constexpr int UBN = 32;                           // rows q (columns of C) of a tile
 constexpr int UK = 64;                            // panel width (columns of P): one 128-byte row
 constexpr int ND = 7;                             // digits per entry (55 bits)
 constexpr int WMAX = 7;                           // largest pair weight kept
@@ -80,29 +80,36 @@ constexpr int NW = WMAX + 1;
 constexpr int NPAIR = 34;                         // pairs (s, t), s, t < 7, s + t <= 7
 static_assert(NPAIR == 7 + 7 + 6 + 5 + 4 + 3 + 2, "pair count");
 constexpr uint32_t P_PLANE = UBM * 128;           // 16 KB: 128 rows of one digit
-constexpr uint32_t Q_PLANE = UBN * 128;           // 8 KB: 64 rows of one digit
-constexpr uint32_t LOAD_BYTES = ND * (P_PLANE + Q_PLANE);  // 168 KB
-constexpr uint32_t TMEM_COLS = NW * UBN;          // 512
+constexpr uint32_t Q_PLANE = UBN * 128;           // 4 KB: 32 rows of one digit
+constexpr uint32_t P_BYTES = ND * P_PLANE;        // 112 KB: the P planes of a row block of tiles
+constexpr uint32_t Q_BYTES = ND * Q_PLANE;        // 28 KB: the Q planes of a tile (two buffers)
+constexpr uint32_t LOAD_BYTES = P_BYTES + 2 * Q_BYTES;  // 168 KB
+constexpr uint32_t BUF_COLS = NW * UBN;           // 256: the 8 weight accumulators of a tile
+constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;      // 512: two tiles in flight
 constexpr int NUM_THREADS = 576;                  // 2 role warps + 16 epilogue warps
 constexpr int EPI_WARPS = NUM_THREADS / 32 - 2;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)LOAD_BYTES + 256;
+// Per epilogue warp, a 32-row staging area for the scaled updates (8 columns,
+// pitch 9 doubles): C is read and written in a coalesced layout while the
+// updates are formed with one tile row per lane (the tensor-memory layout).
+constexpr int STG_PITCH = 9;
+constexpr size_t STG_BYTES = (size_t)(NUM_THREADS / 32 - 2) * 32 * STG_PITCH * sizeof(double);
+constexpr size_t SMEM_BYTES = 1024 + (size_t)LOAD_BYTES + 256 + STG_BYTES;
 
 // The pairs (s, t) with a fixed s have consecutive t; the Q planes t lie one
-// after another in shared memory (64 rows each, the same 8-row group stride)
+// after another in shared memory (32 rows each, the same 8-row group stride)
 // and the accumulators of the weights s + t one after another in tensor
-// memory, so one MMA with N = 64 x (pairs) covers up to 4 of them.  A group
-// starts its weights' accumulators (no accumulation at its first K step)
-// when it holds the first product of each of them: pair (0, w), or (1, 6)
-// for w = 7, which therefore gets a group of its own.
+// memory, so one MMA with N = 32 x (pairs) covers them.  A group starts its
+// weights' accumulators (no accumulation at its first K step) when it holds
+// the first product of each of them: pair (0, w), or (1, 6) for w = 7, which
+// therefore gets a group of its own.
 struct MmaGroup {
   int s, t0, nt;
   bool first;
 };
-constexpr int NGROUP = 12;
+constexpr int NGROUP = 8;
 __host__ __device__ constexpr MmaGroup mma_group(int g) {
-  constexpr MmaGroup G[NGROUP] = {{0, 0, 4, true},  {0, 4, 3, true},  {1, 0, 4, false}, {1, 4, 2, false},
-                                  {1, 6, 1, true},  {2, 0, 4, false}, {2, 4, 2, false}, {3, 0, 4, false},
-                                  {3, 4, 1, false}, {4, 0, 4, false}, {5, 0, 3, false}, {6, 0, 2, false}};
+  constexpr MmaGroup G[NGROUP] = {{0, 0, 7, true},  {1, 0, 6, false}, {1, 6, 1, true},  {2, 0, 6, false},
+                                  {3, 0, 5, false}, {4, 0, 4, false}, {5, 0, 3, false}, {6, 0, 2, false}};
   return G[g];
 }
 // the groups cover each pair (s, t), s + t <= WMAX, once; a group's first
@@ -113,7 +120,7 @@ constexpr bool groups_ok() {
   int pairs = 0;
   for (int g = 0; g < NGROUP; ++g) {
     const MmaGroup G = mma_group(g);
-    if (G.nt < 1 || G.nt > 4 || G.t0 + G.nt > ND) return false;
+    if (G.nt < 1 || UBN * G.nt > 256 || G.t0 + G.nt > ND) return false;
     for (int t = G.t0; t < G.t0 + G.nt; ++t) {
       if (G.s + t > WMAX || seen[G.s][t]++) return false;
       if (started[G.s + t] == G.first) return false;
@@ -469,23 +476,24 @@ __device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t w_stride, ui
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Tile b of the update: (I, J) with J <= 2 I + 1 (row block I has 2 I + 2
-// tiles, the first I (I + 1) tiles precede it); false when the tile lies
+// Tile b of the update: (I, J) with J <= 4 I + 3 (row block I has 4 I + 4
+// tiles, the first 2 I (I + 1) tiles precede it); false when the tile lies
 // outside the trailing matrix.
 __device__ __forceinline__ bool update_tile(int64_t b, int64_t rows, int64_t& p0, int64_t& q0) {
-  int64_t I = (int64_t)((sqrtf(4.0f * (float)b + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
-  while (I * (I + 1) > b) --I;
-  while ((I + 1) * (I + 2) <= b) ++I;
+  int64_t I = (int64_t)((sqrtf(2.0f * (float)b + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
+  while (2 * I * (I + 1) > b) --I;
+  while (2 * (I + 1) * (I + 2) <= b) ++I;
   p0 = I * UBM;
-  q0 = (b - I * (I + 1)) * UBN;
+  q0 = (b - 2 * I * (I + 1)) * UBN;
   return q0 < rows && q0 <= p0 + UBM - 1;
 }
 
 // C_pq -= (P P')_pq for the lower tiles of the trailing matrix (rows and
-// columns base + [0, rows)).  Persistent: CTA x takes tiles x, x + grid, ...
-// in order, and the stages of consecutive tiles overlap -- the copy of the
-// next tile's planes lands while this tile's epilogue runs, and the next
-// tile's MMAs start as soon as the epilogue has read the accumulators.
+// columns base + [0, rows)).  Persistent: CTA x takes a contiguous range of
+// tiles, so consecutive tiles share their row block and its P planes (copied
+// once per row block).  Two tiles are in flight: the Q planes and the
+// accumulators are double-buffered, so the MMAs of tile i + 1 run while the
+// epilogue reads and writes back tile i.
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_dig_update(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int64_t ldm,
                  double* __restrict__ M, int64_t base, int64_t rows, int64_t ntiles, const int* __restrict__ e,
@@ -494,18 +502,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (*(volatile const int*)&sc->status != 0) return;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LOAD_BYTES);  // full | free | mma done | tmem free | drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
+  // barriers: P full | P free | Q full[2] | Q free[2] | MMA done[2] | TMEM free[2] | drain
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LOAD_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* diag_go = reinterpret_cast<volatile int*>(tmem_slot + 2);
-  const uint32_t full = smem_u32(bars), pfree = smem_u32(bars + 1), mma_done = smem_u32(bars + 2),
-                 tfree = smem_u32(bars + 3), drain = smem_u32(bars + 4);
+  double* stage_all = reinterpret_cast<double*>(smem + LOAD_BYTES + 256);
+  const uint32_t pfull = smem_u32(bars), pfree = smem_u32(bars + 1), drain = smem_u32(bars + 10);
+  auto qfull = [&](int b) { return smem_u32(bars + 2 + b); };
+  auto qfree = [&](int b) { return smem_u32(bars + 4 + b); };
+  auto mma_done = [&](int b) { return smem_u32(bars + 6 + b); };
+  auto tfree = [&](int b) { return smem_u32(bars + 8 + b); };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
+    mbar_init(pfull, 1);
     mbar_init(pfree, 1);
-    mbar_init(mma_done, 1);
-    mbar_init(tfree, EPI_WARPS);  // one arrival per epilogue warp
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(qfull(b), 1);
+      mbar_init(qfree(b), 1);
+      mbar_init(mma_done(b), 1);
+      mbar_init(tfree(b), EPI_WARPS);  // one arrival per epilogue warp
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -517,87 +534,126 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   fence_after();
   const uint32_t tmem = *tmem_slot;
   int64_t p0, q0;
-  // with the next panel's diagonal block folded in (kbn > 0), CTA 0 takes
-  // tile 0 alone (the tile that holds that block) and factors the block
-  // once the tile is written; the other CTAs share the rest of the tiles
+  // this CTA's tiles [tb, te).  With the next panel's diagonal block folded
+  // in (kbn > 0), CTA 0 takes tiles 0 and 1 alone (rows 0..127, columns
+  // 0..63: they hold that block) and factors the block once they are
+  // written; the other CTAs share the rest in equal contiguous ranges.
   const bool fold = kbn > 0;
-  const int64_t b_step = !fold ? (int64_t)gridDim.x : (blockIdx.x == 0 ? ntiles : (int64_t)gridDim.x - 1);
+  int64_t tb, te;
+  if (fold && gridDim.x > 1) {
+    const int64_t head = ntiles < 2 ? ntiles : 2, rest = ntiles - head, g = gridDim.x - 1;
+    tb = blockIdx.x == 0 ? 0 : head + rest * (blockIdx.x - 1) / g;
+    te = blockIdx.x == 0 ? head : head + rest * blockIdx.x / g;
+  } else {
+    tb = ntiles * blockIdx.x / gridDim.x;
+    te = ntiles * (blockIdx.x + 1) / gridDim.x;
+  }
 
   if (warp == 0) {
     if (lane == 0) {
-      int it = 0;
-      for (int64_t b = blockIdx.x; b < ntiles; b += b_step) {
+      int i = 0, pl = 0;  // tiles and P copies issued
+      int64_t cur = -1;   // row block of the P planes in shared memory
+      for (int64_t b = tb; b < te; ++b) {
         if (!update_tile(b, rows, p0, q0)) continue;
-        if (it > 0 && !mbar_wait(pfree, (uint32_t)(it - 1) & 1u, abort_flag)) {
+        if (p0 != cur) {  // a new row block: its P planes, once the last one's MMAs are done
+          if (pl > 0 && !mbar_wait(pfree, (uint32_t)(pl - 1) & 1u, abort_flag)) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(pfull, P_BYTES);
+          tma_load_3d(sbase, &tmP, 0, (int)p0, 0, pfull);
+          cur = p0;
+          ++pl;
+        }
+        const int bf = i & 1;
+        if (i >= 2 && !mbar_wait(qfree(bf), (uint32_t)((i >> 1) - 1) & 1u, abort_flag)) {
           *abort_flag = 1;
           break;
         }
-        mbar_expect_tx(full, LOAD_BYTES);
-        tma_load_3d(sbase, &tmP, 0, (int)p0, 0, full);
-        tma_load_3d(sbase + ND * P_PLANE, &tmQ, 0, (int)q0, 0, full);
-        ++it;
+        mbar_expect_tx(qfull(bf), Q_BYTES);
+        tma_load_3d(sbase + P_BYTES + (uint32_t)bf * Q_BYTES, &tmQ, 0, (int)q0, 0, qfull(bf));
+        ++i;
       }
-      if (it > 0) mbar_wait(full, (uint32_t)(it - 1) & 1u, nullptr);  // the last copy has landed
+      // every issued copy has landed before the CTA can leave
+      if (pl > 0) mbar_wait(pfull, (uint32_t)(pl - 1) & 1u, nullptr);
+      for (int k = i > 2 ? i - 2 : 0; k < i; ++k) mbar_wait(qfull(k & 1), (uint32_t)(k >> 1) & 1u, nullptr);
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      int it = 0;
-      for (int64_t b = blockIdx.x; b < ntiles && !*abort_flag; b += b_step) {
+      int i = 0, pl = 0;
+      int64_t cur = -1;
+      for (int64_t b = tb; b < te && !*abort_flag; ++b) {
         if (!update_tile(b, rows, p0, q0)) continue;
-        if (!mbar_wait(full, (uint32_t)it & 1u, abort_flag) ||
-            (it > 0 && !mbar_wait(tfree, (uint32_t)(it - 1) & 1u, abort_flag))) {
+        const int bf = i & 1;
+        if (p0 != cur) {
+          if (cur >= 0) umma_commit(pfree);  // the last row block's MMAs: its P planes may be overwritten
+          if (!mbar_wait(pfull, (uint32_t)pl & 1u, abort_flag)) {
+            *abort_flag = 1;
+            break;
+          }
+          cur = p0;
+          ++pl;
+        }
+        if (!mbar_wait(qfull(bf), (uint32_t)(i >> 1) & 1u, abort_flag) ||
+            (i >= 2 && !mbar_wait(tfree(bf), (uint32_t)((i >> 1) - 1) & 1u, abort_flag))) {
           *abort_flag = 1;
           break;
         }
         fence_after();
+        const uint32_t qb = sbase + P_BYTES + (uint32_t)bf * Q_BYTES;
+        const uint32_t dbuf = tmem + (uint32_t)bf * BUF_COLS;
 #pragma unroll
         for (int g = 0; g < NGROUP; ++g) {
           const MmaGroup G = mma_group(g);
           const uint64_t ad = sdesc_sw128(sbase + G.s * P_PLANE);
-          const uint64_t bd = sdesc_sw128(sbase + ND * P_PLANE + G.t0 * Q_PLANE);
-          const uint32_t d = tmem + (uint32_t)((G.s + G.t0) * UBN);
+          const uint64_t bd = sdesc_sw128(qb + G.t0 * Q_PLANE);
+          const uint32_t d = dbuf + (uint32_t)((G.s + G.t0) * UBN);
           const uint32_t idesc = idesc_bf16(UBM, UBN * G.nt);
 #pragma unroll
           for (int k = 0; k < 4; ++k)  // 32 bytes (16 BF16) along K per MMA
             umma_f16(d, ad + 2 * k, bd + 2 * k, idesc, G.first && k == 0 ? 0u : 1u);
         }
-        umma_commit(pfree);     // the planes may be overwritten once these MMAs are done
-        umma_commit(mma_done);  // and the accumulators read
-        ++it;
+        umma_commit(qfree(bf));     // the Q planes may be overwritten once these MMAs are done
+        umma_commit(mma_done(bf));  // and the accumulators read
+        ++i;
       }
       umma_commit(drain);  // every MMA issued above has completed before the CTA leaves
       mbar_wait(drain, 0, nullptr);
     }
     __syncwarp();
   } else {
-    constexpr int EC = UBN / (EPI_WARPS / 4);  // columns per epilogue thread: 16
+    constexpr int EC = UBN / (EPI_WARPS / 4);  // columns per epilogue warp: 8
+    static_assert(EC == 8, "one staging round of 8 columns per tile");
     const int quarter = warp & 3, cg = (warp - 2) >> 2;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cg * EC);
-    int it = 0;
-    for (int64_t b = blockIdx.x; b < ntiles; b += b_step) {
+    double* stg = stage_all + (warp - 2) * 32 * STG_PITCH;
+    int i = 0;
+    for (int64_t b = tb; b < te; ++b) {
       if (!update_tile(b, rows, p0, q0)) continue;
-      // this thread's entries: row p (its tensor-memory lane), columns q0 + 16 cg + [0, 16),
-      // those with q <= p inside the trailing matrix
-      const int64_t p = p0 + quarter * 32 + lane;
+      const int bf = i & 1;
+      // this warp's block: rows p0 + 32 quarter + [0, 32) (row p = lane in
+      // tensor memory), columns qb + [0, 8), those with q <= p inside the
+      // trailing matrix
+      const int64_t rw = p0 + quarter * 32;
+      const int64_t p = rw + lane;
       const int64_t qb = q0 + cg * EC;
       const bool prow = p < rows;
       const int ep = prow ? e[p] : 0;
       const int eq_lane = lane < EC && qb + lane < rows ? e[qb + lane] : 0;  // e_q of column qb + lane, by shuffles
-      // this thread's entries of C, loaded before the wait: the loads are in
-      // flight while the tile's MMAs run (C does not depend on them)
-      double* crow = M + (prow ? (base + p) * ldm + base + qb : 0);
-      double2 cv[EC / 2];
+      // C is read and written in a coalesced layout: lane l takes column
+      // qb + (l & 7) of rows rw + (l >> 3) + 4 k, k < 8 (four 64-byte row
+      // segments per access).  The loads are issued before the wait, so they
+      // are in flight while the tile's MMAs run (C does not depend on them).
+      const int cl = lane & 7, rl = lane >> 3;
+      double cc[8];
 #pragma unroll
-      for (int v = 0; v < EC / 2; ++v) {
-        const int64_t q = qb + 2 * v;
-        if (prow && q + 1 <= p)
-          cv[v] = *reinterpret_cast<const double2*>(crow + 2 * v);
-        else
-          cv[v] = make_double2(prow && q <= p ? crow[2 * v] : 0.0, 0.0);
+      for (int k = 0; k < 8; ++k) {
+        const int64_t r = rw + rl + 4 * k, q = qb + cl;
+        cc[k] = (r < rows && q <= r) ? M[(base + r) * ldm + base + q] : 0.0;
       }
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(mma_done, (uint32_t)it & 1u, abort_flag) && !*abort_flag;
+      if (lane == 0) ok = mbar_wait(mma_done(bf), (uint32_t)(i >> 1) & 1u, abort_flag) && !*abort_flag;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) {
         if (lane == 0) *abort_flag = 1;
@@ -611,15 +667,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       //   t_ab = I_a 2^8 + I_b, exact in int32 (|I_w| <= 7 2^20)
       // (|I_0| <= 2^20: |Z| < 2^63; the rounding is 2^-43 of
       // sum_w 2^-8w I_w, below the digits' own truncation).  All of the
-      // tile's accumulators are read first, so the next tile's MMAs can
+      // tile's accumulators are read first, so the MMAs of tile i + 2 can
       // start; Z 2^(e_p + e_q - 56) is then built as a double on the integer
-      // pipes and subtracted from C (the one FP64 operation of an entry)
-      // while those MMAs run.
+      // pipes and subtracted from C (the one FP64 operation of an entry).
       long long Z[EC];
 #pragma unroll
       for (int g = 0; g < EC / 2; ++g) {  // 2 columns at a time
         uint32_t r[NW][2];
-        tmem_ld8x2(lane_addr + (uint32_t)(g * 2), UBN, r);
+        tmem_ld8x2(lane_addr + (uint32_t)bf * BUF_COLS + (uint32_t)(g * 2), UBN, r);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           int iw[NW];
@@ -633,30 +688,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tfree);  // the accumulators may be overwritten
+      if (lane == 0) mbar_arrive(tfree(bf));  // the accumulators may be overwritten
+      // the updates of row p (this lane) go through the warp's staging area
 #pragma unroll
-      for (int v = 0; v < EC / 2; ++v) {
-        const int e0 = __shfl_sync(0xffffffffu, eq_lane, 2 * v), e1 = __shfl_sync(0xffffffffu, eq_lane, 2 * v + 1);
-        const int64_t q = qb + 2 * v;
-        if (prow && q <= p) {
-          const double u0 = scaled_int_to_double(Z[2 * v], ep + e0 - 56);
-          if (q + 1 <= p) {
-            const double u1 = scaled_int_to_double(Z[2 * v + 1], ep + e1 - 56);
-            cv[v].x -= u0;
-            cv[v].y -= u1;
-            *reinterpret_cast<double2*>(crow + 2 * v) = cv[v];
-          } else {
-            crow[2 * v] = cv[v].x - u0;
-          }
-        }
+      for (int c = 0; c < EC; ++c) {
+        const int eqc = __shfl_sync(0xffffffffu, eq_lane, c);
+        stg[lane * STG_PITCH + c] = (prow && qb + c <= p) ? scaled_int_to_double(Z[c], ep + eqc - 56) : 0.0;
       }
-      ++it;
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t r = rw + rl + 4 * k, q = qb + cl;
+        if (r < rows && q <= r) M[(base + r) * ldm + base + q] = cc[k] - stg[(rl + 4 * k) * STG_PITCH + cl];
+      }
+      __syncwarp();
+      ++i;
     }
     if (fold && blockIdx.x == 0) {
-      // tile 0 is written (the barrier orders every epilogue thread's stores
-      // before the reads below) and its MMAs are done, so the plane buffer is
-      // free: the epilogue warps factor the next panel's diagonal block there,
-      // if no wait of this CTA gave up (one thread decides, all follow)
+      // tiles 0 and 1 are written (the barrier orders every epilogue
+      // thread's stores before the reads below) and their MMAs are done, so
+      // the plane buffer is free: the epilogue warps factor the next panel's
+      // diagonal block there, if no wait of this CTA gave up (one thread
+      // decides, all follow)
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       if (threadIdx.x == 64) *diag_go = !*abort_flag;
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
@@ -776,7 +829,7 @@ cudaError_t cholesky_dig(cudaStream_t st, CholDigWorkspace* w, int64_t ldm, doub
         k_dig_panel_rows<32><<<(unsigned)((rows + 3) / 4), PR_THREADS, 0, st>>>(ldm, M, dinv, k0, kb, rows, w->mpad,
                                                                                 w->e, planes, sc);
     }
-    const int64_t nI = (rows + UBM - 1) / UBM, ntiles = nI * (nI + 1);
+    const int64_t nI = (rows + UBM - 1) / UBM, ntiles = 2 * nI * (nI + 1);
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, w->sub_partitions / 4);
     const int kbn = (int)std::min<int64_t>(UK, rows);  // the next panel's width: its diagonal block is folded in
     k_dig_update<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(hs->mapP, hs->mapQ, ldm, M, k0 + kb, rows, ntiles, w->e,
