@@ -677,9 +677,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tmem_ld8x2(lane_addr + (uint32_t)bf * BUF_COLS + (uint32_t)(g * 2), UBN, r);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
+          // weights 0..3 collect at most 4 pairs: |I_w| <= 2^22, so the FP32
+          // sum I_w + 1.5 2^23 is exact and its bits minus those of 1.5 2^23
+          // are I_w (an add on the FMA pipe); weights 4..7 through the
+          // conversion pipe
           int iw[NW];
 #pragma unroll
-          for (int w = 0; w < NW; ++w) iw[w] = __float2int_rn(__uint_as_float(r[w][j]));
+          for (int w = 0; w < NW; ++w)
+            iw[w] = w < 4 ? __float_as_int(__uint_as_float(r[w][j]) + 12582912.0f) - 0x4B400000
+                          : __float2int_rn(__uint_as_float(r[w][j]));
           const int t01 = iw[0] * 256 + iw[1], t23 = iw[2] * 256 + iw[3], t45 = iw[4] * 256 + iw[5];
           const int t67 = iw[6] * 256 + iw[7];
           Z[g * 2 + j] = (long long)t01 * (1ll << 34) + (long long)t23 * (1ll << 18) + (long long)t45 * 4 +
