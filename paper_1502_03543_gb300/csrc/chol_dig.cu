@@ -8,8 +8,9 @@
 //                                      launch of its own for the first panel;
 //                                      for the others CTA 0 of the previous
 //                                      panel's update factors the block right
-//                                      after writing tile 0, which holds it,
-//                                      while the other CTAs update the rest;
+//                                      after writing tiles 0 and 1, which
+//                                      hold it, while the other CTAs update
+//                                      the rest;
 //   k_dig_panel_rows                -- the panel rows P (trailing rows
 //                                      r >= k0 + kb, the kb panel columns)
 //                                      solved in FP64, P L_11' = B, 32 rows
@@ -36,23 +37,23 @@
 // the subtraction: FP64-grade, where the FP64 pipes would take 1/64 of the
 // FP32 rate.
 //
-// k_dig_update: persistent, one CTA per SM over the 128 x 64 tiles, 18 warps:
-//   warp 0      per tile one TMA load of the 7 planes for rows p (128 x 64
-//               columns) and the 7 planes for rows q (64 x 64 columns),
-//               168 KB, as soon as the previous tile's MMAs are done;
-//   warp 1      allocates 512 TMEM columns (8 weights x 64); one lane issues
-//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=64, K=16), 34
-//               pairs x 4 K steps, pair (s, t) into weight s + t, as soon as
-//               the planes have landed and the previous tile's accumulators
-//               have been read;
+// k_dig_update: persistent, one CTA per SM over a contiguous range of the
+// 128 x 32 tiles, 18 warps, two tiles in flight:
+//   warp 0      TMA: the 7 planes of the tile's rows p (128 x 64 columns,
+//               112 KB) once per row block, and per tile the 7 planes of its
+//               rows q (32 x 64 columns, 28 KB) into one of two buffers;
+//   warp 1      allocates 512 TMEM columns (2 buffers x 8 weights x 32); one
+//               lane issues tcgen05.mma.cta_group::1.kind::f16 (M = 128,
+//               N = 32 x pairs, K = 16): 8 groups of the 34 digit pairs x 4
+//               K steps, pair (s, t) into weight s + t, as soon as the tile's
+//               planes have landed and the epilogue has read the buffer's
+//               previous tile;
 //   warps 2..17 thread (warp w, lane) owns row 32 (w % 4) + lane of the tile
-//               and columns 16 ((w - 2) / 4).. of it: it reads its TMEM lane
-//               of every weight and combines the weights into one integer
-//               per entry; once all of them have read, the next tile's MMAs
-//               may start, and the thread subtracts the scaled update from
-//               C in place (16-byte accesses).  The epilogue is the longest
-//               stage of a tile (integer work per entry and C's latency), so
-//               it has 16 warps to hide that latency.
+//               and columns 8 ((w - 2) / 4).. of it: it reads its TMEM lane
+//               of every weight, combines the weights into one integer per
+//               entry and releases the buffer; the scaled updates then go
+//               through a per-warp staging area, and C is read (before the
+//               MMA wait) and written back in a coalesced layout.
 // Every mbarrier wait is bounded (2 s); on a timeout the CTA sets
 // PDAS_ERR_TIMEOUT, lets its copy land and its MMAs finish, frees TMEM, exits.
 #include <cuda.h>
