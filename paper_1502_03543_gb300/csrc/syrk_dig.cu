@@ -29,7 +29,7 @@
 // rounding of an entry besides the digits' own truncation.
 //
 // The tensor cores read both operands of every MMA from shared memory, and
-// that operand traffic bounds the kernel (the tc pipe, not the math, was
+// that operand traffic bounded the kernel (the tc pipe, not the math, was
 // 89 % busy at N = 32).  The tiles are therefore 128 rows p x 64 rows q, and
 // the product runs in two passes so that one pass's weights fit tensor
 // memory twice (2 chunk buffers x 4 weights x 64 columns = 512 columns) and
@@ -43,9 +43,13 @@
 //               planes (64 rows), 64-byte swizzle, 48 KB or 72 KB, into a
 //               ring of 3 stages;
 //   warp 1      allocates 512 TMEM columns; one lane issues
-//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=64, K=16), 2 per
-//               pair per stage, pair (s, t) into the accumulator of weight
-//               s + t of the current chunk buffer;
+//               tcgen05.mma.cta_group::1.kind::f16 (M = 128, K = 16), 2 per
+//               A digit per stage: the pairs (s, t) of A digit s in the pass
+//               have consecutive t, so one MMA with N = 64 x (pairs) reads
+//               the A plane once for all of them and writes the
+//               accumulators of weights s + t, which lie one after another
+//               in the current chunk buffer (4 or 5 MMAs per K step instead
+//               of 10 or 20);
 //   warps 2..9  warp w reads TMEM lanes 32 (w % 4).. and columns
 //               32 ((w - 2) / 4).. of every weight: per chunk 4 x 32 values,
 //               converted and added into int64 sums; then the buffer is
