@@ -432,8 +432,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_dig_panel_rows(int64_t ldm, doub
     balanced_digits(__double2ll_rn(v1 * sc), d1);
 #pragma unroll
     for (int s = 0; s < ND; ++s) {
-      const uint32_t pair = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d0[s])) |
-                            ((uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d1[s])) << 16);
+      const uint32_t pair = bf16_bits_small(d0[s]) | (bf16_bits_small(d1[s]) << 16);
       reinterpret_cast<uint32_t*>(planes + ((int64_t)s * mpad + i) * UK)[lane] = pair;
     }
   }

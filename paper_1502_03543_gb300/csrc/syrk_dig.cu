@@ -359,17 +359,32 @@ __global__ void k_dig_rowexp(int64_t m, int64_t n, const __nv_bfloat16* __restri
     const uint16_t* row = Ab + p * n;
     unsigned amag = 0;   // largest |A_pj| as BF16 magnitude bits (ordered like the values)
     int ebm = INT_MIN;   // largest frexp exponent of A_pj D_j
-    for (int64_t i = lane; i < k; i += 32) {
-      const int64_t j = idx ? idx[i] : i;
-      const uint16_t h = row[j];
-      const unsigned mag = h & 0x7fffu;
-      if (mag == 0) continue;
-      amag = max(amag, mag);
-      unsigned long long sa, sd;
-      int e_a, e_d;
-      bf16_fields(h, sa, e_a);
-      f64_fields(__ldg(Db + j), sd, e_d);
-      ebm = max(ebm, frexp_exp(sa * sd, e_a + e_d));
+    constexpr int U = 8;  // gathers in flight per lane
+    for (int64_t i0 = lane; i0 < k; i0 += 32 * U) {
+      int64_t j[U];
+      uint16_t h[U];
+      unsigned long long dbits[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + 32 * u;
+        j[u] = i < k ? (idx ? (int64_t)idx[i] : i) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        h[u] = j[u] >= 0 ? row[j[u]] : (uint16_t)0;
+        dbits[u] = j[u] >= 0 ? __ldg(Db + j[u]) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned mag = h[u] & 0x7fffu;
+        if (mag == 0) continue;
+        amag = max(amag, mag);
+        unsigned long long sa, sd;
+        int e_a, e_d;
+        bf16_fields(h[u], sa, e_a);
+        f64_fields(dbits[u], sd, e_d);
+        ebm = max(ebm, frexp_exp(sa * sd, e_a + e_d));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -414,8 +429,7 @@ __device__ __forceinline__ void balanced_digits(long long v, int (&dig)[ND]) {
 }
 
 __device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
-  return (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(lo)) |
-         ((uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(hi)) << 16);
+  return bf16_bits_small(lo) | (bf16_bits_small(hi) << 16);
 }
 
 // The digit planes: plane s of A (SA planes) and plane t of B (SB planes),

@@ -131,6 +131,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// BF16 bits of a small integer d (|d| <= 2^8, so exact in BF16) without the
+// conversion pipe: d + 1.5 2^23 as FP32 bits is exact, subtracting 1.5 2^23
+// in FP32 gives float(d) exactly, and its top 16 bits are the BF16 value
+// (the low 16 bits are zero for at most 8 significant bits).
+__device__ __forceinline__ uint32_t bf16_bits_small(int d) {
+  return __float_as_uint(__int_as_float(d + 0x4B400000) - 12582912.0f) >> 16;
+}
+
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
 // Bits 4-5: accumulator type (1 = FP32); 7-9 and 10-12: A and B type (kind::f16:
 // 1 = BF16; kind::tf32: 2 = TF32); 17-22: N / 8; 24-28: M / 16.
