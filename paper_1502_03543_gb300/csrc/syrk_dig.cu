@@ -92,7 +92,6 @@ constexpr int NWP = 4;                                 // weights per pass: 0-3,
 constexpr int CHUNK_STAGES = 6;                        // 192 columns per exact chunk
 constexpr uint32_t A_PLANE = DBM * DSK * 2;            // 8 KB: 128 rows of one digit, one stage
 constexpr uint32_t B_PLANE = DBN * DSK * 2;            // 4 KB
-constexpr int STAGES = 3;
 constexpr uint32_t BUF_COLS = NWP * DBN;               // 256 TMEM columns per chunk buffer
 constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;           // 512
 constexpr int NUM_THREADS = 320;
@@ -108,6 +107,9 @@ struct DigPass {
   static constexpr int NA = PASS == 0 ? 4 : SA;  // A planes loaded
   static constexpr int NB = PASS == 0 ? 4 : SB;  // B planes loaded
   static constexpr uint32_t STAGE_BYTES = NA * A_PLANE + NB * B_PLANE;  // 48 KB or 72 KB
+  // copies in flight: pass 0 has half the pairs per copied K step, so it
+  // keeps one more stage in flight (4 x 48 KB; pass 1 3 x 72 KB)
+  static constexpr int STAGES = PASS == 0 ? 4 : 3;
   static constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
   __host__ __device__ static constexpr bool kept(int s, int t) { return s + t >= W0 && s + t < W0 + NWP && s < NA && t < NB; }
   // the B digits t paired with A digit s in this pass: first_t(s) .. last_t(s)
@@ -130,7 +132,7 @@ constexpr bool pass_groups_ok() {
 static_assert(pass_groups_ok<0>() && pass_groups_ok<1>(), "one MMA per A digit covers the pass's pairs");
 static_assert(5 * DSK * CHUNK_STAGES * 16384 < (1 << 24), "exact chunk");
 static_assert(DigPass<0>::W0 + 2 * NWP - 1 == WMAX, "the two passes cover the weights 0..WMAX");
-static_assert(DigPass<1>::SMEM_BYTES <= 232448, "shared memory of one CTA");
+static_assert(DigPass<0>::SMEM_BYTES <= 232448 && DigPass<1>::SMEM_BYTES <= 232448, "shared memory of one CTA");
 
 // Shared-memory matrix descriptor: K-major operand, rows of 64 bytes (32 BF16)
 // with the 64-byte swizzle; 8-row groups 512 bytes apart (version 1 at bit
@@ -158,15 +160,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * P::STAGE_BYTES);
-  // bars: full[STAGES] | empty[STAGES] | chunk_full[2] | chunk_free[2] | done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::STAGES * P::STAGE_BYTES);
+  // bars: full[stages] | empty[stages] | chunk_full[2] | chunk_free[2] | done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * P::STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full = [&](int s) { return smem_u32(bars + s); };
-  auto empty = [&](int s) { return smem_u32(bars + STAGES + s); };
-  auto chunk_full = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
-  auto chunk_free = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
-  const uint32_t done_bar = smem_u32(bars + 2 * STAGES + 4);
+  auto empty = [&](int s) { return smem_u32(bars + P::STAGES + s); };
+  auto chunk_full = [&](int b) { return smem_u32(bars + 2 * P::STAGES + b); };
+  auto chunk_free = [&](int b) { return smem_u32(bars + 2 * P::STAGES + 2 + b); };
+  const uint32_t done_bar = smem_u32(bars + 2 * P::STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int2 tile = tiles[blockIdx.x];
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int nchunks = (nk + CHUNK_STAGES - 1) / CHUNK_STAGES;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < P::STAGES; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
@@ -197,8 +199,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (lane == 0) {
       int issued = 0;
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        const int s = kb % P::STAGES;
+        const uint32_t ph = (uint32_t)(kb / P::STAGES) & 1u;
         if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
           *abort_flag = 1;
           break;
@@ -210,8 +212,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         issued = kb + 1;
       }
       if (*abort_flag) {  // let every issued copy land before the CTA can exit
-        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-          mbar_wait(full(kb % STAGES), (uint32_t)(kb / STAGES) & 1u, nullptr);
+        for (int kb = issued > P::STAGES ? issued - P::STAGES : 0; kb < issued; ++kb)
+          mbar_wait(full(kb % P::STAGES), (uint32_t)(kb / P::STAGES) & 1u, nullptr);
       }
     }
     __syncwarp();
@@ -225,8 +227,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           *abort_flag = 1;
           break;
         }
-        const int s = kb % STAGES;
-        if (!mbar_wait(full(s), (uint32_t)(kb / STAGES) & 1u, abort_flag)) {
+        const int s = kb % P::STAGES;
+        if (!mbar_wait(full(s), (uint32_t)(kb / P::STAGES) & 1u, abort_flag)) {
           *abort_flag = 1;
           break;
         }
